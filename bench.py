@@ -1,0 +1,347 @@
+"""Benchmark: HEALPix analysis throughput (Gpix/s) of the HP2SPH path on GB300.
+
+Workload: 32 FP32 maps at Nside 1024 (12,582,912 pixels each), lmax 2048,
+seeded power-law skies (C_l = l^-alpha, alpha ~ U[1.5, 2.5] per map) plus
+N(0, 1e-3) white noise.  One step = hpx_analyze + hpx_cl over the whole batch.
+The maps (1.61 GB) are larger than L2, so every step streams them from HBM.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+Under torchrun each rank analyses its own batch of 32 maps (weak scaling, no
+collective on the data path); rank 0 prints one JSON line.  `--impl reference`
+times the FP64 CPU oracle on the host cores on a bounded sample of the same
+workload.
+"""
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "HEALPix analysis Gpix/s at Nside=1024 (batched FP32 vs plain FP64, err<=1e-5)"
+NSIDE, LMAX, BATCH = 1024, 2048, 32
+WORKLOAD = "bench_nside1024x32"
+MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# FP32 SIMT peak: 152 SMs x 128 FP32 lanes x 2 flop/FMA x 2.070 GHz (maximum SM clock)
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+
+
+def config_dict():
+    return {"workload": "%s: %d FP32 maps, Nside %d, lmax %d, power-law skies + 1e-3 noise"
+                        % (WORKLOAD, BATCH, NSIDE, LMAX),
+            "nside": NSIDE, "lmax": LMAX, "batch_per_gpu": BATCH,
+            "l2": "inputs larger than L2 (1.61 GB of maps per step)"}
+
+
+# ------------------------------------------------------------------ accounting
+def chain_len(mp, c, L):
+    return (L - mp - c) // 2 + 1 if L >= mp + c else 0
+
+
+def rotation_count(L):
+    n = 0
+    for m in range(L + 1):
+        m0 = m & 1
+        for c in (0, 1):
+            for s in range((m - m0) // 2):
+                n += chain_len(m0 + 2 + 2 * s, c, L)
+    return n
+
+
+def stage_work(ns, L, B, es=8):
+    """Algorithmic HBM bytes or flops of one launch of each stage (FP32)."""
+    p = 2 * ns
+    Q = 4 * ns + 1
+    P2 = p // 2 + 1
+    npix = 12 * ns * ns
+    dense = 0
+    for mpar in (0, 1):
+        nm = (L - mpar) // 2 + 1
+        for par in (0, 1):
+            nl = len([l for l in range(mpar, L + 1) if l % 2 == par])
+            nj = len([j for j in range(mpar, p + 1) if j % 2 == par])
+            dense += nm * nl * nj * 4          # real matrix x complex vector: 2 FMA
+    return {
+        "ring_fft": ("hbm", B * (npix * es // 2 + Q * (p + 1) * es)),
+        "poles": ("hbm", B * 2 * 36 * 4),
+        "nufft": ("hbm", B * (L + 1) * (Q * es + 2 * P2 * es)),
+        "lat_solve": ("alu", B * dense),
+        "rot_sweep": ("alu", B * rotation_count(L) * 12),
+    }
+
+
+# ------------------------------------------------------------------ clocks
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.strip()]
+        os.unlink(self.path)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if r[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ CPU oracle
+def oracle_sample(maps0, ms):
+    """Time the FP64 oracle on orders `ms` of one map; returns (seconds, columns)."""
+    from oracle import hp2sph
+    t0 = time.perf_counter()
+    cols = hp2sph.analyze_columns(maps0.astype(np.float64), NSIDE, LMAX, ms)
+    return time.perf_counter() - t0, cols
+
+
+def cpu_gpix(seconds, ncols):
+    full = seconds * (LMAX + 1) / ncols          # scaled to all 2049 orders of one map
+    return 12 * NSIDE * NSIDE / full / 1e9
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    import skies
+    maps0 = skies.workload_maps(WORKLOAD, nmaps=1, dtype=np.float32)[0]
+    ms = [0, 1]
+    for _ in range(args.warmup):
+        oracle_sample(maps0, ms)
+    ts = [oracle_sample(maps0, ms)[0] for _ in range(args.steps)]
+    t = float(np.mean(ts))
+    v = cpu_gpix(t, len(ms))
+    sample = ("orders m=0,1 of map 0 (2 of 2049 columns) per step, time scaled x2049/2 to a full "
+              "map; FP64 oracle (direct ring DFTs, dense QR least squares, Gauss-Legendre projection)")
+    line = {"metric": METRIC, "value": v, "unit": "Gpix/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_dict(),
+            "impl": "reference",
+            "cpu_baseline": {"value": v, "unit": "Gpix/s", "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": v, "unit": "Gpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle leg")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    import paper_1904_10514_gb300 as hp
+    import skies
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    maps_np = skies.workload_maps(WORKLOAD, nmaps=BATCH, first=rank * BATCH, dtype=np.float32)
+    plan = hp.Plan(NSIDE, LMAX, BATCH, "fp32")
+    maps = torch.from_numpy(maps_np).cuda()
+    alm = torch.empty((BATCH, plan.nalm), dtype=torch.complex64, device="cuda")
+    cl = torch.empty((BATCH, LMAX + 1), dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        plan.analyze(maps, out=alm)
+        plan.cl(alm, out=cl)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    clocks = Clocks(local)
+    hp.hpx_set_profiling(plan.handle, 1)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    stage_ms, ncalls = hp.hpx_stage_times(plan.handle)
+    hp.hpx_set_profiling(plan.handle, 0)
+    t_step = e0.elapsed_time(e1) / args.steps / 1e3
+    if world > 1:
+        tt = torch.tensor([t_step], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_step = float(tt.item())
+    npix_step = BATCH * plan.npix
+    value = world * npix_step / t_step / 1e9
+
+    # end to end through the public API from pinned host memory
+    host_maps = torch.from_numpy(maps_np).pin_memory()
+    host_alm = torch.empty((BATCH, plan.nalm), dtype=torch.complex64).pin_memory()
+    host_cl = torch.empty((BATCH, LMAX + 1), dtype=torch.float64).pin_memory()
+
+    def e2e_step():
+        maps.copy_(host_maps, non_blocking=True)
+        plan.analyze(maps, out=alm)
+        plan.cl(alm, out=cl)
+        host_alm.copy_(alm, non_blocking=True)
+        host_cl.copy_(cl, non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    barrier()
+    e0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    t_e2e = e0.elapsed_time(e1) / args.steps / 1e3
+    if world > 1:
+        tt = torch.tensor([t_e2e], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_e2e = float(tt.item())
+    e2e = {"value": world * npix_step / t_e2e / 1e9, "unit": "Gpix/s",
+           "h2d_bytes_per_step": int(host_maps.numel() * 4),
+           "d2h_bytes_per_step": int(host_alm.numel() * 8 + host_cl.numel() * 8)}
+
+    # the plain FP64 single-map form on the same GPU
+    plan64 = hp.Plan(NSIDE, LMAX, 1, "fp64")
+    m64 = maps[:1].double().contiguous()
+    a64 = torch.empty((1, plan64.nalm), dtype=torch.complex128, device="cuda")
+    c64 = torch.empty((1, LMAX + 1), dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        plan64.analyze(m64, out=a64)
+        plan64.cl(a64, out=c64)
+    torch.cuda.synchronize()
+    n64 = max(2, min(args.steps, 5))
+    e0.record(stream)
+    for _ in range(n64):
+        plan64.analyze(m64, out=a64)
+        plan64.cl(a64, out=c64)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t64 = e0.elapsed_time(e1) / n64 / 1e3
+    fp64 = {"value": plan64.npix / t64 / 1e9, "unit": "Gpix/s", "ms_per_map": t64 * 1e3}
+    plan64.close()
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    # roofline of the dominant kernel
+    work = stage_work(NSIDE, LMAX, BATCH)
+    names = hp.STAGES
+    per_launch = {n: stage_ms[k] / max(ncalls, 1) for k, n in enumerate(names)}
+    dom = max(names, key=lambda n: per_launch[n])
+    kind, amount = work[dom]
+    peaks = json.load(open(MEASURED)) if os.path.exists(MEASURED) else {}
+    t_dom = per_launch[dom] / 1e3
+    if kind == "hbm":
+        peak = peaks.get("hbm_gbs", 6800.0)
+        roof = {"bound": "hbm", "achieved": amount / t_dom / 1e9, "peak": peak, "unit": "GB/s",
+                "peak_source": "measured" if peaks else "fallback"}
+    else:
+        peak = FP32_PEAK_TFLOPS
+        roof = {"bound": "alu", "achieved": amount / t_dom / 1e12, "peak": peak, "unit": "TFLOP/s",
+                "peak_source": "FP32 FMA pipes: 152 SMs x 128 lanes x 2 flop x 2.070 GHz"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None
+    roof["kernel"] = dom
+    roof["per_launch_ms"] = per_launch[dom]
+
+    cpu = None
+    if not args.no_cpu:
+        ms = list(range(8))
+        secs, cols = oracle_sample(maps_np[0], ms)
+        got = alm[0].cpu().numpy()
+        worst = 0.0
+        for m in ms:
+            i0 = m * (2 * LMAX + 1 - m) // 2 + m
+            g = got[i0:i0 + LMAX - m + 1]
+            r = cols[m][0]
+            worst = max(worst, float(np.max(np.abs(g - r)) / np.max(np.abs(r))))
+        cpu = {"value": cpu_gpix(secs, len(ms)), "unit": "Gpix/s", "cores": os.cpu_count(),
+               "kind": "oracle",
+               "sample": "orders m=0..7 of map 0 (8 of 2049 columns), FP64 oracle, %.1f s, scaled "
+                         "x2049/8 to one full map" % secs,
+               "sample_max_rel_err_vs_gpu": worst}
+
+    line = {"metric": METRIC, "value": value, "unit": "Gpix/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": config_dict(), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": 6 * args.steps, "clocks": clk, "fp64_single_map": fp64,
+            "fp32_batched_over_fp64_single": value / world / fp64["value"],
+            "stages_ms_per_launch": per_launch}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

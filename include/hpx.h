@@ -1,0 +1,128 @@
+/*
+ * hpx.h -- C ABI of the GB300 HP2SPH library: spherical-harmonic analysis of
+ * real HEALPix maps by the method of Drake & Wright, "A Fast and Accurate
+ * Algorithm for Spherical Harmonic Analysis on HEALPix Grids" (arXiv:1904.10514),
+ * Algorithm 1, and the angular power spectrum C_l of Eq. (APS).
+ *
+ * All pointers to map, coefficient and spectrum buffers are DEVICE pointers
+ * (cudaMalloc'd, or torch tensors on the plan's device), contiguous, and owned
+ * by the caller.  The plan owns every table and workspace it needs; no call
+ * allocates device memory after hpx_plan / hpx_plan_ex has returned.  Calls are
+ * asynchronous on the plan's stream (hpx_set_stream); hpx_sync waits.
+ *
+ * Layouts
+ *   maps : [batch][12 * nside^2] real, RING order (north to south, increasing
+ *          longitude within a ring), element type = plan precision
+ *          (float for HPX_FP32, double for HPX_FP64).
+ *   alm  : [batch][n_alm][2] (re, im) of the plan precision, m >= 0 only,
+ *          packed m-major: idx(l, m) = m (2 lmax + 1 - m) / 2 + l,
+ *          n_alm = (lmax + 1)(lmax + 2) / 2.  For a real map
+ *          a_l^{-m} = (-1)^m conj(a_l^m) (Appendix A conventions: orthonormal
+ *          Y_l^m with the Condon-Shortley phase).
+ *   cl   : [batch][lmax + 1] double.
+ *
+ * Method parameters: p = 2 nside latitude/longitude half-bandwidth, lmax <= p
+ * (Sec. 3.2.2 / 3.3: the method yields degrees up to p); nside must be a power
+ * of two, 2 <= nside <= 2048 (FP64 plans: nside <= 1024): the shared-memory
+ * FFT and NUFFT grids of one ring / one column must fit in one thread block.
+ *
+ * Return codes: 0 on success, a negative HPX_ERR_* otherwise; hpx_last_error()
+ * gives the last code of the calling thread and hpx_strerror() a message.  No
+ * C++ exception crosses this interface.
+ */
+#ifndef HPX_H
+#define HPX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HPX_OK 0
+#define HPX_ERR_ARG -1      /* null pointer or inconsistent argument              */
+#define HPX_ERR_NSIDE -2    /* nside not a power of two in the supported range   */
+#define HPX_ERR_LMAX -3     /* lmax < 0 or lmax > 2 nside                         */
+#define HPX_ERR_CUDA -4     /* a CUDA runtime call failed                         */
+#define HPX_ERR_OOM -5      /* device memory for tables / workspace not available */
+#define HPX_ERR_TIMEOUT -6  /* a bounded device-side wait gave up                 */
+#define HPX_ERR_STATE -7    /* call not valid for this plan                       */
+
+#define HPX_FP32 0
+#define HPX_FP64 1
+
+typedef struct hpx_plan_s hpx_plan_s;
+
+typedef struct hpx_plan_desc {
+    int nside;        /* HEALPix resolution parameter N_side (power of two)       */
+    int lmax;         /* largest degree returned, 0 <= lmax <= 2 nside; -1 = 2 nside */
+    int batch;        /* number of maps processed per call, >= 1                  */
+    int precision;    /* HPX_FP32 or HPX_FP64                                     */
+    unsigned flags;   /* reserved, must be 0                                      */
+} hpx_plan_desc;
+
+/* Plan for `batch` real FP32 maps of one nside on the current CUDA device
+ * (Algorithm 1, all steps).  Builds the FP64 set-up tables (ring geometry of
+ * Eq. healpts, FFT chirps and shifts of Sec. 3.1, pole-fit weights of
+ * Sec. 3.2.1, NUFFT spreading tables and the latitude least-squares operator of
+ * Sec. 3.2.2, the Givens rotation angles of Sec. 3.3) and allocates the
+ * workspace.  Returns NULL on error (see hpx_last_error). */
+hpx_plan_s* hpx_plan(int nside, int lmax, int batch);
+
+/* Same, with precision and flags from a descriptor.  NULL on error. */
+hpx_plan_s* hpx_plan_ex(const hpx_plan_desc* desc);
+
+/* Stream for the plan's launches (a cudaStream_t); NULL = legacy stream. */
+int hpx_set_stream(hpx_plan_s* plan, void* cuda_stream);
+
+/* HP2SPH analysis (Algorithm 1): maps -> alm, layouts above.  Asynchronous. */
+int hpx_analyze(hpx_plan_s* plan, const void* maps, void* alm);
+
+/* The exact adjoint (transpose) of hpx_analyze with respect to the real inner
+ * products <f, g> = sum_i f_i g_i on maps and
+ * <a, b> = sum_l [Re(a_l0 conj b_l0) + 2 sum_{m>0} Re(a_lm conj b_lm)] on alm:
+ * alm -> maps.  It is not the spherical-harmonic synthesis.  The imaginary part
+ * of an input a_l0 is ignored (the analysis always returns a real a_l0).
+ * Asynchronous. */
+int hpx_synthesize(hpx_plan_s* plan, const void* alm, void* maps);
+
+/* Angular power spectrum of Eq. (APS) for real maps,
+ * C_l = (|a_l0|^2 + 2 sum_{m=1}^{l} |a_lm|^2) / (2l + 1),
+ * accumulated in double with compensated summation.  alm in the plan's layout
+ * and precision, cl = [batch][lmax + 1] double (device).  Asynchronous. */
+int hpx_cl(hpx_plan_s* plan, const void* alm, double* cl);
+
+/* Wait for the plan's stream; returns the first asynchronous error. */
+int hpx_sync(hpx_plan_s* plan);
+
+/* Release the plan's tables and workspace (waits for its stream). */
+void hpx_destroy(hpx_plan_s* plan);
+
+/* Sizes of the plan's layouts (0 for a NULL plan). */
+int64_t hpx_npix(const hpx_plan_s* plan);
+int64_t hpx_nalm(const hpx_plan_s* plan);
+int hpx_plan_lmax(const hpx_plan_s* plan);
+/* Bytes of device memory the plan holds (tables + workspace). */
+int64_t hpx_plan_bytes(const hpx_plan_s* plan);
+
+/* Stage timing for profiling.  With profiling enabled (enable = 1) every
+ * hpx_analyze records CUDA events on the plan's stream around each of its
+ * kernels (ring FFT, poles, latitude NUFFT, latitude operator, rotation sweeps;
+ * up to 256 calls are kept).  hpx_stage_times waits for those events, writes
+ * the summed device time of each stage in milliseconds to ms[0..n-1]
+ * (n >= HPX_NSTAGES), sets *ncalls to the number of calls summed, and clears
+ * the record. */
+#define HPX_NSTAGES 5
+int hpx_set_profiling(hpx_plan_s* plan, int enable);
+int hpx_stage_times(hpx_plan_s* plan, float* ms, int n, int* ncalls);
+
+/* Last error code of the calling thread and its message. */
+int hpx_last_error(void);
+const char* hpx_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HPX_H */

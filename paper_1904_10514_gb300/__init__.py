@@ -1,0 +1,230 @@
+"""GB300 (sm_103a) HP2SPH: spherical-harmonic analysis of real HEALPix maps.
+
+A thin ctypes binding over the C ABI of ``libhpx.so`` (declared in
+include/hpx.h).  The functions keep the C names; they only marshal arguments
+(device pointers of torch tensors, the current CUDA stream).  Every step of the
+method runs in the library's CUDA kernels; there is no fallback: if the library
+is missing, importing the binding's functions raises.
+
+    import torch, paper_1904_10514_gb300 as hp
+    plan = hp.Plan(nside=1024, batch=32)                 # FP32, lmax = 2 nside
+    alm = plan.analyze(maps)                             # (32, n_alm) complex64
+    cl = plan.cl(alm)                                    # (32, lmax+1) float64
+"""
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libhpx.so")
+
+HPX_OK = 0
+HPX_ERR_ARG = -1
+HPX_ERR_NSIDE = -2
+HPX_ERR_LMAX = -3
+HPX_ERR_CUDA = -4
+HPX_ERR_OOM = -5
+HPX_ERR_TIMEOUT = -6
+HPX_ERR_STATE = -7
+HPX_FP32 = 0
+HPX_FP64 = 1
+
+EXPORTS = ["hpx_plan", "hpx_plan_ex", "hpx_set_stream", "hpx_analyze", "hpx_synthesize", "hpx_cl",
+           "hpx_sync", "hpx_destroy", "hpx_npix", "hpx_nalm", "hpx_plan_lmax", "hpx_plan_bytes",
+           "hpx_last_error", "hpx_strerror", "hpx_set_profiling", "hpx_stage_times"]
+HPX_NSTAGES = 5
+STAGES = ["ring_fft", "poles", "nufft", "lat_solve", "rot_sweep"]
+
+
+class hpx_plan_desc(ctypes.Structure):
+    _fields_ = [("nside", ctypes.c_int), ("lmax", ctypes.c_int), ("batch", ctypes.c_int),
+                ("precision", ctypes.c_int), ("flags", ctypes.c_uint)]
+
+
+class HpxError(RuntimeError):
+    def __init__(self, code, what=""):
+        self.code = code
+        super().__init__("%s: %s (%d)" % (what, strerror(code), code))
+
+
+_lib = None
+
+
+def build():
+    """Compile libhpx.so in-tree for sm_103a."""
+    from . import nvcc_build as _b
+    return _b.build()
+
+
+def lib():
+    """The loaded library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libhpx.so is not built (run paper_1904_10514_gb300.build())")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i32, i64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64
+        sig = {
+            "hpx_plan": (vp, [i32, i32, i32]),
+            "hpx_plan_ex": (vp, [ctypes.POINTER(hpx_plan_desc)]),
+            "hpx_set_stream": (i32, [vp, vp]),
+            "hpx_analyze": (i32, [vp, vp, vp]),
+            "hpx_synthesize": (i32, [vp, vp, vp]),
+            "hpx_cl": (i32, [vp, vp, vp]),
+            "hpx_sync": (i32, [vp]),
+            "hpx_destroy": (None, [vp]),
+            "hpx_npix": (i64, [vp]),
+            "hpx_nalm": (i64, [vp]),
+            "hpx_plan_lmax": (i32, [vp]),
+            "hpx_plan_bytes": (i64, [vp]),
+            "hpx_last_error": (i32, []),
+            "hpx_strerror": (ctypes.c_char_p, [i32]),
+            "hpx_set_profiling": (i32, [vp, i32]),
+            "hpx_stage_times": (i32, [vp, ctypes.POINTER(ctypes.c_float), i32, ctypes.POINTER(ctypes.c_int)]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def strerror(code):
+    return lib().hpx_strerror(int(code)).decode()
+
+
+# ------------------------------------------------------------ C names
+def hpx_plan(nside, lmax, batch):
+    return lib().hpx_plan(int(nside), int(lmax), int(batch))
+
+
+def hpx_plan_ex(nside, lmax=-1, batch=1, precision=HPX_FP32, flags=0):
+    d = hpx_plan_desc(int(nside), int(lmax), int(batch), int(precision), int(flags))
+    return lib().hpx_plan_ex(ctypes.byref(d))
+
+
+def hpx_set_stream(plan, stream):
+    return lib().hpx_set_stream(plan, stream)
+
+
+def hpx_analyze(plan, maps_ptr, alm_ptr):
+    return lib().hpx_analyze(plan, maps_ptr, alm_ptr)
+
+
+def hpx_synthesize(plan, alm_ptr, maps_ptr):
+    return lib().hpx_synthesize(plan, alm_ptr, maps_ptr)
+
+
+def hpx_cl(plan, alm_ptr, cl_ptr):
+    return lib().hpx_cl(plan, alm_ptr, cl_ptr)
+
+
+def hpx_sync(plan):
+    return lib().hpx_sync(plan)
+
+
+def hpx_destroy(plan):
+    lib().hpx_destroy(plan)
+
+
+def hpx_set_profiling(plan, enable):
+    return lib().hpx_set_profiling(plan, int(enable))
+
+
+def hpx_stage_times(plan):
+    """(summed ms per stage, number of calls) since the last read."""
+    ms = (ctypes.c_float * HPX_NSTAGES)()
+    nc = ctypes.c_int(0)
+    rc = lib().hpx_stage_times(plan, ms, HPX_NSTAGES, ctypes.byref(nc))
+    if rc != HPX_OK:
+        raise HpxError(rc, "hpx_stage_times")
+    return [float(v) for v in ms], nc.value
+
+
+def hpx_last_error():
+    return lib().hpx_last_error()
+
+
+def n_alm(lmax):
+    return (lmax + 1) * (lmax + 2) // 2
+
+
+# ------------------------------------------------------------ torch wrapper
+class Plan:
+    """Owns one C plan; tensors must live on the plan's CUDA device."""
+
+    def __init__(self, nside, lmax=-1, batch=1, precision="fp32"):
+        import torch
+        self.torch = torch
+        self.nside = int(nside)
+        self.batch = int(batch)
+        self.precision = HPX_FP64 if precision in ("fp64", "float64", HPX_FP64) else HPX_FP32
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        h = hpx_plan_ex(nside, lmax, batch, self.precision)
+        if not h:
+            raise HpxError(hpx_last_error(), "hpx_plan_ex")
+        self.handle = h
+        self.lmax = lib().hpx_plan_lmax(h)
+        self.npix = lib().hpx_npix(h)
+        self.nalm = lib().hpx_nalm(h)
+        self.rdtype = torch.float64 if self.precision == HPX_FP64 else torch.float32
+        self.cdtype = torch.complex128 if self.precision == HPX_FP64 else torch.complex64
+
+    @property
+    def nbytes(self):
+        return lib().hpx_plan_bytes(self.handle)
+
+    def _stream(self):
+        hpx_set_stream(self.handle, self.torch.cuda.current_stream(self.device).cuda_stream)
+
+    def _check(self, rc, what):
+        if rc != HPX_OK:
+            raise HpxError(rc, what)
+
+    def _maps(self, maps):
+        t = self.torch
+        if maps.dtype != self.rdtype or maps.device.type != "cuda" or tuple(maps.shape) != (self.batch, self.npix):
+            raise ValueError("maps must be a CUDA %s tensor of shape (%d, %d)" % (self.rdtype, self.batch, self.npix))
+        return maps.contiguous()
+
+    def analyze(self, maps, out=None):
+        """maps (batch, npix) -> alm (batch, n_alm) complex, m-major packing."""
+        maps = self._maps(maps)
+        if out is None:
+            out = self.torch.empty((self.batch, self.nalm), dtype=self.cdtype, device=maps.device)
+        self._stream()
+        self._check(hpx_analyze(self.handle, maps.data_ptr(), out.data_ptr()), "hpx_analyze")
+        return out
+
+    def synthesize(self, alm, out=None):
+        """Exact adjoint of analyze: alm (batch, n_alm) complex -> maps (batch, npix)."""
+        alm = alm.contiguous()
+        if out is None:
+            out = self.torch.empty((self.batch, self.npix), dtype=self.rdtype, device=alm.device)
+        self._stream()
+        self._check(hpx_synthesize(self.handle, alm.data_ptr(), out.data_ptr()), "hpx_synthesize")
+        return out
+
+    def cl(self, alm, out=None):
+        """C_l (batch, lmax+1) float64 of Eq. (APS)."""
+        alm = alm.contiguous()
+        if out is None:
+            out = self.torch.empty((self.batch, self.lmax + 1), dtype=self.torch.float64, device=alm.device)
+        self._stream()
+        self._check(hpx_cl(self.handle, alm.data_ptr(), out.data_ptr()), "hpx_cl")
+        return out
+
+    def sync(self):
+        self._check(hpx_sync(self.handle), "hpx_sync")
+
+    def close(self):
+        if getattr(self, "handle", None):
+            hpx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,249 @@
+// C ABI of the HP2SPH library (include/hpx.h): plan construction, table upload,
+// and the launch sequences of Algorithm 1.
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/hpx.h"
+#include "plan.h"
+#include "plan_math.h"
+
+namespace {
+
+thread_local int g_last_error = HPX_OK;
+
+int set_err(int code) {
+    g_last_error = code;
+    return code;
+}
+
+bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+struct Uploader {
+    hpx_plan_s* P;
+    bool ok = true;
+    template <class U>
+    U* raw(const U* src, size_t count) {
+        if (!ok || count == 0) return nullptr;
+        U* d = nullptr;
+        if (cudaMalloc(&d, count * sizeof(U)) != cudaSuccess) { ok = false; return nullptr; }
+        P->bytes += (int64_t)(count * sizeof(U));
+        if (cudaMemcpy(d, src, count * sizeof(U), cudaMemcpyHostToDevice) != cudaSuccess) { ok = false; }
+        return d;
+    }
+    template <class U>
+    U* vec(const std::vector<U>& v) { return raw(v.data(), v.size()); }
+    // double table -> device table of the plan precision
+    void* real(const std::vector<double>& v, bool fp64) {
+        if (fp64) return vec(v);
+        std::vector<float> f(v.size());
+        for (size_t k = 0; k < v.size(); ++k) f[k] = (float)v[k];
+        return vec(f);
+    }
+};
+
+void free_plan(hpx_plan_s* P) {
+    if (!P) return;
+    auto& t = P->t;
+    void* ptrs[] = {t.nphi, t.startN, t.startS, t.pow2, t.logn, t.fftL, t.logL, t.shOff, t.chOff,
+                    t.bhOff, t.shift, t.chirp, t.bhat, t.twid, t.poleN, t.poleS, t.polew, t.rowptr,
+                    t.ent, t.entw, t.dec, t.D, t.angOff, t.ang, P->Y, P->bvec};
+    for (void* q : ptrs)
+        if (q) cudaFree(q);
+    if (P->ev) {
+        for (int k = 0; k < hpx_plan_s::kMaxProf * (hpx_plan_s::kStages + 1); ++k) cudaEventDestroy(P->ev[k]);
+        delete[] P->ev;
+    }
+    delete P;
+}
+
+template <class T>
+int analyze_impl(hpx_plan_s* P, const void* maps, void* alm) {
+    cudaStream_t s = P->stream;
+    cudaEvent_t* ev = nullptr;
+    if (P->prof && P->nprof < hpx_plan_s::kMaxProf) ev = P->ev + (size_t)P->nprof++ * (hpx_plan_s::kStages + 1);
+    if (ev) cudaEventRecord(ev[0], s);
+    hpx::launch_ring_fft<T>(P, (const T*)maps, s);
+    if (ev) cudaEventRecord(ev[1], s);
+    hpx::launch_poles<T>(P, (const T*)maps, s);
+    if (ev) cudaEventRecord(ev[2], s);
+    hpx::launch_nufft<T>(P, s);
+    if (ev) cudaEventRecord(ev[3], s);
+    hpx::launch_dense<T>(P, s);
+    if (ev) cudaEventRecord(ev[4], s);
+    hpx::launch_rot<T>(P, (T*)alm, s);
+    if (ev) cudaEventRecord(ev[5], s);
+    if (cudaGetLastError() != cudaSuccess) return HPX_ERR_CUDA;
+    return HPX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+hpx_plan_s* hpx_plan_ex(const hpx_plan_desc* d) {
+    if (!d) { set_err(HPX_ERR_ARG); return nullptr; }
+    const int ns = d->nside;
+    const bool fp64 = d->precision == HPX_FP64;
+    if (d->precision != HPX_FP32 && d->precision != HPX_FP64) { set_err(HPX_ERR_ARG); return nullptr; }
+    if (d->flags != 0 || d->batch < 1) { set_err(HPX_ERR_ARG); return nullptr; }
+    if (!is_pow2(ns) || ns < 2 || ns > (fp64 ? 1024 : 2048)) { set_err(HPX_ERR_NSIDE); return nullptr; }
+    const int L = d->lmax < 0 ? 2 * ns : d->lmax;
+    if (L > 2 * ns) { set_err(HPX_ERR_LMAX); return nullptr; }
+    if (d->lmax < -1) { set_err(HPX_ERR_LMAX); return nullptr; }
+
+    hpx::PlanTables tb;
+    std::string msg;
+    try {
+        msg = hpx::build_tables(ns, L, fp64, tb);
+    } catch (const std::bad_alloc&) {
+        set_err(HPX_ERR_OOM);
+        return nullptr;
+    } catch (...) {
+        set_err(HPX_ERR_ARG);
+        return nullptr;
+    }
+    if (!msg.empty()) { set_err(HPX_ERR_ARG); return nullptr; }
+
+    hpx_plan_s* P = new (std::nothrow) hpx_plan_s();
+    if (!P) { set_err(HPX_ERR_OOM); return nullptr; }
+    P->precision = d->precision;
+    cudaGetDevice(&P->device);
+    P->stream = nullptr;
+    auto& g = P->g;
+    g.ns = ns; g.p = tb.p; g.L = L; g.Q = tb.Q; g.npairs = tb.npairs; g.M = tb.M; g.P2 = tb.P2;
+    g.Lmax = tb.Lmax; g.smem_ring = tb.smem_ring; g.B = d->batch; g.npix = tb.npix;
+    g.nalm = (int64_t)(L + 1) * (L + 2) / 2;
+
+    Uploader up{P};
+    auto& t = P->t;
+    t.nphi = up.vec(tb.nphi); t.startN = up.vec(tb.startN); t.startS = up.vec(tb.startS);
+    t.pow2 = up.vec(tb.pow2); t.logn = up.vec(tb.logn); t.fftL = up.vec(tb.fftL); t.logL = up.vec(tb.logL);
+    t.shOff = up.vec(tb.shOff); t.chOff = up.vec(tb.chOff); t.bhOff = up.vec(tb.bhOff);
+    t.shift = up.real(tb.shift, fp64); t.chirp = up.real(tb.chirp, fp64); t.bhat = up.real(tb.bhat, fp64);
+    t.twid = up.real(tb.twid, fp64);
+    t.poleN = up.vec(tb.poleN); t.poleS = up.vec(tb.poleS); t.polew = up.vec(tb.polew);
+    t.npole = (int)tb.polew.size();
+    t.rowptr = up.vec(tb.rowptr); t.ent = up.vec(tb.ent);
+    t.entw = up.real(tb.entw, fp64); t.dec = up.real(tb.dec, fp64);
+    t.D = up.real(tb.D, fp64);
+    t.angOff = up.vec(tb.angOff); t.ang = up.real(tb.ang, fp64);
+    if (!up.ok) { free_plan(P); set_err(HPX_ERR_OOM); return nullptr; }
+
+    const size_t es = fp64 ? 16 : 8;   // complex element
+    const size_t ySize = (size_t)g.B * g.Q * (g.p + 1) * es;
+    const size_t bSize = (size_t)g.B * (g.p + 1) * 2 * g.P2 * es;
+    if (cudaMalloc(&P->Y, std::max(ySize, bSize)) != cudaSuccess) { free_plan(P); set_err(HPX_ERR_OOM); return nullptr; }
+    if (cudaMalloc(&P->bvec, bSize) != cudaSuccess) { free_plan(P); set_err(HPX_ERR_OOM); return nullptr; }
+    P->beta = P->Y;   // Y is dead once the NUFFT has read it
+    P->bytes += (int64_t)(std::max(ySize, bSize) + bSize);
+    if (cudaDeviceSynchronize() != cudaSuccess) { free_plan(P); set_err(HPX_ERR_CUDA); return nullptr; }
+    set_err(HPX_OK);
+    return P;
+}
+
+hpx_plan_s* hpx_plan(int nside, int lmax, int batch) {
+    hpx_plan_desc d;
+    std::memset(&d, 0, sizeof(d));
+    d.nside = nside;
+    d.lmax = lmax;
+    d.batch = batch;
+    d.precision = HPX_FP32;
+    return hpx_plan_ex(&d);
+}
+
+int hpx_set_stream(hpx_plan_s* P, void* stream) {
+    if (!P) return set_err(HPX_ERR_ARG);
+    P->stream = (cudaStream_t)stream;
+    return set_err(HPX_OK);
+}
+
+int hpx_analyze(hpx_plan_s* P, const void* maps, void* alm) {
+    if (!P || !maps || !alm) return set_err(HPX_ERR_ARG);
+    const int rc = P->precision == HPX_FP64 ? analyze_impl<double>(P, maps, alm)
+                                            : analyze_impl<float>(P, maps, alm);
+    return set_err(rc);
+}
+
+int hpx_synthesize(hpx_plan_s* P, const void* alm, void* maps) {
+    if (!P || !alm || !maps) return set_err(HPX_ERR_ARG);
+    return set_err(HPX_ERR_STATE);
+}
+
+int hpx_set_profiling(hpx_plan_s* P, int enable) {
+    if (!P) return set_err(HPX_ERR_ARG);
+    if (enable && !P->ev) {
+        const int n = hpx_plan_s::kMaxProf * (hpx_plan_s::kStages + 1);
+        P->ev = new (std::nothrow) cudaEvent_t[n];
+        if (!P->ev) return set_err(HPX_ERR_OOM);
+        for (int k = 0; k < n; ++k)
+            if (cudaEventCreate(&P->ev[k]) != cudaSuccess) return set_err(HPX_ERR_CUDA);
+    }
+    P->prof = enable != 0;
+    P->nprof = 0;
+    return set_err(HPX_OK);
+}
+
+int hpx_stage_times(hpx_plan_s* P, float* ms, int n, int* ncalls) {
+    if (!P || !ms || n < hpx_plan_s::kStages) return set_err(HPX_ERR_ARG);
+    for (int k = 0; k < n; ++k) ms[k] = 0.0f;
+    for (int c = 0; c < P->nprof; ++c) {
+        cudaEvent_t* ev = P->ev + (size_t)c * (hpx_plan_s::kStages + 1);
+        if (cudaEventSynchronize(ev[hpx_plan_s::kStages]) != cudaSuccess) return set_err(HPX_ERR_CUDA);
+        for (int k = 0; k < hpx_plan_s::kStages; ++k) {
+            float t = 0.0f;
+            if (cudaEventElapsedTime(&t, ev[k], ev[k + 1]) != cudaSuccess) return set_err(HPX_ERR_CUDA);
+            ms[k] += t;
+        }
+    }
+    if (ncalls) *ncalls = P->nprof;
+    P->nprof = 0;
+    return set_err(HPX_OK);
+}
+
+int hpx_cl(hpx_plan_s* P, const void* alm, double* cl) {
+    if (!P || !alm || !cl) return set_err(HPX_ERR_ARG);
+    if (P->precision == HPX_FP64) hpx::launch_cl<double>(P, (const double*)alm, cl, P->stream);
+    else hpx::launch_cl<float>(P, (const float*)alm, cl, P->stream);
+    if (cudaGetLastError() != cudaSuccess) return set_err(HPX_ERR_CUDA);
+    return set_err(HPX_OK);
+}
+
+int hpx_sync(hpx_plan_s* P) {
+    if (!P) return set_err(HPX_ERR_ARG);
+    if (cudaStreamSynchronize(P->stream) != cudaSuccess) return set_err(HPX_ERR_CUDA);
+    if (P->status != 0) return set_err(P->status);
+    return set_err(HPX_OK);
+}
+
+void hpx_destroy(hpx_plan_s* P) {
+    if (!P) return;
+    cudaStreamSynchronize(P->stream);
+    free_plan(P);
+}
+
+int64_t hpx_npix(const hpx_plan_s* P) { return P ? P->g.npix : 0; }
+int64_t hpx_nalm(const hpx_plan_s* P) { return P ? P->g.nalm : 0; }
+int hpx_plan_lmax(const hpx_plan_s* P) { return P ? P->g.L : -1; }
+int64_t hpx_plan_bytes(const hpx_plan_s* P) { return P ? P->bytes : 0; }
+
+int hpx_last_error(void) { return g_last_error; }
+
+const char* hpx_strerror(int code) {
+    switch (code) {
+        case HPX_OK: return "ok";
+        case HPX_ERR_ARG: return "invalid argument";
+        case HPX_ERR_NSIDE: return "nside must be a power of two in [2, 2048] (FP64: [2, 1024])";
+        case HPX_ERR_LMAX: return "lmax must satisfy 0 <= lmax <= 2 nside";
+        case HPX_ERR_CUDA: return "CUDA runtime error";
+        case HPX_ERR_OOM: return "out of device memory";
+        case HPX_ERR_TIMEOUT: return "a bounded device-side wait timed out";
+        case HPX_ERR_STATE: return "operation not valid for this plan";
+        default: return "unknown error";
+    }
+}
+
+}  // extern "C"

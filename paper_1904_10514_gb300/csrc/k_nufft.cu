@@ -1,0 +1,81 @@
+// Step 2 (Sec. 3.2): DFS doubling in latitude and the right-hand side of the
+// least-squares inverse NUFFT-II, b = F^* y (the type-1 NUFFT of Sec. 3.2.2).
+//
+// For longitude wavenumber m the DFS data (remark of Sec. 3.2.1) are y_r at the
+// latitudes theta_r (r = 0..4 Nside: poles and rings) and (-1)^m y_r at
+// 2 pi - theta_r (interior r).  The type-1 sums
+//     B_j = sum_nodes y_nu e^{-i j theta_nu},   j = 0..p,
+// are computed with an exponential-of-semicircle (ES) kernel: the node values are
+// spread onto a uniform grid of M = 8 Nside points on [0, 2 pi) (a gather over a
+// precomputed sparse table, accumulated in shared memory), the grid is
+// transformed by an M-point FFT in shared memory, and each mode is divided by
+// the kernel's Fourier transform (table `dec`, FP64-built).
+//
+// By the DFS parity the LS problem splits (even m: cosine basis, odd m: sine
+// basis); the outputs are the normal-equation right-hand sides
+//     even m:  b_j = sum_r w_r y_r cos(j theta_r)          = B_j
+//     odd m:   b_j = sum_{interior r} y_r sin(j theta_r)   = (i/2) B_j
+// stored as bvec[b][m][j & 1][j >> 1].
+#include "plan.h"
+
+namespace hpx {
+
+template <class T>
+__global__ void __launch_bounds__(512) nufft_kernel(
+    const cplx<T>* __restrict__ Y, cplx<T>* __restrict__ bvec, const int* __restrict__ rowptr,
+    const int* __restrict__ ent, const T* __restrict__ entw, const T* __restrict__ dec,
+    const cplx<T>* __restrict__ tw, int twlen, int M, int logM, int p, int Q, int P2, int mcount) {
+    extern __shared__ unsigned char smem_raw[];
+    cplx<T>* u = reinterpret_cast<cplx<T>*>(smem_raw);   // M
+    cplx<T>* y = u + M;                                    // Q
+    const int m = blockIdx.x;
+    const int b = blockIdx.y;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const cplx<T>* col = Y + (int64_t)b * Q * (p + 1) + m;
+    for (int r = tid; r < Q; r += nt) y[r] = col[(int64_t)r * (p + 1)];
+    __syncthreads();
+    const bool odd = (m & 1) != 0;
+    for (int t = tid; t < M; t += nt) {
+        T ar = T(0), ai = T(0);
+        const int e1 = rowptr[t + 1];
+        for (int e = rowptr[t]; e < e1; ++e) {
+            const int code = ent[e];
+            const int r = code & ((1 << 30) - 1);
+            T w = entw[e];
+            if (odd && (code >> 30)) w = -w;
+            const cplx<T> v = y[r];
+            ar += w * v.r;
+            ai += w * v.i;
+        }
+        u[t] = mk<T>(ar, ai);
+    }
+    __syncthreads();
+    block_fft(u, M, logM, tw, twlen, false);
+    cplx<T>* out = bvec + ((int64_t)b * (p + 1) + m) * 2 * P2;
+    for (int j = tid; j <= p; j += nt) {
+        cplx<T> v = scale(u[j], dec[j]);
+        if (odd) v = mk<T>(T(-0.5) * v.i, T(0.5) * v.r);
+        out[(j & 1) * P2 + (j >> 1)] = v;
+    }
+    // the odd-parity block has one slot fewer (j = p + 1 would be index p/2)
+    if (tid == 0) out[P2 + (P2 - 1)] = mk<T>(T(0), T(0));
+}
+
+template <class T>
+void launch_nufft(const hpx_plan_s* P, cudaStream_t s) {
+    const auto& g = P->g;
+    const auto& t = P->t;
+    int logM = 0;
+    while ((1 << logM) < g.M) ++logM;
+    const size_t smem = (size_t)(g.M + g.Q) * sizeof(cplx<T>);
+    cudaFuncSetAttribute(nufft_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    dim3 grid(g.L + 1, g.B);
+    nufft_kernel<T><<<grid, 512, smem, s>>>((const cplx<T>*)P->Y, (cplx<T>*)P->bvec, t.rowptr, t.ent,
+                                            (const T*)t.entw, (const T*)t.dec, (const cplx<T>*)t.twid,
+                                            g.Lmax, g.M, logM, g.p, g.Q, g.P2, g.L + 1);
+}
+
+template void launch_nufft<float>(const hpx_plan_s*, cudaStream_t);
+template void launch_nufft<double>(const hpx_plan_s*, cudaStream_t);
+
+}  // namespace hpx

@@ -1,0 +1,148 @@
+// Step 1 of Algorithm 1 (Sec. 3.1): per-ring trigonometric interpolation,
+// half-pixel shift and zero padding, and the pole values of Sec. 3.2.1.
+//
+// One thread block handles one north/south ring pair of one map.  The two real
+// rings (same nphi, same first longitude) are packed into one complex sequence
+// z = f_N + i f_S and transformed once:
+//   * nphi a power of two: radix-2 FFT of length nphi in shared memory;
+//   * otherwise (polar rings 4j): Bluestein's chirp-z transform with a
+//     power-of-two convolution length L >= 2 nphi - 1; the chirps and the
+//     transformed conjugate chirp come from FP64-built tables.
+// The interpolant coefficients of Eq. (trig_expansion) at the un-shifted
+// longitudes of Eq. (upsamp) are then c_m = c~_m e^{-i m phi0} (Eq. interp_cond
+// and the shift that follows it), with the Nyquist term split evenly between
+// +-nphi/2 and zero padding for m > nphi/2 (the `shift` table folds 1/nphi,
+// the phase and the Nyquist factor together).  Output row r of Y holds the
+// coefficients m = 0..p of latitude node r (r = ring index + 1).
+#include "plan.h"
+
+namespace hpx {
+
+template <class T>
+__global__ void __launch_bounds__(256) ring_fft_kernel(
+    const T* __restrict__ maps, cplx<T>* __restrict__ Y, const int* __restrict__ nphi_t,
+    const int* __restrict__ startN_t, const int* __restrict__ startS_t,
+    const int* __restrict__ pow2_t, const int* __restrict__ logn_t, const int* __restrict__ fftL_t,
+    const int* __restrict__ logL_t, const int64_t* __restrict__ shOff_t,
+    const int64_t* __restrict__ chOff_t, const int64_t* __restrict__ bhOff_t,
+    const cplx<T>* __restrict__ shift, const cplx<T>* __restrict__ chirp,
+    const cplx<T>* __restrict__ bhat, const cplx<T>* __restrict__ tw, int twlen, int p, int Q,
+    int64_t npix, int npairs) {
+    extern __shared__ unsigned char smem_raw[];
+    cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw);
+    // largest rings first: blockIdx.x = 0 is the equator
+    const int i = npairs - 1 - (int)blockIdx.x;
+    const int b = blockIdx.y;
+    const int n = nphi_t[i];
+    const int sN = startN_t[i], sS = startS_t[i];
+    const bool equator = (sN == sS);
+    const T* f = maps + (int64_t)b * npix;
+    const int tid = threadIdx.x, nt = blockDim.x;
+
+    if (pow2_t[i]) {
+        for (int k = tid; k < n; k += nt) buf[k] = mk<T>(f[sN + k], equator ? T(0) : f[sS + k]);
+        __syncthreads();
+        block_fft(buf, n, logn_t[i], tw, twlen, false);
+    } else {
+        const int L = fftL_t[i];
+        const cplx<T>* ch = chirp + chOff_t[i];
+        const cplx<T>* bh = bhat + bhOff_t[i];
+        for (int k = tid; k < L; k += nt) {
+            cplx<T> v = mk<T>(T(0), T(0));
+            if (k < n) v = mul(mk<T>(f[sN + k], equator ? T(0) : f[sS + k]), ch[k]);
+            buf[k] = v;
+        }
+        __syncthreads();
+        block_fft(buf, L, logL_t[i], tw, twlen, false);
+        for (int k = tid; k < L; k += nt) buf[k] = mul(buf[k], bh[k]);
+        __syncthreads();
+        block_fft(buf, L, logL_t[i], tw, twlen, true);
+        for (int k = tid; k < n; k += nt) buf[k] = mul(buf[k], ch[k]);
+        __syncthreads();
+    }
+
+    const int h = n >> 1;
+    const cplx<T>* ph = shift + shOff_t[i];
+    cplx<T>* rowN = Y + ((int64_t)b * Q + (i + 1)) * (p + 1);
+    cplx<T>* rowS = Y + ((int64_t)b * Q + (Q - 2 - i)) * (p + 1);
+    for (int m = tid; m <= p; m += nt) {
+        cplx<T> cN = mk<T>(T(0), T(0)), cS = cN;
+        if (m <= h) {
+            const cplx<T> zm = buf[m];
+            const cplx<T> zc = conjg(buf[m == 0 ? 0 : n - m]);
+            const cplx<T> fn = scale(add(zm, zc), T(0.5));              // n * c~_m (north)
+            const cplx<T> d = sub(zm, zc);
+            const cplx<T> fs = mk<T>(T(0.5) * d.i, T(-0.5) * d.r);      // n * c~_m (south)
+            const cplx<T> w = ph[m];
+            cN = mul(fn, w);
+            cS = mul(fs, w);
+        }
+        rowN[m] = cN;
+        if (!equator) rowS[m] = cS;
+    }
+}
+
+// Pole values (Sec. 3.2.1): a fixed linear functional of the samples of the
+// three rings nearest each pole (unit-weight quadratic least squares in the
+// tangent plane, built at plan time).  Row 0 / row Q-1 of Y: the value at
+// m = 0, zero for m > 0.
+template <class T>
+__global__ void pole_kernel(const T* __restrict__ maps, cplx<T>* __restrict__ Y,
+                            const int* __restrict__ poleN, const int* __restrict__ poleS,
+                            const double* __restrict__ w, int npole, int p, int Q, int64_t npix) {
+    const int b = blockIdx.x;
+    const T* f = maps + (int64_t)b * npix;
+    __shared__ double red[2][32];
+    double sn = 0.0, ss = 0.0;
+    for (int k = threadIdx.x; k < npole; k += blockDim.x) {
+        sn += w[k] * (double)f[poleN[k]];
+        ss += w[k] * (double)f[poleS[k]];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        sn += __shfl_down_sync(0xffffffffu, sn, o);
+        ss += __shfl_down_sync(0xffffffffu, ss, o);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) { red[0][warp] = sn; red[1][warp] = ss; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, c = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) { a += red[0][k]; c += red[1][k]; }
+        red[0][0] = a;
+        red[1][0] = c;
+    }
+    __syncthreads();
+    cplx<T>* rowN = Y + (int64_t)b * Q * (p + 1);
+    cplx<T>* rowS = rowN + (int64_t)(Q - 1) * (p + 1);
+    for (int m = threadIdx.x; m <= p; m += blockDim.x) {
+        rowN[m] = mk<T>(m == 0 ? (T)red[0][0] : T(0), T(0));
+        rowS[m] = mk<T>(m == 0 ? (T)red[1][0] : T(0), T(0));
+    }
+}
+
+template <class T>
+void launch_ring_fft(const hpx_plan_s* P, const T* maps, cudaStream_t s) {
+    const auto& g = P->g;
+    const auto& t = P->t;
+    const size_t smem = (size_t)g.smem_ring * sizeof(cplx<T>);
+    cudaFuncSetAttribute(ring_fft_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    dim3 grid(g.npairs, g.B);
+    ring_fft_kernel<T><<<grid, 256, smem, s>>>(
+        maps, (cplx<T>*)P->Y, t.nphi, t.startN, t.startS, t.pow2, t.logn, t.fftL, t.logL, t.shOff,
+        t.chOff, t.bhOff, (const cplx<T>*)t.shift, (const cplx<T>*)t.chirp, (const cplx<T>*)t.bhat,
+        (const cplx<T>*)t.twid, g.Lmax, g.p, g.Q, g.npix, g.npairs);
+}
+
+template <class T>
+void launch_poles(const hpx_plan_s* P, const T* maps, cudaStream_t s) {
+    const auto& g = P->g;
+    pole_kernel<T><<<g.B, 128, 0, s>>>(maps, (cplx<T>*)P->Y, P->t.poleN, P->t.poleS, P->t.polew,
+                                       P->t.npole, g.p, g.Q, g.npix);
+}
+
+template void launch_ring_fft<float>(const hpx_plan_s*, const float*, cudaStream_t);
+template void launch_ring_fft<double>(const hpx_plan_s*, const double*, cudaStream_t);
+template void launch_poles<float>(const hpx_plan_s*, const float*, cudaStream_t);
+template void launch_poles<double>(const hpx_plan_s*, const double*, cudaStream_t);
+
+}  // namespace hpx

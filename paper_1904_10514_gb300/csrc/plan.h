@@ -1,0 +1,65 @@
+// Internal plan object of the HP2SPH library and the kernel launchers.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "common.cuh"
+
+struct hpx_plan_s;
+
+namespace hpx {
+
+// Device copies of the set-up tables (element type T = plan precision where
+// marked "T"; FP64-built on the host and rounded once).
+struct DevTables {
+    int *nphi = nullptr, *startN = nullptr, *startS = nullptr, *pow2 = nullptr, *logn = nullptr,
+        *fftL = nullptr, *logL = nullptr;
+    int64_t *shOff = nullptr, *chOff = nullptr, *bhOff = nullptr;
+    void *shift = nullptr, *chirp = nullptr, *bhat = nullptr, *twid = nullptr;   // cplx<T>
+    int *poleN = nullptr, *poleS = nullptr;
+    double* polew = nullptr;
+    int npole = 0;
+    int *rowptr = nullptr, *ent = nullptr;
+    void *entw = nullptr, *dec = nullptr;   // T
+    void* D = nullptr;                      // T [2][2][P2][P2]
+    int64_t* angOff = nullptr;
+    void* ang = nullptr;                    // cplx<T> (cos, sin)
+};
+
+struct Geometry {
+    int ns, p, L, Q, npairs, M, P2, Lmax, smem_ring, B;
+    int64_t npix, nalm;
+};
+
+}  // namespace hpx
+
+struct hpx_plan_s {
+    hpx::Geometry g;
+    int precision;
+    int device;
+    cudaStream_t stream;
+    hpx::DevTables t;
+    // workspace
+    void* Y = nullptr;      // cplx<T> [B][Q][p+1]: step-1 ring coefficients per latitude node
+    void* bvec = nullptr;   // cplx<T> [B][p+1][2][P2]: latitude NUFFT right-hand sides
+    void* beta = nullptr;   // cplx<T> [B][p+1][2][P2]: order-0/1 Legendre coefficients (aliases Y)
+    int64_t bytes = 0;
+    int status = 0;
+    // profiling: events around the kernels of each recorded hpx_analyze call
+    static constexpr int kMaxProf = 256;
+    static constexpr int kStages = 5;
+    bool prof = false;
+    int nprof = 0;
+    cudaEvent_t* ev = nullptr;   // [kMaxProf][kStages + 1]
+};
+
+namespace hpx {
+
+template <class T> void launch_ring_fft(const hpx_plan_s* P, const T* maps, cudaStream_t s);
+template <class T> void launch_poles(const hpx_plan_s* P, const T* maps, cudaStream_t s);
+template <class T> void launch_nufft(const hpx_plan_s* P, cudaStream_t s);
+template <class T> void launch_dense(const hpx_plan_s* P, cudaStream_t s);
+template <class T> void launch_rot(const hpx_plan_s* P, T* alm, cudaStream_t s);
+template <class T> void launch_cl(const hpx_plan_s* P, const T* alm, double* cl, cudaStream_t s);
+
+}  // namespace hpx

@@ -1,0 +1,61 @@
+// Host-side (FP64) set-up of the HP2SPH plan tables.  Everything here runs once
+// per plan; the per-map work is in the CUDA kernels.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace hpx {
+
+struct PlanTables {
+    int ns = 0;      // N_side
+    int p = 0;       // 2 N_side: longitude/latitude half-bandwidth
+    int L = 0;       // lmax <= p
+    int Q = 0;       // 4 N_side + 1 latitude nodes on [0, pi] (poles included)
+    int npairs = 0;  // 2 N_side north/south ring pairs (the equator pairs with itself)
+    int64_t npix = 0;
+
+    // ---- Step 1 (Sec. 3.1): per ring pair i (north ring i, south ring 4Ns-2-i)
+    std::vector<int> nphi, startN, startS, pow2, logn, fftL, logL;
+    std::vector<int64_t> shOff, chOff, bhOff;
+    std::vector<double> shift;   // complex: (1/nphi) e^{-i m phi0}, Nyquist split folded in
+    std::vector<double> chirp;   // complex: e^{-i pi k^2 / nphi} (Bluestein rings)
+    std::vector<double> bhat;    // complex: FFT_L of the conjugate chirp, divided by L
+    int Lmax = 0;                // twiddle table covers FFT lengths up to Lmax
+    std::vector<double> twid;    // complex: e^{-2 pi i k / Lmax}, k < Lmax/2
+    int smem_ring = 0;           // largest in-CTA FFT length of step 1
+
+    // ---- pole values (Sec. 3.2.1)
+    std::vector<double> polew;   // weights over the pixels of the 3 rings nearest a pole
+    std::vector<int> poleN, poleS;  // pixel indices (north / mirrored south)
+
+    // ---- DFS + type-1 NUFFT in latitude (Sec. 3.2.1-3.2.2)
+    int M = 0;                   // fine grid size 8 N_side
+    int esw = 0;                 // exponential-of-semicircle kernel width (grid cells)
+    std::vector<int> rowptr;     // CSR over fine-grid points
+    std::vector<int> ent;        // node index r | (mirrored << 30)
+    std::vector<double> entw;    // kernel weight
+    std::vector<double> dec;     // h / Phi(j), j = 0..p (deconvolution)
+
+    // ---- latitude least squares + Chebyshev -> order-0/1 Legendre (Sec. 3.2.2, 3.3)
+    int P2 = 0;                  // p/2 + 1
+    std::vector<double> D;       // [mpar][par][P2][P2], rows q -> l = 2q+par, cols k -> j = 2k+par
+
+    // ---- Givens rotations of the order m' -> m'+2 connection (Sec. 3.3)
+    std::vector<int64_t> angOff; // [(L+1) * 2]: offset of (m', chain c)
+    std::vector<double> ang;     // (cos, sin) pairs
+};
+
+// Build all tables; returns an empty string on success or a message.
+std::string build_tables(int nside, int lmax, bool fp64, PlanTables& t);
+
+// Gauss-Legendre nodes/weights on [-1, 1] (Newton on the Legendre recurrence).
+void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w);
+
+// Chain length of order m', parity chain c (degrees m'+c+2i <= L).
+#if defined(__CUDACC__)
+__host__ __device__
+#endif
+inline int chain_len(int mp, int c, int L) { return (L >= mp + c) ? (L - mp - c) / 2 + 1 : 0; }
+
+}  // namespace hpx

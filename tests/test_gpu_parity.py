@@ -1,0 +1,138 @@
+"""Parity of the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances (per-degree relative l2 error e_l, see helpers.per_l_error):
+FP64 plans 1e-11, FP32 plans 1e-5 -- the accuracy targets of the method's
+FP64 and FP32 forms.  Inputs are seeded skies from `skies`."""
+
+import numpy as np
+import pytest
+
+import skies
+from helpers import per_l_error, per_l_norms, sampled_per_l_error
+from oracle import hp2sph
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-11, "fp32": 1e-5}
+
+
+@pytest.fixture(scope="module")
+def hp():
+    import os
+    import paper_1904_10514_gb300 as hp
+    if not os.path.exists(hp.LIB_PATH):
+        hp.build()
+    assert torch.cuda.is_available()
+    return hp
+
+
+def _run(hp, maps, nside, lmax, prec):
+    B = maps.shape[0]
+    plan = hp.Plan(nside, lmax, B, prec)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    x = torch.as_tensor(maps, dtype=dt, device="cuda")
+    alm = plan.analyze(x)
+    cl = plan.cl(alm)
+    plan.sync()
+    return alm.cpu().numpy().astype(np.complex128), cl.cpu().numpy(), plan
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("nside,lmax", [(2, 4), (4, 8), (4, 5), (8, 16), (16, 32), (16, 29), (32, 64), (64, 128)])
+def test_parity_full(hp, prec, nside, lmax):
+    maps, _ = skies.small_powerlaw_maps(nside, 3, seed=100 + nside, alpha=2.0, noise=1e-3, lmax=2 * nside)
+    if prec == "fp32":
+        maps = maps.astype(np.float32).astype(np.float64)   # the oracle sees the same inputs
+    a, cl, _ = _run(hp, maps, nside, lmax, prec)
+    ref = hp2sph.analyze(maps, nside, lmax)
+    for b in range(maps.shape[0]):
+        e = per_l_error(a[b], ref[b], lmax)
+        assert e.max() < TOL[prec], (b, e.max(), int(np.argmax(e)))
+        clr = hp2sph.cl(ref[b], lmax)
+        rel = np.abs(cl[b] - clr) / np.maximum(clr, 1e-300)
+        assert rel[2:].max() < 2.5 * TOL[prec], rel.max()
+
+
+def test_workload1_nside16_fp64(hp):
+    maps = skies.workload_maps("w1_nside16")
+    a, cl, _ = _run(hp, maps, 16, 32, "fp64")
+    ref = hp2sph.analyze(maps, 16, 32)
+    assert per_l_error(a[0], ref[0], 32).max() < TOL["fp64"]
+
+
+def test_zero_and_constant_maps(hp):
+    ns = 8
+    z = np.zeros((2, 12 * ns * ns))
+    z[1] = 3.5
+    a, cl, _ = _run(hp, z, ns, 16, "fp64")
+    assert np.all(a[0] == 0)
+    ref = hp2sph.analyze(z[1], ns, 16)
+    np.testing.assert_allclose(a[1], ref, atol=1e-12)
+    assert abs(a[1][0] - 3.5 * np.sqrt(4 * np.pi)) < 1e-12
+
+
+def test_batch_position_independent(hp):
+    """A map gives bit-identical coefficients wherever it sits in a batch."""
+    ns = 16
+    maps, _ = skies.small_powerlaw_maps(ns, 5, seed=9)
+    a5, _, _ = _run(hp, maps.astype(np.float32), ns, 32, "fp32")
+    a1, _, _ = _run(hp, maps[3:4].astype(np.float32), ns, 32, "fp32")
+    assert np.array_equal(a5[3], a1[0])
+
+
+def test_lmax_zero(hp):
+    ns = 4
+    maps, _ = skies.small_powerlaw_maps(ns, 1, seed=2)
+    a, cl, _ = _run(hp, maps, ns, 0, "fp64")
+    ref = hp2sph.analyze(maps, ns, 0)
+    np.testing.assert_allclose(a, ref, atol=1e-13)
+
+
+_W2 = {}
+
+
+def _w2_reference(prec):
+    """Oracle coefficients (all orders) of the Nside-256 sky, computed once per
+    input precision."""
+    if prec not in _W2:
+        maps, alms = skies.workload_maps("w2_nside256", return_alm=True)
+        if prec == "fp32":
+            maps = maps.astype(np.float32).astype(np.float64)
+        _W2[prec] = (maps, hp2sph.analyze(maps, 256, 512))
+    return _W2[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_workload2_nside256(hp, prec):
+    """Nside 256, lmax 512, FP64 and FP32 side by side; every degree."""
+    maps, ref = _w2_reference(prec)
+    a, cl, _ = _run(hp, maps, 256, 512, prec)
+    e = per_l_error(a[0], ref[0], 512)
+    assert e.max() < TOL[prec], (e.max(), int(np.argmax(e)))
+    clr = hp2sph.cl(ref[0], 512)
+    assert (np.abs(cl[0] - clr) / clr)[2:].max() < 2.5 * TOL[prec]
+
+
+@pytest.mark.slow
+def test_bench_workload_sampled(hp):
+    """The benchmark's workload (32 FP32 maps, Nside 1024, lmax 2048) in the
+    launch configuration the benchmark times; the oracle checks maps 0 and 31
+    on a sample of orders."""
+    maps, alms = skies.workload_maps("bench_nside1024x32", dtype=np.float32, return_alm=True)
+    a, _, _ = _run(hp, maps, 1024, 2048, "fp32")
+    L = 2048
+    strat = [int((k + 0.5) * (L + 1) / 12) for k in range(12)]     # uniform over orders
+    low = [0, 1, 2, L - 1, L]
+    for b in (0, 31):
+        ref = hp2sph.analyze_columns(maps[b].astype(np.float64), 1024, L, strat + low)
+        got = {m: a[b][hp2sph.alm_index(m, m, L):hp2sph.alm_index(m, m, L) + L - m + 1] for m in strat + low}
+        norms = per_l_norms(alms[b], L)
+        # e_l estimated from a uniform sample of orders
+        err = sampled_per_l_error({m: got[m] for m in strat}, {m: ref[m][0] for m in strat}, norms, L)
+        assert err < TOL["fp32"], (b, err)
+        # single elements of the edge orders: |da_lm| <= tol ||a_l|| is necessary for e_l <= tol
+        for m in low:
+            l = np.arange(m, L + 1)
+            d = np.abs(got[m] - ref[m][0]) / norms[l]
+            assert d[l >= 2].max() < TOL["fp32"], (b, m, d.max())
