@@ -117,6 +117,30 @@ int64_t hpx_plan_bytes(const hpx_plan_s* plan);
 int hpx_set_profiling(hpx_plan_s* plan, int enable);
 int hpx_stage_times(hpx_plan_s* plan, float* ms, int n, int* ncalls);
 
+/* Allocation-free analysis of ONE real FP32 map (the paper has no counterpart;
+ * this is a service for callers, not a step of the method).
+ *
+ * For callers that cannot call cudaMalloc: code running while someone else is
+ * capturing the stream into a CUDA graph, plugins whose device memory belongs to
+ * a host application's pool, real-time or embedded code that must not allocate
+ * after start-up.  It computes the same coefficients as a one-map FP32
+ * hpx_analyze plan, but every table and every intermediate buffer lives in one
+ * fixed device array inside the library (8 MiB, reserved on every GPU that loads
+ * the library until the process exits), so it needs no plan and allocates no
+ * device memory.  The caller still passes the input and output buffers:
+ *   maps : device float[12 nside^2] (RING order), alm : device float[n_alm][2].
+ * Limits: 2 <= nside <= HPX_NOALLOC_MAX_NSIDE (power of two), -1 <= lmax <= 2 nside
+ * (-1 = 2 nside); larger sizes return HPX_ERR_NSIDE / HPX_ERR_LMAX.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call before
+ * any stream capture.  A call whose nside/lmax differ from the previous call's on
+ * the same device rebuilds the tables on the host and copies them into the array
+ * (synchronising `cuda_stream`).  All calls share the array and it keeps the
+ * last call's contents, so calls that overlap on the GPU (different streams or
+ * threads) race; serialise them.  Asynchronous on `cuda_stream` otherwise. */
+#define HPX_NOALLOC_MAX_NSIDE 128
+int hpx_analyze_noalloc(int nside, int lmax, const float* maps, float* alm, void* cuda_stream);
+
 /* Last error code of the calling thread and its message. */
 int hpx_last_error(void);
 const char* hpx_strerror(int code);

@@ -31,7 +31,9 @@ HPX_FP64 = 1
 
 EXPORTS = ["hpx_plan", "hpx_plan_ex", "hpx_set_stream", "hpx_analyze", "hpx_synthesize", "hpx_cl",
            "hpx_sync", "hpx_destroy", "hpx_npix", "hpx_nalm", "hpx_plan_lmax", "hpx_plan_bytes",
-           "hpx_last_error", "hpx_strerror", "hpx_set_profiling", "hpx_stage_times"]
+           "hpx_last_error", "hpx_strerror", "hpx_set_profiling", "hpx_stage_times",
+           "hpx_analyze_noalloc"]
+HPX_NOALLOC_MAX_NSIDE = 128
 HPX_NSTAGES = 5
 STAGES = ["ring_fft", "poles", "nufft", "lat_solve", "rot_sweep"]
 
@@ -80,6 +82,7 @@ def lib():
             "hpx_last_error": (i32, []),
             "hpx_strerror": (ctypes.c_char_p, [i32]),
             "hpx_set_profiling": (i32, [vp, i32]),
+            "hpx_analyze_noalloc": (i32, [i32, i32, vp, vp, vp]),
             "hpx_stage_times": (i32, [vp, ctypes.POINTER(ctypes.c_float), i32, ctypes.POINTER(ctypes.c_int)]),
         }
         for name, (res, args) in sig.items():
@@ -126,6 +129,11 @@ def hpx_sync(plan):
 
 def hpx_destroy(plan):
     lib().hpx_destroy(plan)
+
+
+def hpx_analyze_noalloc(nside, lmax, maps_ptr, alm_ptr, stream):
+    """Allocation-free one-map FP32 analysis (see include/hpx.h)."""
+    return lib().hpx_analyze_noalloc(int(nside), int(lmax), maps_ptr, alm_ptr, stream)
 
 
 def hpx_set_profiling(plan, enable):

@@ -82,6 +82,8 @@ int analyze_impl(hpx_plan_s* P, const void* maps, void* alm) {
 
 }  // namespace
 
+int hpx_internal_set_error(int code) { return set_err(code); }
+
 extern "C" {
 
 hpx_plan_s* hpx_plan_ex(const hpx_plan_desc* d) {
