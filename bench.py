@@ -174,6 +174,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle leg")
+    ap.add_argument("--kernels-only", action="store_true",
+                    help="time only the device-resident step (for profiler runs): no e2e, FP64 or CPU legs")
+    ap.add_argument("--nside", type=int, default=NSIDE, help="smaller cases for profiler captures")
+    ap.add_argument("--batch", type=int, default=BATCH)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -199,11 +203,15 @@ def main():
         if world > 1:
             dist.barrier()
 
-    maps_np = skies.workload_maps(WORKLOAD, nmaps=BATCH, first=rank * BATCH, dtype=np.float32)
-    plan = hp.Plan(NSIDE, LMAX, BATCH, "fp32")
+    ns, nb = args.nside, args.batch
+    if ns == NSIDE:
+        maps_np = skies.workload_maps(WORKLOAD, nmaps=nb, first=rank * nb, dtype=np.float32)
+    else:
+        maps_np = skies.small_powerlaw_maps(ns, nb, seed=6000 + rank, alpha=2.0, noise=1e-3)[0].astype(np.float32)
+    plan = hp.Plan(ns, 2 * ns, nb, "fp32")
     maps = torch.from_numpy(maps_np).cuda()
-    alm = torch.empty((BATCH, plan.nalm), dtype=torch.complex64, device="cuda")
-    cl = torch.empty((BATCH, LMAX + 1), dtype=torch.float64, device="cuda")
+    alm = torch.empty((nb, plan.nalm), dtype=torch.complex64, device="cuda")
+    cl = torch.empty((nb, plan.lmax + 1), dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream()
 
     def step():
@@ -234,13 +242,21 @@ def main():
         tt = torch.tensor([t_step], device="cuda", dtype=torch.float64)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         t_step = float(tt.item())
-    npix_step = BATCH * plan.npix
+    npix_step = nb * plan.npix
     value = world * npix_step / t_step / 1e9
+    if args.kernels_only:
+        if rank == 0:
+            per_launch = {n: stage_ms[k] / max(ncalls, 1) for k, n in enumerate(hp.STAGES)}
+            print(json.dumps({"nside": ns, "batch": nb, "value": value, "unit": "Gpix/s",
+                              "ms_per_step": t_step * 1e3, "stages_ms_per_launch": per_launch}), flush=True)
+        if world > 1:
+            dist.destroy_process_group()
+        return
 
     # end to end through the public API from pinned host memory
     host_maps = torch.from_numpy(maps_np).pin_memory()
-    host_alm = torch.empty((BATCH, plan.nalm), dtype=torch.complex64).pin_memory()
-    host_cl = torch.empty((BATCH, LMAX + 1), dtype=torch.float64).pin_memory()
+    host_alm = torch.empty((nb, plan.nalm), dtype=torch.complex64).pin_memory()
+    host_cl = torch.empty((nb, plan.lmax + 1), dtype=torch.float64).pin_memory()
 
     def e2e_step():
         maps.copy_(host_maps, non_blocking=True)

@@ -236,3 +236,71 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+# ------------------------------------------------------------ autograd
+def _torch_functions():
+    import torch
+
+    class AnalyzeFn(torch.autograd.Function):
+        """alm = A maps; the backward pass is the library's adjoint (hpx_synthesize).
+
+        torch hands the backward pass g = dL/dRe(a) + i dL/dIm(a).  The map gradient
+        is sum_lm Re(A[lm, i] conj(g_lm)), i.e. the transpose with unit weights;
+        hpx_synthesize weights m > 0 by 2, so those entries are halved first."""
+
+        @staticmethod
+        def forward(ctx, maps, plan):
+            ctx.plan = plan
+            return plan.analyze(maps)
+
+        @staticmethod
+        def backward(ctx, g):
+            plan = ctx.plan
+            g = g.contiguous().clone()
+            g[:, plan.lmax + 1:] *= 0.5
+            return plan.synthesize(g), None
+
+    class ClFn(torch.autograd.Function):
+        """C_l of Eq. (APS) (hpx_cl); backward dL/da_lm = dL/dC_l * 2 w_m a_lm / (2l+1)."""
+
+        @staticmethod
+        def forward(ctx, alm, plan):
+            ctx.plan = plan
+            ctx.save_for_backward(alm)
+            return plan.cl(alm)
+
+        @staticmethod
+        def backward(ctx, gcl):
+            (alm,) = ctx.saved_tensors
+            plan = ctx.plan
+            l_idx, w_idx = plan.index_tables()
+            scale = gcl[:, l_idx] * (2.0 * w_idx / (2.0 * l_idx.to(gcl.dtype) + 1.0))
+            return alm * scale.to(alm.real.dtype), None
+
+    return AnalyzeFn, ClFn
+
+
+def analyze(maps, plan):
+    """Differentiable analysis (torch.autograd) through the C ABI."""
+    return _torch_functions()[0].apply(maps, plan)
+
+
+def cl(alm, plan):
+    """Differentiable C_l (torch.autograd) through the C ABI."""
+    return _torch_functions()[1].apply(alm, plan)
+
+
+def _index_tables(self):
+    """(l, weight) of every packed coefficient, on the plan's device (cached)."""
+    if getattr(self, "_idx", None) is None:
+        t = self.torch
+        L = self.lmax
+        m = t.cat([t.full((L + 1 - k,), k, dtype=t.int64) for k in range(L + 1)])
+        l = t.cat([t.arange(k, L + 1, dtype=t.int64) for k in range(L + 1)])
+        w = t.where(m == 0, 1.0, 2.0).to(t.float64)
+        self._idx = (l.to(self.device), w.to(self.device))
+    return self._idx
+
+
+Plan.index_tables = _index_tables

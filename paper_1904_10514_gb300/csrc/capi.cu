@@ -50,7 +50,7 @@ void free_plan(hpx_plan_s* P) {
     auto& t = P->t;
     void* ptrs[] = {t.nphi, t.startN, t.startS, t.pow2, t.logn, t.fftL, t.logL, t.shOff, t.chOff,
                     t.bhOff, t.shift, t.chirp, t.bhat, t.twid, t.poleN, t.poleS, t.polew, t.rowptr,
-                    t.ent, t.entw, t.dec, t.D, t.angOff, t.ang, P->Y, P->bvec};
+                    t.ent, t.entw, t.dec, t.D, t.angOff, t.ang, t.skOff, t.skew, t.skewT, t.nrowptr, t.nent, t.nentw, P->Y, P->bvec};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     if (P->ev) {
@@ -133,6 +133,9 @@ hpx_plan_s* hpx_plan_ex(const hpx_plan_desc* d) {
     t.entw = up.real(tb.entw, fp64); t.dec = up.real(tb.dec, fp64);
     t.D = up.real(tb.D, fp64);
     t.angOff = up.vec(tb.angOff); t.ang = up.real(tb.ang, fp64);
+    t.skOff = up.vec(tb.skOff); t.skew = up.real(tb.skew, fp64); t.nq = tb.nq;
+    t.skewT = up.real(tb.skewT, fp64);
+    t.nrowptr = up.vec(tb.nrowptr); t.nent = up.vec(tb.nent); t.nentw = up.real(tb.nentw, fp64);
     if (!up.ok) { free_plan(P); set_err(HPX_ERR_OOM); return nullptr; }
 
     const size_t es = fp64 ? 16 : 8;   // complex element
@@ -172,7 +175,10 @@ int hpx_analyze(hpx_plan_s* P, const void* maps, void* alm) {
 
 int hpx_synthesize(hpx_plan_s* P, const void* alm, void* maps) {
     if (!P || !alm || !maps) return set_err(HPX_ERR_ARG);
-    return set_err(HPX_ERR_STATE);
+    if (P->precision == HPX_FP64) hpx::launch_adjoint<double>(P, (const double*)alm, (double*)maps, P->stream);
+    else hpx::launch_adjoint<float>(P, (const float*)alm, (float*)maps, P->stream);
+    if (cudaGetLastError() != cudaSuccess) return set_err(HPX_ERR_CUDA);
+    return set_err(HPX_OK);
 }
 
 int hpx_set_profiling(hpx_plan_s* P, int enable) {

@@ -8,7 +8,9 @@
 // (m odd), scaled by sqrt(2 pi).  Both maps are fixed and shared by all columns
 // and maps, so the plan premultiplies them (FP64) into one dense operator per
 // (parity of m, parity of l):  beta = D b.  This kernel is that multi-column
-// contraction:  beta[b][m][par][q] = sum_k D[m&1][par][q][k] * bvec[b][m][par][k].
+// contraction:  beta[m][par][q][b][re/im] = sum_k D[m&1][par][q][k] * bvec[b][m][par][k].
+// The output is column-contiguous (all maps of one (m, par, q) side by side) for
+// the rotation sweeps, which process one real column per lane.
 #include "plan.h"
 
 namespace hpx {
@@ -51,7 +53,7 @@ __global__ void __launch_bounds__(256) dense_kernel(const T* __restrict__ D,
             const int col = c0 + cc, k = k0 + kk;
             cplx<T> v = mk<T>(T(0), T(0));
             if (col < ncols && k < P2) {
-                const int b = col / nmp, mi = col % nmp;
+                const int b = col % B, mi = col / B;
                 const int m = 2 * mi + mpar;
                 v = bvec[(((int64_t)b * (p + 1) + m) * 2 + par) * P2 + k];
             }
@@ -80,13 +82,12 @@ __global__ void __launch_bounds__(256) dense_kernel(const T* __restrict__ D,
     for (int c = 0; c < 2; ++c) {
         const int col = c0 + ty * 2 + c;
         if (col >= ncols) continue;
-        const int b = col / nmp, mi = col % nmp;
+        const int b = col % B, mi = col / B;
         const int m = 2 * mi + mpar;
-        cplx<T>* out = beta + (((int64_t)b * (p + 1) + m) * 2 + par) * P2;
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
             const int q = q0 + tx * 4 + r;
-            if (q < P2) out[q] = mk<T>(accr[r][c], acci[r][c]);
+            if (q < P2) beta[(((int64_t)m * 2 + par) * P2 + q) * B + b] = mk<T>(accr[r][c], acci[r][c]);
         }
     }
 }

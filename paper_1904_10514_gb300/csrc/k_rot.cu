@@ -12,20 +12,134 @@
 // span).  The angles are FP64-built at plan time from the QR factorisation of
 // the tridiagonal multiplication-by-sin^2 operator.
 //
-// Kernel layout: one block per (m, group of G maps), one warp per parity chain.
-// Lane s of a warp applies stage s0 + s of the current pass of 32 stages; the
-// chain streams through the lanes as a wavefront (lane s runs two steps behind
-// lane s - 1) and each rotated value is handed to the next stage with a warp
-// shuffle.  Lane 0 reads the chain from shared memory and the last lane writes
-// the pass's output chain back in place.  Each lane carries 2G real values
-// (re, im of G maps) that share one angle load.
+// Kernel layout.  One warp per (m, parity chain c, group of 32 real columns),
+// one lane per real column (re or im of one map).  A pass applies K consecutive
+// sweeps at once as a wavefront held in registers: at time step t, stage k
+// performs its rotation i = t - 2k, reading the value stage k-1 produced at the
+// previous step, so the K rotations of a step are independent (ILP = K) and
+// no data crosses lanes.  Stage 0 reads the chain from global memory (one
+// coalesced 128-byte row per step); the last stage writes its output back in
+// place (output index < input index, same lane).  The K angles of a step are
+// the same for all lanes and come from a pre-skewed table (idle slots hold the
+// rotation (1, 0), which only moves the input into the carry), so the inner
+// loop has no branches.  m/2 sweeps take passes of 32 stages and then
+// 16, 8, 4, 2, 1.
 #include "plan.h"
 #include "plan_math.h"
 
 namespace hpx {
 
+// Angles of stages k and k+1 of one skewed row (adjacent pairs; 16-byte
+// aligned for even k, which holds for every pass of two or more stages).
+template <class T>
+__device__ __forceinline__ void load2(const cplx<T>* p, cplx<T>& a, cplx<T>& b) {
+    if constexpr (sizeof(T) == 4) {
+        const float4 v = *reinterpret_cast<const float4*>(p);
+        a = mk<T>(v.x, v.y);
+        b = mk<T>(v.z, v.w);
+    } else {
+        a = p[0];
+        b = p[1];
+    }
+}
+
+// One pass of K sweeps over a chain of `n` complex elements chain[i * ldc]
+// (the real and imaginary parts share each rotation).  `A` points at row 0 of
+// the skewed block, `coff` is the column of stage 0.
+template <class T, int K>
+__device__ __forceinline__ void sweep_pass(cplx<T>* chain, int64_t ldc, int n, const cplx<T>* __restrict__ A,
+                                           int coff) {
+    cplx<T> carry[K], pipe[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) { carry[k] = mk<T>(T(0), T(0)); pipe[k] = carry[k]; }
+    const int steps = n + 2 * (K - 1);
+    const int nout = n - K;   // outputs of the last stage
+    for (int t = 0; t < steps; ++t) {
+        const cplx<T> x0 = (t < n) ? chain[(int64_t)t * ldc] : mk<T>(T(0), T(0));
+        const cplx<T>* row = A + (int64_t)t * 32 + coff;
+        cplx<T> cs[K];
+        if constexpr (K == 1) {
+            cs[0] = row[0];
+        } else {
+#pragma unroll
+            for (int k = 0; k < K; k += 2) load2(row + k, cs[k], cs[k + 1]);
+        }
+#pragma unroll
+        for (int k = K - 1; k >= 0; --k) {
+            const cplx<T> x = (k == 0) ? x0 : pipe[k - 1];
+            const T c = cs[k].r, s = cs[k].i;
+            pipe[k] = mk<T>(c * carry[k].r + s * x.r, c * carry[k].i + s * x.i);
+            carry[k] = mk<T>(c * x.r - s * carry[k].r, c * x.i - s * carry[k].i);
+        }
+        const int j = t - 2 * K + 1;
+        if (j >= 0 && j < nout) chain[(int64_t)j * ldc] = pipe[K - 1];
+    }
+}
+
+template <class T, int KMAX>
+__global__ void __launch_bounds__(64) rot_kernel(cplx<T>* __restrict__ beta2, cplx<T>* __restrict__ alm,
+                                                  const int64_t* __restrict__ skOff,
+                                                  const cplx<T>* __restrict__ skew, int nq, int P2, int L,
+                                                  int B, int64_t nalm, int ngroups, int nitems) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp >= nitems) return;
+    // heaviest orders first: item -> (m descending, chain, column group)
+    const int g = warp % ngroups;
+    const int c = (warp / ngroups) & 1;
+    const int m = L - warp / (2 * ngroups);
+    const int m0 = m & 1;
+    const int S = (m - m0) >> 1;
+    const int ncol = B;                 // one complex column per map
+    const int col = 32 * g + lane;      // map index
+    const bool live = col < ncol;
+    // chain c of order m0 sits in parity block par at rows q0, q0+1, ...
+    const int par = (m0 + c) & 1;
+    const int q0 = (m0 == 1 && c == 1) ? 1 : 0;
+    cplx<T>* chain = beta2 + (((int64_t)m * 2 + par) * P2 + q0) * ncol + (live ? col : 0);
+    const int64_t ldc = ncol;
+    int n = chain_len(m0, c, L);
+    int s0 = 0;
+    // A pass of K stages starting at stage s0 reads the skewed block of stages
+    // 32*(s0/32).., offset by d = s0 % 32 stages: its time step t is block row
+    // t + 2d and its stage k is block column k + d.
+    auto block = [&](int s) {
+        return skew + (skOff[(size_t)(m0 * 2 + c) * nq + (s >> 5)] + 2 * (s & 31)) * 32;
+    };
+    if (live) {
+        while (S - s0 >= KMAX && n > 0) {
+            sweep_pass<T, KMAX>(chain, ldc, n, block(s0), s0 & 31);
+            n -= KMAX;
+            s0 += KMAX;
+        }
+    }
+    // remaining stages: 16, 8, 4, 2, 1
+#define HPX_SUBPASS(KK)                                                                   \
+    if (KK < KMAX && live && S - s0 >= KK && n > 0) {                                     \
+        sweep_pass<T, KK>(chain, ldc, n, block(s0), s0 & 31);                            \
+        n -= KK;                                                                          \
+        s0 += KK;                                                                         \
+    }
+    HPX_SUBPASS(16)
+    HPX_SUBPASS(8)
+    HPX_SUBPASS(4)
+    HPX_SUBPASS(2)
+    HPX_SUBPASS(1)
+#undef HPX_SUBPASS
+    if (!live) return;
+    // n == chain_len(m, c, L): degrees l = m + c + 2i
+    cplx<T>* out = alm + (int64_t)col * nalm;
+    const int64_t base = (int64_t)m * (2 * L + 1 - m) / 2 + m + c;
+    for (int i = 0; i < n; ++i) out[base + 2 * i] = chain[(int64_t)i * ldc];
+}
+
+// Small batches (fewer than 16 maps) leave most lanes of the kernel above idle;
+// they use this layout instead: one warp per parity chain, lane s applies stage
+// s of a pass of 32 sweeps, the chain streams through the lanes as a wavefront
+// (lane s two steps behind lane s-1, values handed on by warp shuffles), G maps
+// per lane share each angle load.
 template <class T, int G>
-__global__ void __launch_bounds__(64) rot_kernel(const cplx<T>* __restrict__ beta, cplx<T>* __restrict__ alm,
+__global__ void __launch_bounds__(64) rot_stage_kernel(const cplx<T>* __restrict__ beta, cplx<T>* __restrict__ alm,
                                                  const int64_t* __restrict__ angOff,
                                                  const cplx<T>* __restrict__ ang, int p, int P2, int L, int B,
                                                  int64_t nalm, int nmax) {
@@ -46,7 +160,7 @@ __global__ void __launch_bounds__(64) rot_kernel(const cplx<T>* __restrict__ bet
 #pragma unroll
         for (int g = 0; g < G; ++g) {
             cplx<T> v = mk<T>(T(0), T(0));
-            if (b0 + g < B) v = beta[(((int64_t)(b0 + g) * (p + 1) + m) * 2 + par) * P2 + q];
+            if (b0 + g < B) v = beta[(((int64_t)m * 2 + par) * P2 + q) * B + (b0 + g)];
             buf[idx * V + 2 * g] = v.r;
             buf[idx * V + 2 * g + 1] = v.i;
         }
@@ -108,22 +222,24 @@ __global__ void __launch_bounds__(64) rot_kernel(const cplx<T>* __restrict__ bet
 template <class T>
 void launch_rot(const hpx_plan_s* P, T* alm, cudaStream_t s) {
     const auto& g = P->g;
-    const int nmax = g.L / 2 + 1;
-    if (g.B >= 4) {
-        constexpr int G = 4;
-        const size_t smem = (size_t)2 * nmax * 2 * G * sizeof(T);
-        cudaFuncSetAttribute(rot_kernel<T, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        dim3 grid(g.L + 1, (g.B + G - 1) / G);
-        rot_kernel<T, G><<<grid, 64, smem, s>>>((const cplx<T>*)P->beta, (cplx<T>*)alm, P->t.angOff,
-                                                (const cplx<T>*)P->t.ang, g.p, g.P2, g.L, g.B, g.nalm, nmax);
-    } else {
-        constexpr int G = 1;
-        const size_t smem = (size_t)2 * nmax * 2 * G * sizeof(T);
-        cudaFuncSetAttribute(rot_kernel<T, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        dim3 grid(g.L + 1, g.B);
-        rot_kernel<T, G><<<grid, 64, smem, s>>>((const cplx<T>*)P->beta, (cplx<T>*)alm, P->t.angOff,
-                                                (const cplx<T>*)P->t.ang, g.p, g.P2, g.L, g.B, g.nalm, nmax);
+    if (g.B >= 16) {
+        const int ngroups = (g.B + 31) / 32;
+        const int nitems = (g.L + 1) * 2 * ngroups;
+        const int threads = 64;
+        const int blocks = (nitems * 32 + threads - 1) / threads;
+        constexpr int KMAX = sizeof(T) == 4 ? 32 : 16;
+        rot_kernel<T, KMAX><<<blocks, threads, 0, s>>>((cplx<T>*)P->beta, (cplx<T>*)alm, P->t.skOff,
+                                                      (const cplx<T>*)P->t.skew, P->t.nq, g.P2, g.L, g.B,
+                                                      g.nalm, ngroups, nitems);
+        return;
     }
+    const int nmax = g.L / 2 + 1;
+    constexpr int G = 1;
+    const size_t smem = (size_t)2 * nmax * 2 * G * sizeof(T);
+    cudaFuncSetAttribute(rot_stage_kernel<T, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    dim3 grid(g.L + 1, g.B);
+    rot_stage_kernel<T, G><<<grid, 64, smem, s>>>((const cplx<T>*)P->beta, (cplx<T>*)alm, P->t.angOff,
+                                                  (const cplx<T>*)P->t.ang, g.p, g.P2, g.L, g.B, g.nalm, nmax);
 }
 
 template void launch_rot<float>(const hpx_plan_s*, float*, cudaStream_t);

@@ -37,7 +37,7 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Offsets {
     size_t nphi, startN, startS, pow2, logn, fftL, logL, shOff, chOff, bhOff, shift, chirp, bhat, twid,
-        poleN, poleS, polew, rowptr, ent, entw, dec, D, angOff, ang;
+        poleN, poleS, polew, rowptr, ent, entw, dec, D, angOff, ang, skOff, skew;
     size_t Y, bvec;
     int npole;
 };
@@ -45,6 +45,7 @@ struct Offsets {
 struct DevState {
     unsigned char* base = nullptr;   // device address of g_noalloc_scratch
     int nside = -1, lmax = -1;       // size whose tables the array currently holds
+    int nq = 0;
     Offsets off;
     hpx::Geometry geo;
 };
@@ -112,6 +113,7 @@ extern "C" int hpx_analyze_noalloc(int nside, int lmax, const float* maps, float
         o.npole = (int)tb.polew.size();
         o.rowptr = img.vec(tb.rowptr); o.ent = img.vec(tb.ent); o.entw = img.real(tb.entw);
         o.dec = img.real(tb.dec); o.D = img.real(tb.D); o.angOff = img.vec(tb.angOff); o.ang = img.real(tb.ang);
+        o.skOff = img.vec(tb.skOff); o.skew = img.real(tb.skew); st.nq = tb.nq;
         const size_t ySize = (size_t)tb.Q * (tb.p + 1) * 8;    // step-1 coefficients (complex FP32)
         const size_t bSize = (size_t)(tb.p + 1) * 2 * tb.P2 * 8;
         o.Y = align256(img.bytes.size());
@@ -143,6 +145,7 @@ extern "C" int hpx_analyze_noalloc(int nside, int lmax, const float* maps, float
     t.polew = (double*)(b + o.polew); t.npole = o.npole; t.rowptr = (int*)(b + o.rowptr);
     t.ent = (int*)(b + o.ent); t.entw = b + o.entw; t.dec = b + o.dec; t.D = b + o.D;
     t.angOff = (int64_t*)(b + o.angOff); t.ang = b + o.ang;
+    t.skOff = (int64_t*)(b + o.skOff); t.skew = b + o.skew; t.nq = st.nq;
     P.g = st.geo;
     P.precision = HPX_FP32;
     P.device = dev;

@@ -24,6 +24,12 @@ struct DevTables {
     void* D = nullptr;                      // T [2][2][P2][P2]
     int64_t* angOff = nullptr;
     void* ang = nullptr;                    // cplx<T> (cos, sin)
+    int64_t* skOff = nullptr;               // skewed angle blocks for the sweep wavefront
+    void* skew = nullptr;                   // cplx<T>
+    int nq = 0;
+    void* skewT = nullptr;                  // cplx<T>, transposed sweeps
+    int *nrowptr = nullptr, *nent = nullptr;   // NUFFT transpose: CSR over nodes
+    void* nentw = nullptr;                  // T
 };
 
 struct Geometry {
@@ -60,6 +66,7 @@ template <class T> void launch_poles(const hpx_plan_s* P, const T* maps, cudaStr
 template <class T> void launch_nufft(const hpx_plan_s* P, cudaStream_t s);
 template <class T> void launch_dense(const hpx_plan_s* P, cudaStream_t s);
 template <class T> void launch_rot(const hpx_plan_s* P, T* alm, cudaStream_t s);
+template <class T> void launch_adjoint(const hpx_plan_s* P, const T* alm, T* maps, cudaStream_t s);
 template <class T> void launch_cl(const hpx_plan_s* P, const T* alm, double* cl, cudaStream_t s);
 
 }  // namespace hpx

@@ -321,6 +321,23 @@ std::string build_tables(int nside, int lmax, bool fp64, PlanTables& t) {
                 t.ent[t.rowptr[i] + e] = rows[i][e].first;
                 t.entw[t.rowptr[i] + e] = rows[i][e].second;
             }
+        // the same entries grouped by latitude node (for the transposed NUFFT)
+        std::vector<std::vector<std::pair<int, double>>> byNode(Q);
+        for (int i = 0; i < M; ++i)
+            for (const auto& e : rows[i]) {
+                const int r = e.first & ((1 << 30) - 1);
+                const int mir = e.first >> 30;
+                byNode[r].push_back({i | (mir << 30), e.second});
+            }
+        t.nrowptr.assign(Q + 1, 0);
+        for (int r = 0; r < Q; ++r) t.nrowptr[r + 1] = t.nrowptr[r] + (int)byNode[r].size();
+        t.nent.resize(t.nrowptr[Q]);
+        t.nentw.resize(t.nrowptr[Q]);
+        for (int r = 0; r < Q; ++r)
+            for (size_t e = 0; e < byNode[r].size(); ++e) {
+                t.nent[t.nrowptr[r] + e] = byNode[r][e].first;
+                t.nentw[t.nrowptr[r] + e] = byNode[r][e].second;
+            }
         std::vector<double> zg, wz;
         gauss_legendre(512, zg, wz);
         t.dec.resize(p + 1);
@@ -450,6 +467,71 @@ std::string build_tables(int nside, int lmax, bool fp64, PlanTables& t) {
                 }
             }
         }
+        // skewed copy for the register wavefront (rows of 32 (cos, sin) pairs)
+        const int nq = (L / 2 + 31) / 32 + 1;
+        t.nq = nq;
+        t.skOff.assign((size_t)4 * nq + 1, 0);
+        int64_t rows = 0;
+        for (int m0 = 0; m0 < 2; ++m0)
+            for (int c = 0; c < 2; ++c)
+                for (int q = 0; q < nq; ++q) {
+                    t.skOff[(size_t)(m0 * 2 + c) * nq + q] = rows;
+                    const int n0 = chain_len(m0 + 64 * q, c, L);
+                    rows += (n0 > 0) ? n0 + 62 : 0;
+                }
+        t.skOff[(size_t)4 * nq] = rows;
+        t.skew.assign((size_t)rows * 64, 0.0);
+        for (int64_t r = 0; r < rows; ++r)
+            for (int k = 0; k < 32; ++k) t.skew[(size_t)r * 64 + 2 * k] = 1.0;
+#pragma omp parallel for collapse(3) schedule(dynamic, 1)
+        for (int m0 = 0; m0 < 2; ++m0)
+            for (int c = 0; c < 2; ++c)
+                for (int q = 0; q < nq; ++q) {
+                    const int n0 = chain_len(m0 + 64 * q, c, L);
+                    if (n0 <= 0) continue;
+                    const int64_t base = t.skOff[(size_t)(m0 * 2 + c) * nq + q];
+                    for (int k = 0; k < 32; ++k) {
+                        const int mp = m0 + 2 * (32 * q + k);   // order entering stage 32q+k
+                        if (mp + 2 > L + 1) continue;
+                        const int nrot = chain_len(mp + 2, c, L);
+                        const int64_t o = t.angOff[(size_t)mp * 2 + c];
+                        for (int i = 1; i <= nrot; ++i) {
+                            const int64_t row = base + i + 2 * k;
+                            if (row >= base + n0 + 62) break;
+                            t.skew[(size_t)row * 64 + 2 * k] = t.ang[2 * (o + i - 1)];
+                            t.skew[(size_t)row * 64 + 2 * k + 1] = t.ang[2 * (o + i - 1) + 1];
+                        }
+                    }
+                }
+        // reverse (transposed) sweeps: stage k of block q undoes forward stage 32q+31-k
+        t.skewT.assign((size_t)rows * 64, 0.0);
+#pragma omp parallel for collapse(3) schedule(dynamic, 1)
+        for (int m0 = 0; m0 < 2; ++m0)
+            for (int c = 0; c < 2; ++c)
+                for (int q = 0; q < nq; ++q) {
+                    const int n0 = chain_len(m0 + 64 * q, c, L);
+                    if (n0 <= 0) continue;
+                    const int64_t base = t.skOff[(size_t)(m0 * 2 + c) * nq + q];
+                    const int64_t nrows = n0 + 62;
+                    for (int k = 0; k < 32; ++k) {
+                        const int s = 32 * q + 31 - k;
+                        const int mp = m0 + 2 * s;
+                        const int ns = (mp + 2 <= L + 1) ? chain_len(mp + 2, c, L) : 0;
+                        const int64_t o = (mp <= L) ? t.angOff[(size_t)mp * 2 + c] : 0;
+                        for (int64_t tt = 0; tt < nrows; ++tt) {
+                            const int64_t i = ns + k - tt;
+                            double cs = 0.0, sn = 0.0;
+                            if (i >= 1 && i <= ns) {
+                                cs = t.ang[2 * (o + i - 1)];
+                                sn = t.ang[2 * (o + i - 1) + 1];
+                            } else if (i == 0) {
+                                cs = 1.0;
+                            }
+                            t.skewT[(size_t)(base + tt) * 64 + 2 * k] = cs;
+                            t.skewT[(size_t)(base + tt) * 64 + 2 * k + 1] = sn;
+                        }
+                    }
+                }
     }
     return "";
 }

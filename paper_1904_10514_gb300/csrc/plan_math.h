@@ -44,6 +44,24 @@ struct PlanTables {
     // ---- Givens rotations of the order m' -> m'+2 connection (Sec. 3.3)
     std::vector<int64_t> angOff; // [(L+1) * 2]: offset of (m', chain c)
     std::vector<double> ang;     // (cos, sin) pairs
+    // The same angles re-laid for the register wavefront of the sweep kernel:
+    // for start parity m0, chain c and block q of 32 stages (stages 32q..32q+31,
+    // orders m' = m0 + 2 s), row t, column k holds the angle that stage 32q+k
+    // applies at time step t (rotation index t - 2k), or (1, 0) where that stage
+    // is idle.  skOff[(m0 * 2 + c) * nq + q] = first row; each row = 32 pairs.
+    int nq = 0;
+    std::vector<int64_t> skOff;
+    std::vector<double> skew;
+    // Transposed sweeps (the adjoint): reverse stage k of block q undoes forward
+    // stage 32q+31-k; row t, column k holds its angle at rotation index
+    // i = n_s + k - t (n_s = rotations of that stage), (1, 0) at i = 0 (emit the
+    // carry), (0, 0) elsewhere (clear the carry / idle).  Same offsets as skOff.
+    std::vector<double> skewT;
+
+    // ---- transpose of the NUFFT spreading: CSR over latitude nodes
+    std::vector<int> nrowptr;    // [Q + 1]
+    std::vector<int> nent;       // grid point t | (mirrored << 30)
+    std::vector<double> nentw;
 };
 
 // Build all tables; returns an empty string on success or a message.
