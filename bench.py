@@ -70,12 +70,16 @@ def stage_work(ns, L, B, es=8):
             nl = len([l for l in range(mpar, L + 1) if l % 2 == par])
             nj = len([j for j in range(mpar, p + 1) if j % 2 == par])
             dense += nm * nl * nj * 4          # real matrix x complex vector: 2 FMA
+    nalm = (L + 1) * (L + 2) // 2
     return {
         "ring_fft": ("hbm", B * (npix * es // 2 + Q * (p + 1) * es)),
         "poles": ("hbm", B * 2 * 36 * 4),
         "nufft": ("hbm", B * (L + 1) * (Q * es + 2 * P2 * es)),
         "lat_solve": ("alu", B * dense),
         "rot_sweep": ("alu", B * rotation_count(L) * 12),
+        # per-order operators: n_alm x P2 real matrix entries, each applied to B complex columns
+        "fused_fsht": ("alu", B * nalm * P2 * 4),
+        "unused": ("alu", 0),
     }
 
 
@@ -246,7 +250,7 @@ def main():
     value = world * npix_step / t_step / 1e9
     if args.kernels_only:
         if rank == 0:
-            per_launch = {n: stage_ms[k] / max(ncalls, 1) for k, n in enumerate(hp.STAGES)}
+            per_launch = {n: stage_ms[k] / max(ncalls, 1) for k, n in enumerate(plan.stages)}
             print(json.dumps({"nside": ns, "batch": nb, "value": value, "unit": "Gpix/s",
                               "ms_per_step": t_step * 1e3, "stages_ms_per_launch": per_launch}), flush=True)
         if world > 1:
@@ -311,7 +315,7 @@ def main():
 
     # roofline of the dominant kernel
     work = stage_work(NSIDE, LMAX, BATCH)
-    names = hp.STAGES
+    names = [n for n in plan.stages if n != "unused"]
     per_launch = {n: stage_ms[k] / max(ncalls, 1) for k, n in enumerate(names)}
     dom = max(names, key=lambda n: per_launch[n])
     kind, amount = work[dom]
@@ -351,7 +355,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": config_dict(), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": 6 * args.steps, "clocks": clk, "fp64_single_map": fp64,
+            "gpu_launches": (len(names) + 1) * args.steps, "clocks": clk, "fp64_single_map": fp64,
             "fp32_batched_over_fp64_single": value / world / fp64["value"],
             "stages_ms_per_launch": per_launch}
     print(json.dumps(line), flush=True)

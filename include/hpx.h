@@ -52,6 +52,16 @@ extern "C" {
 #define HPX_FP32 0
 #define HPX_FP64 1
 
+/* Plan flags.
+ * HPX_FLAG_SWEEPS: apply the latitude operator D and the Givens sweeps of the
+ *   Fourier-to-SH conversion at run time (two kernels per call).  Without it the
+ *   plan composes, for every order m and parity chain, D with the sweeps into
+ *   one matrix M_{m,c} (built once in FP64 on the GPU from the same rotations,
+ *   n_alm x (nside + 1) entries, 8.6 GB in FP32 at nside 1024) and the analysis
+ *   applies those as one batched contraction; if that memory is not available
+ *   the plan falls back to the sweeps and sets this flag (hpx_plan_flags). */
+#define HPX_FLAG_SWEEPS 1u
+
 typedef struct hpx_plan_s hpx_plan_s;
 
 typedef struct hpx_plan_desc {
@@ -59,7 +69,7 @@ typedef struct hpx_plan_desc {
     int lmax;         /* largest degree returned, 0 <= lmax <= 2 nside; -1 = 2 nside */
     int batch;        /* number of maps processed per call, >= 1                  */
     int precision;    /* HPX_FP32 or HPX_FP64                                     */
-    unsigned flags;   /* reserved, must be 0                                      */
+    unsigned flags;   /* 0 or HPX_FLAG_SWEEPS                                      */
 } hpx_plan_desc;
 
 /* Plan for `batch` real FP32 maps of one nside on the current CUDA device
@@ -105,6 +115,8 @@ int64_t hpx_nalm(const hpx_plan_s* plan);
 int hpx_plan_lmax(const hpx_plan_s* plan);
 /* Bytes of device memory the plan holds (tables + workspace). */
 int64_t hpx_plan_bytes(const hpx_plan_s* plan);
+/* Flags in effect (HPX_FLAG_SWEEPS set when the sweeps run at call time). */
+int hpx_plan_flags(const hpx_plan_s* plan);
 
 /* Stage timing for profiling.  With profiling enabled (enable = 1) every
  * hpx_analyze records CUDA events on the plan's stream around each of its

@@ -32,10 +32,12 @@ HPX_FP64 = 1
 EXPORTS = ["hpx_plan", "hpx_plan_ex", "hpx_set_stream", "hpx_analyze", "hpx_synthesize", "hpx_cl",
            "hpx_sync", "hpx_destroy", "hpx_npix", "hpx_nalm", "hpx_plan_lmax", "hpx_plan_bytes",
            "hpx_last_error", "hpx_strerror", "hpx_set_profiling", "hpx_stage_times",
-           "hpx_analyze_noalloc"]
+           "hpx_analyze_noalloc", "hpx_plan_flags"]
+HPX_FLAG_SWEEPS = 1
 HPX_NOALLOC_MAX_NSIDE = 128
 HPX_NSTAGES = 5
-STAGES = ["ring_fft", "poles", "nufft", "lat_solve", "rot_sweep"]
+STAGES = ["ring_fft", "poles", "nufft", "lat_solve", "rot_sweep"]          # HPX_FLAG_SWEEPS plans
+STAGES_FUSED = ["ring_fft", "poles", "nufft", "fused_fsht", "unused"]     # per-order operators
 
 
 class hpx_plan_desc(ctypes.Structure):
@@ -79,6 +81,7 @@ def lib():
             "hpx_nalm": (i64, [vp]),
             "hpx_plan_lmax": (i32, [vp]),
             "hpx_plan_bytes": (i64, [vp]),
+            "hpx_plan_flags": (i32, [vp]),
             "hpx_last_error": (i32, []),
             "hpx_strerror": (ctypes.c_char_p, [i32]),
             "hpx_set_profiling": (i32, [vp, i32]),
@@ -162,18 +165,20 @@ def n_alm(lmax):
 class Plan:
     """Owns one C plan; tensors must live on the plan's CUDA device."""
 
-    def __init__(self, nside, lmax=-1, batch=1, precision="fp32"):
+    def __init__(self, nside, lmax=-1, batch=1, precision="fp32", sweeps=False):
         import torch
         self.torch = torch
         self.nside = int(nside)
         self.batch = int(batch)
         self.precision = HPX_FP64 if precision in ("fp64", "float64", HPX_FP64) else HPX_FP32
         self.device = torch.device("cuda", torch.cuda.current_device())
-        h = hpx_plan_ex(nside, lmax, batch, self.precision)
+        h = hpx_plan_ex(nside, lmax, batch, self.precision, HPX_FLAG_SWEEPS if sweeps else 0)
         if not h:
             raise HpxError(hpx_last_error(), "hpx_plan_ex")
         self.handle = h
         self.lmax = lib().hpx_plan_lmax(h)
+        self.flags = lib().hpx_plan_flags(h)
+        self.stages = STAGES if self.flags & HPX_FLAG_SWEEPS else STAGES_FUSED
         self.npix = lib().hpx_npix(h)
         self.nalm = lib().hpx_nalm(h)
         self.rdtype = torch.float64 if self.precision == HPX_FP64 else torch.float32

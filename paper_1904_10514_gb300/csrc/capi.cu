@@ -50,7 +50,8 @@ void free_plan(hpx_plan_s* P) {
     auto& t = P->t;
     void* ptrs[] = {t.nphi, t.startN, t.startS, t.pow2, t.logn, t.fftL, t.logL, t.shOff, t.chOff,
                     t.bhOff, t.shift, t.chirp, t.bhat, t.twid, t.poleN, t.poleS, t.polew, t.rowptr,
-                    t.ent, t.entw, t.dec, t.D, t.angOff, t.ang, t.skOff, t.skew, t.skewT, t.nrowptr, t.nent, t.nentw, P->Y, P->bvec};
+                    t.ent, t.entw, t.dec, t.D, t.angOff, t.ang, t.skOff, t.skew, t.skewT, t.nrowptr, t.nent, t.nentw, P->Y, P->bvec,
+                    P->fusedM, P->fusedOff, P->fusedTiles};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     if (P->ev) {
@@ -72,9 +73,14 @@ int analyze_impl(hpx_plan_s* P, const void* maps, void* alm) {
     if (ev) cudaEventRecord(ev[2], s);
     hpx::launch_nufft<T>(P, s);
     if (ev) cudaEventRecord(ev[3], s);
-    hpx::launch_dense<T>(P, s);
-    if (ev) cudaEventRecord(ev[4], s);
-    hpx::launch_rot<T>(P, (T*)alm, s);
+    if (P->fusedM) {
+        hpx::launch_fused<T>(P, (T*)alm, s);
+        if (ev) cudaEventRecord(ev[4], s);
+    } else {
+        hpx::launch_dense<T>(P, s);
+        if (ev) cudaEventRecord(ev[4], s);
+        hpx::launch_rot<T>(P, (T*)alm, s);
+    }
     if (ev) cudaEventRecord(ev[5], s);
     if (cudaGetLastError() != cudaSuccess) return HPX_ERR_CUDA;
     return HPX_OK;
@@ -91,7 +97,7 @@ hpx_plan_s* hpx_plan_ex(const hpx_plan_desc* d) {
     const int ns = d->nside;
     const bool fp64 = d->precision == HPX_FP64;
     if (d->precision != HPX_FP32 && d->precision != HPX_FP64) { set_err(HPX_ERR_ARG); return nullptr; }
-    if (d->flags != 0 || d->batch < 1) { set_err(HPX_ERR_ARG); return nullptr; }
+    if ((d->flags & ~(unsigned)HPX_FLAG_SWEEPS) != 0 || d->batch < 1) { set_err(HPX_ERR_ARG); return nullptr; }
     if (!is_pow2(ns) || ns < 2 || ns > (fp64 ? 1024 : 2048)) { set_err(HPX_ERR_NSIDE); return nullptr; }
     const int L = d->lmax < 0 ? 2 * ns : d->lmax;
     if (L > 2 * ns) { set_err(HPX_ERR_LMAX); return nullptr; }
@@ -145,6 +151,42 @@ hpx_plan_s* hpx_plan_ex(const hpx_plan_desc* d) {
     if (cudaMalloc(&P->bvec, bSize) != cudaSuccess) { free_plan(P); set_err(HPX_ERR_OOM); return nullptr; }
     P->beta = P->Y;   // Y is dead once the NUFFT has read it
     P->bytes += (int64_t)(std::max(ySize, bSize) + bSize);
+    P->flags = d->flags;
+    if (!(d->flags & HPX_FLAG_SWEEPS)) {
+        // per-order operators; without room for them the plan keeps the sweeps
+        std::vector<int64_t> off((size_t)(L + 1) * 2 + 1, 0);
+        std::vector<int> tiles;
+        for (int m = 0; m <= L; ++m)
+            for (int c = 0; c < 2; ++c) {
+                const int n = hpx::chain_len(m, c, L);
+                off[(size_t)m * 2 + c + 1] = off[(size_t)m * 2 + c] + n;
+                for (int i0 = 0; i0 < n; i0 += 128) { tiles.push_back(m); tiles.push_back(c); tiles.push_back(i0); }
+            }
+        const size_t mBytes = (size_t)off.back() * g.P2 * (fp64 ? 8 : 4);
+        size_t freeB = 0, totalB = 0;
+        cudaMemGetInfo(&freeB, &totalB);
+        if (mBytes + ((size_t)1 << 30) < freeB && cudaMalloc(&P->fusedM, mBytes) == cudaSuccess) {
+            P->bytes += (int64_t)mBytes;
+            P->fusedOff = up.vec(off);
+            P->fusedTiles = up.vec(tiles);
+            P->fused_ntiles = (int)(tiles.size() / 3);
+            double* D64 = (double*)t.D;
+            hpx::cplx<double>* sk64 = (hpx::cplx<double>*)t.skew;
+            if (!fp64) { D64 = up.vec(tb.D); sk64 = (hpx::cplx<double>*)up.vec(tb.skew); }
+            int rc = up.ok ? (fp64 ? hpx::build_fused<double>(P, D64, sk64, nullptr)
+                                   : hpx::build_fused<float>(P, D64, sk64, nullptr))
+                           : -1;
+            if (!fp64) {
+                if (D64) { cudaFree(D64); P->bytes -= (int64_t)(tb.D.size() * 8); }
+                if (sk64) { cudaFree(sk64); P->bytes -= (int64_t)(tb.skew.size() * 8); }
+            }
+            if (rc != 0 || !up.ok) { free_plan(P); set_err(HPX_ERR_CUDA); return nullptr; }
+        } else {
+            P->fusedM = nullptr;
+            cudaGetLastError();
+            P->flags |= HPX_FLAG_SWEEPS;
+        }
+    }
     if (cudaDeviceSynchronize() != cudaSuccess) { free_plan(P); set_err(HPX_ERR_CUDA); return nullptr; }
     set_err(HPX_OK);
     return P;
@@ -237,6 +279,7 @@ int64_t hpx_npix(const hpx_plan_s* P) { return P ? P->g.npix : 0; }
 int64_t hpx_nalm(const hpx_plan_s* P) { return P ? P->g.nalm : 0; }
 int hpx_plan_lmax(const hpx_plan_s* P) { return P ? P->g.L : -1; }
 int64_t hpx_plan_bytes(const hpx_plan_s* P) { return P ? P->bytes : 0; }
+int hpx_plan_flags(const hpx_plan_s* P) { return P ? (int)P->flags : -1; }
 
 int hpx_last_error(void) { return g_last_error; }
 

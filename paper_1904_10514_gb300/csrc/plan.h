@@ -57,6 +57,12 @@ struct hpx_plan_s {
     bool prof = false;
     int nprof = 0;
     cudaEvent_t* ev = nullptr;   // [kMaxProf][kStages + 1]
+    // per-order operators M_{m,c} (default analysis path; see k_fused.cu)
+    unsigned flags = 0;
+    void* fusedM = nullptr;        // T, n_alm x P2
+    int64_t* fusedOff = nullptr;   // first row of (m, c)
+    int* fusedTiles = nullptr;     // (m, c, first row) per block of the apply kernel
+    int fused_ntiles = 0;
 };
 
 namespace hpx {
@@ -66,6 +72,8 @@ template <class T> void launch_poles(const hpx_plan_s* P, const T* maps, cudaStr
 template <class T> void launch_nufft(const hpx_plan_s* P, cudaStream_t s);
 template <class T> void launch_dense(const hpx_plan_s* P, cudaStream_t s);
 template <class T> void launch_rot(const hpx_plan_s* P, T* alm, cudaStream_t s);
+template <class T> void launch_fused(const hpx_plan_s* P, T* alm, cudaStream_t s);
+template <class T> int build_fused(hpx_plan_s* P, const double* D64, const cplx<double>* skew64, cudaStream_t s);
 template <class T> void launch_adjoint(const hpx_plan_s* P, const T* alm, T* maps, cudaStream_t s);
 template <class T> void launch_cl(const hpx_plan_s* P, const T* alm, double* cl, cudaStream_t s);
 

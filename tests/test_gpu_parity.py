@@ -27,9 +27,10 @@ def hp():
     return hp
 
 
-def _run(hp, maps, nside, lmax, prec):
+def _run(hp, maps, nside, lmax, prec, sweeps=False):
     B = maps.shape[0]
-    plan = hp.Plan(nside, lmax, B, prec)
+    plan = hp.Plan(nside, lmax, B, prec, sweeps=sweeps)
+    assert bool(plan.flags & hp.HPX_FLAG_SWEEPS) == sweeps
     dt = torch.float64 if prec == "fp64" else torch.float32
     x = torch.as_tensor(maps, dtype=dt, device="cuda")
     alm = plan.analyze(x)
@@ -38,13 +39,15 @@ def _run(hp, maps, nside, lmax, prec):
     return alm.cpu().numpy().astype(np.complex128), cl.cpu().numpy(), plan
 
 
+@pytest.mark.parametrize("sweeps", [False, True], ids=["fused", "sweeps"])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
-@pytest.mark.parametrize("nside,lmax", [(2, 4), (4, 8), (4, 5), (8, 16), (16, 32), (16, 29), (32, 64), (64, 128)])
-def test_parity_full(hp, prec, nside, lmax):
-    maps, _ = skies.small_powerlaw_maps(nside, 3, seed=100 + nside, alpha=2.0, noise=1e-3, lmax=2 * nside)
+@pytest.mark.parametrize("nside,lmax,B", [(2, 4, 3), (4, 8, 3), (4, 5, 3), (8, 16, 3), (16, 32, 3), (16, 29, 17),
+                                          (32, 64, 3), (64, 128, 33)])
+def test_parity_full(hp, prec, nside, lmax, B, sweeps):
+    maps, _ = skies.small_powerlaw_maps(nside, B, seed=100 + nside, alpha=2.0, noise=1e-3, lmax=2 * nside)
     if prec == "fp32":
         maps = maps.astype(np.float32).astype(np.float64)   # the oracle sees the same inputs
-    a, cl, _ = _run(hp, maps, nside, lmax, prec)
+    a, cl, _ = _run(hp, maps, nside, lmax, prec, sweeps)
     ref = hp2sph.analyze(maps, nside, lmax)
     for b in range(maps.shape[0]):
         e = per_l_error(a[b], ref[b], lmax)
@@ -104,10 +107,11 @@ def _w2_reference(prec):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
-def test_workload2_nside256(hp, prec):
+@pytest.mark.parametrize("sweeps", [False, True], ids=["fused", "sweeps"])
+def test_workload2_nside256(hp, prec, sweeps):
     """Nside 256, lmax 512, FP64 and FP32 side by side; every degree."""
     maps, ref = _w2_reference(prec)
-    a, cl, _ = _run(hp, maps, 256, 512, prec)
+    a, cl, _ = _run(hp, maps, 256, 512, prec, sweeps)
     e = per_l_error(a[0], ref[0], 512)
     assert e.max() < TOL[prec], (e.max(), int(np.argmax(e)))
     clr = hp2sph.cl(ref[0], 512)
