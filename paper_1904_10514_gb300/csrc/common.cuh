@@ -37,21 +37,176 @@ __device__ void block_fft(cplx<T>* a, int n, int logn, const cplx<T>* __restrict
         }
     }
     __syncthreads();
-    for (int s = 1; s <= logn; ++s) {
-        const int half = 1 << (s - 1);
-        const int tstride = twlen >> s;   // e^{-2 pi i pos / 2^s} = tw[pos * twlen / 2^s]
+    int s = 1;
+    if (logn & 1) {   // one radix-2 stage so that the rest pair up
         for (int k = tid; k < (n >> 1); k += nt) {
-            const int pos = k & (half - 1);
-            const int i0 = ((k >> (s - 1)) << s) + pos;
-            const int i1 = i0 + half;
-            cplx<T> w = tw[pos * tstride];
-            if (inverse) w.i = -w.i;
-            const cplx<T> u = a[i0];
-            const cplx<T> v = mul(a[i1], w);
-            a[i0] = add(u, v);
-            a[i1] = sub(u, v);
+            const cplx<T> u = a[2 * k], v = a[2 * k + 1];
+            a[2 * k] = add(u, v);
+            a[2 * k + 1] = sub(u, v);
         }
         __syncthreads();
+        s = 2;
+    }
+    // two radix-2 stages (s, s+1) per pass, on the 4 elements j, j+h, j+2h, j+3h
+    // of each group of 4h (h = 2^(s-1)), held in registers
+    for (; s < logn; s += 2) {
+        const int h = 1 << (s - 1);
+        const int st1 = twlen >> s;        // e^{-2 pi i j / 2h} = tw[j * twlen / 2h]
+        const int st2 = twlen >> (s + 1);  // e^{-2 pi i j / 4h}
+        for (int k = tid; k < (n >> 2); k += nt) {
+            const int j = k & (h - 1);
+            const int i0 = ((k >> (s - 1)) << (s + 1)) + j;
+            cplx<T> w1 = tw[j * st1], w2 = tw[j * st2], w3 = tw[(j + h) * st2];
+            if (inverse) { w1.i = -w1.i; w2.i = -w2.i; w3.i = -w3.i; }
+            const cplx<T> x0 = a[i0], x1 = a[i0 + h], x2 = a[i0 + 2 * h], x3 = a[i0 + 3 * h];
+            const cplx<T> t1 = mul(x1, w1), t3 = mul(x3, w1);
+            const cplx<T> y0 = add(x0, t1), y1 = sub(x0, t1), y2 = add(x2, t3), y3 = sub(x2, t3);
+            const cplx<T> u2 = mul(y2, w2), u3 = mul(y3, w3);
+            a[i0] = add(y0, u2);
+            a[i0 + 2 * h] = sub(y0, u2);
+            a[i0 + h] = add(y1, u3);
+            a[i0 + 3 * h] = sub(y1, u3);
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Stockham FFT over shared memory with register radix-R passes.
+//
+// Element i of a transform lives at a[pad(i)]: one spare slot every 16
+// elements, so that the strided accesses of the passes are free of bank
+// conflicts.  A pass of radix R over span S (the product of the radices done so
+// far) takes, for each group k = g S + j, the R elements k + r N/R, multiplies
+// element r by w^(r j) (w = e^{-2 pi i / (S R)}), applies an R-point DFT in
+// registers and stores output q at g S R + j + q S.  Every thread reads all of
+// its groups before a barrier and writes after it, so the pass runs in place.
+__device__ __forceinline__ int pad(int i) { return i + (i >> 4); }
+
+// cos / sin of 2 pi k / 16, k = 0..7
+__device__ __forceinline__ float c16f(int k) {
+    constexpr float c[8] = {1.0f, 0.92387953251128674f, 0.70710678118654752f, 0.38268343236508977f,
+                            0.0f, -0.38268343236508977f, -0.70710678118654752f, -0.92387953251128674f};
+    return c[k];
+}
+__device__ __forceinline__ float s16f(int k) {
+    constexpr float s[8] = {0.0f, 0.38268343236508977f, 0.70710678118654752f, 0.92387953251128674f,
+                            1.0f, 0.92387953251128674f, 0.70710678118654752f, 0.38268343236508977f};
+    return s[k];
+}
+__device__ __forceinline__ double c16d(int k) {
+    constexpr double c[8] = {1.0, 0.92387953251128674, 0.70710678118654752, 0.38268343236508977,
+                             0.0, -0.38268343236508977, -0.70710678118654752, -0.92387953251128674};
+    return c[k];
+}
+__device__ __forceinline__ double s16d(int k) {
+    constexpr double s[8] = {0.0, 0.38268343236508977, 0.70710678118654752, 0.92387953251128674,
+                             1.0, 0.92387953251128674, 0.70710678118654752, 0.38268343236508977};
+    return s[k];
+}
+
+// In-register R-point DFT (R = 2, 4, 8, 16): radix-2 decimation in frequency,
+// then the bit-reversed outputs are renamed into natural order.
+template <class T, int R, bool INV>
+__device__ __forceinline__ void reg_dft(cplx<T>* x) {
+#pragma unroll
+    for (int half = R / 2; half >= 1; half >>= 1) {
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            if ((i & half) == 0) {
+                const int pos = i & (half - 1);
+                const int k16 = pos * (8 / half);   // e^{-2 pi i pos / (2 half)} = e^{-2 pi i k16 / 16}
+                const cplx<T> u = x[i], v = x[i + half];
+                x[i] = add(u, v);
+                const cplx<T> d = sub(u, v);
+                if (pos == 0) {
+                    x[i + half] = d;
+                } else {
+                    const T c = sizeof(T) == 4 ? (T)c16f(k16) : (T)c16d(k16);
+                    const T s = sizeof(T) == 4 ? (T)s16f(k16) : (T)s16d(k16);
+                    const T sn = INV ? s : -s;   // w = c + i sn
+                    x[i + half] = mk<T>(d.r * c - d.i * sn, d.r * sn + d.i * c);
+                }
+            }
+        }
+    }
+    constexpr int br2[2] = {0, 1};
+    constexpr int br4[4] = {0, 2, 1, 3};
+    constexpr int br8[8] = {0, 4, 2, 6, 1, 5, 3, 7};
+    constexpr int br16[16] = {0, 8, 4, 12, 2, 10, 6, 14, 1, 9, 5, 13, 3, 11, 7, 15};
+    cplx<T> y[R];
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+        const int rq = R == 16 ? br16[q] : R == 8 ? br8[q] : R == 4 ? br4[q] : br2[q];
+        y[q] = x[rq];
+    }
+#pragma unroll
+    for (int q = 0; q < R; ++q) x[q] = y[q];
+}
+
+template <class T, int R, int G, bool INV>
+__device__ __forceinline__ void stockham_pass(cplx<T>* a, int N, int logS, const cplx<T>* __restrict__ tw,
+                                              int twlen) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int ngroups = N / R;
+    const int S = 1 << logS;
+    cplx<T> x[G][R];
+#pragma unroll
+    for (int gg = 0; gg < G; ++gg) {
+        const int k = tid + gg * nt;
+        if (k < ngroups) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) x[gg][r] = a[pad(k + r * ngroups)];
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int gg = 0; gg < G; ++gg) {
+        const int k = tid + gg * nt;
+        if (k < ngroups) {
+            const int j = k & (S - 1);
+            const int g = k >> logS;
+            if (S > 1) {
+                const int step = twlen / (S * R);   // w^(r j) = tw[r j step]
+#pragma unroll
+                for (int r = 1; r < R; ++r) {
+                    cplx<T> w = tw[r * j * step];
+                    if (INV) w.i = -w.i;
+                    x[gg][r] = mul(x[gg][r], w);
+                }
+            }
+            reg_dft<T, R, INV>(x[gg]);
+            const int base = g * S * R + j;
+#pragma unroll
+            for (int q = 0; q < R; ++q) a[pad(base + q * S)] = x[gg][q];
+        }
+    }
+    __syncthreads();
+}
+
+// DFT of length N = 2^logn (forward sign -1, or inverse +1 unnormalised) of the
+// padded shared array a, by all threads of the block.  E = elements per thread
+// and pass (16 or 32): radix-16 passes with E/16 groups per thread, then one
+// pass of the remaining radix with E/R groups; the caller guarantees
+// N <= E * blockDim.  `tw` holds e^{-2 pi i k / twlen} for k < twlen (the full
+// circle).  Ends with a barrier.
+template <class T, int E>
+__device__ __forceinline__ void block_fft_pad(cplx<T>* a, int logn, const cplx<T>* __restrict__ tw, int twlen,
+                                              bool inverse) {
+    const int N = 1 << logn;
+    int logS = 0;
+    if (inverse) {
+        for (; logn - logS >= 4; logS += 4) stockham_pass<T, 16, E / 16, true>(a, N, logS, tw, twlen);
+        const int lr = logn - logS;
+        if (lr == 3) stockham_pass<T, 8, E / 8, true>(a, N, logS, tw, twlen);
+        else if (lr == 2) stockham_pass<T, 4, E / 4, true>(a, N, logS, tw, twlen);
+        else if (lr == 1) stockham_pass<T, 2, E / 2, true>(a, N, logS, tw, twlen);
+    } else {
+        for (; logn - logS >= 4; logS += 4) stockham_pass<T, 16, E / 16, false>(a, N, logS, tw, twlen);
+        const int lr = logn - logS;
+        if (lr == 3) stockham_pass<T, 8, E / 8, false>(a, N, logS, tw, twlen);
+        else if (lr == 2) stockham_pass<T, 4, E / 4, false>(a, N, logS, tw, twlen);
+        else if (lr == 1) stockham_pass<T, 2, E / 2, false>(a, N, logS, tw, twlen);
     }
 }
 

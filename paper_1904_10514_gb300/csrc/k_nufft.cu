@@ -20,14 +20,14 @@
 
 namespace hpx {
 
-template <class T>
-__global__ void __launch_bounds__(512) nufft_kernel(
+template <class T, int E>
+__global__ void __launch_bounds__(512, 1) nufft_kernel(
     const cplx<T>* __restrict__ Y, cplx<T>* __restrict__ bvec, const int* __restrict__ rowptr,
     const int* __restrict__ ent, const T* __restrict__ entw, const T* __restrict__ dec,
     const cplx<T>* __restrict__ tw, int twlen, int M, int logM, int p, int Q, int P2, int mcount) {
     extern __shared__ unsigned char smem_raw[];
     cplx<T>* u = reinterpret_cast<cplx<T>*>(smem_raw);   // M
-    cplx<T>* y = u + M;                                    // Q
+    cplx<T>* y = u + M + M / 16;                           // Q (after the padded grid)
     const int m = blockIdx.x;
     const int b = blockIdx.y;
     const int tid = threadIdx.x, nt = blockDim.x;
@@ -47,13 +47,13 @@ __global__ void __launch_bounds__(512) nufft_kernel(
             ar += w * v.r;
             ai += w * v.i;
         }
-        u[t] = mk<T>(ar, ai);
+        u[pad(t)] = mk<T>(ar, ai);
     }
     __syncthreads();
-    block_fft(u, M, logM, tw, twlen, false);
+    block_fft_pad<T, E>(u, logM, tw, twlen, false);
     cplx<T>* out = bvec + ((int64_t)b * (p + 1) + m) * 2 * P2;
     for (int j = tid; j <= p; j += nt) {
-        cplx<T> v = scale(u[j], dec[j]);
+        cplx<T> v = scale(u[pad(j)], dec[j]);
         if (odd) v = mk<T>(T(-0.5) * v.i, T(0.5) * v.r);
         out[(j & 1) * P2 + (j >> 1)] = v;
     }
@@ -67,10 +67,11 @@ void launch_nufft(const hpx_plan_s* P, cudaStream_t s) {
     const auto& t = P->t;
     int logM = 0;
     while ((1 << logM) < g.M) ++logM;
-    const size_t smem = (size_t)(g.M + g.Q) * sizeof(cplx<T>);
-    cudaFuncSetAttribute(nufft_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem = (size_t)(g.M + g.M / 16 + g.Q) * sizeof(cplx<T>);
+    auto kern = g.M > 16 * 512 ? nufft_kernel<T, 32> : nufft_kernel<T, 16>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     dim3 grid(g.L + 1, g.B);
-    nufft_kernel<T><<<grid, 512, smem, s>>>((const cplx<T>*)P->Y, (cplx<T>*)P->bvec, t.rowptr, t.ent,
+    kern<<<grid, 512, smem, s>>>((const cplx<T>*)P->Y, (cplx<T>*)P->bvec, t.rowptr, t.ent,
                                             (const T*)t.entw, (const T*)t.dec, (const cplx<T>*)t.twid,
                                             g.Lmax, g.M, logM, g.p, g.Q, g.P2, g.L + 1);
 }

@@ -1,10 +1,12 @@
 // Step 1 of Algorithm 1 (Sec. 3.1): per-ring trigonometric interpolation,
 // half-pixel shift and zero padding, and the pole values of Sec. 3.2.1.
 //
-// One thread block handles one north/south ring pair of one map.  The two real
-// rings (same nphi, same first longitude) are packed into one complex sequence
-// z = f_N + i f_S and transformed once:
-//   * nphi a power of two: radix-2 FFT of length nphi in shared memory;
+// One thread block handles one north/south ring pair of one map; the blocks of
+// one ring pair for all maps are adjacent in the grid, so the ring's tables stay
+// in L2 while its maps are processed.  The two real rings (same nphi, same first
+// longitude) are packed into one complex sequence z = f_N + i f_S and
+// transformed once:
+//   * nphi a power of two: Stockham FFT of length nphi in shared memory;
 //   * otherwise (polar rings 4j): Bluestein's chirp-z transform with a
 //     power-of-two convolution length L >= 2 nphi - 1; the chirps and the
 //     transformed conjugate chirp come from FP64-built tables.
@@ -18,8 +20,10 @@
 
 namespace hpx {
 
-template <class T>
-__global__ void __launch_bounds__(256) ring_fft_kernel(
+constexpr int kRingThreads = 512;
+
+template <class T, int E>
+__global__ void __launch_bounds__(kRingThreads, 1) ring_fft_kernel(
     const T* __restrict__ maps, cplx<T>* __restrict__ Y, const int* __restrict__ nphi_t,
     const int* __restrict__ startN_t, const int* __restrict__ startS_t,
     const int* __restrict__ pow2_t, const int* __restrict__ logn_t, const int* __restrict__ fftL_t,
@@ -30,9 +34,9 @@ __global__ void __launch_bounds__(256) ring_fft_kernel(
     int64_t npix, int npairs) {
     extern __shared__ unsigned char smem_raw[];
     cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw);
-    // largest rings first: blockIdx.x = 0 is the equator
-    const int i = npairs - 1 - (int)blockIdx.x;
-    const int b = blockIdx.y;
+    // largest rings first: blockIdx.y = 0 is the equator
+    const int i = npairs - 1 - (int)blockIdx.y;
+    const int b = blockIdx.x;
     const int n = nphi_t[i];
     const int sN = startN_t[i], sS = startS_t[i];
     const bool equator = (sN == sS);
@@ -40,9 +44,9 @@ __global__ void __launch_bounds__(256) ring_fft_kernel(
     const int tid = threadIdx.x, nt = blockDim.x;
 
     if (pow2_t[i]) {
-        for (int k = tid; k < n; k += nt) buf[k] = mk<T>(f[sN + k], equator ? T(0) : f[sS + k]);
+        for (int k = tid; k < n; k += nt) buf[pad(k)] = mk<T>(f[sN + k], equator ? T(0) : f[sS + k]);
         __syncthreads();
-        block_fft(buf, n, logn_t[i], tw, twlen, false);
+        block_fft_pad<T, E>(buf, logn_t[i], tw, twlen, false);
     } else {
         const int L = fftL_t[i];
         const cplx<T>* ch = chirp + chOff_t[i];
@@ -50,14 +54,14 @@ __global__ void __launch_bounds__(256) ring_fft_kernel(
         for (int k = tid; k < L; k += nt) {
             cplx<T> v = mk<T>(T(0), T(0));
             if (k < n) v = mul(mk<T>(f[sN + k], equator ? T(0) : f[sS + k]), ch[k]);
-            buf[k] = v;
+            buf[pad(k)] = v;
         }
         __syncthreads();
-        block_fft(buf, L, logL_t[i], tw, twlen, false);
-        for (int k = tid; k < L; k += nt) buf[k] = mul(buf[k], bh[k]);
+        block_fft_pad<T, E>(buf, logL_t[i], tw, twlen, false);
+        for (int k = tid; k < L; k += nt) buf[pad(k)] = mul(buf[pad(k)], bh[k]);
         __syncthreads();
-        block_fft(buf, L, logL_t[i], tw, twlen, true);
-        for (int k = tid; k < n; k += nt) buf[k] = mul(buf[k], ch[k]);
+        block_fft_pad<T, E>(buf, logL_t[i], tw, twlen, true);
+        for (int k = tid; k < n; k += nt) buf[pad(k)] = mul(buf[pad(k)], ch[k]);
         __syncthreads();
     }
 
@@ -68,8 +72,8 @@ __global__ void __launch_bounds__(256) ring_fft_kernel(
     for (int m = tid; m <= p; m += nt) {
         cplx<T> cN = mk<T>(T(0), T(0)), cS = cN;
         if (m <= h) {
-            const cplx<T> zm = buf[m];
-            const cplx<T> zc = conjg(buf[m == 0 ? 0 : n - m]);
+            const cplx<T> zm = buf[pad(m)];
+            const cplx<T> zc = conjg(buf[pad(m == 0 ? 0 : n - m)]);
             const cplx<T> fn = scale(add(zm, zc), T(0.5));              // n * c~_m (north)
             const cplx<T> d = sub(zm, zc);
             const cplx<T> fs = mk<T>(T(0.5) * d.i, T(-0.5) * d.r);      // n * c~_m (south)
@@ -124,10 +128,11 @@ template <class T>
 void launch_ring_fft(const hpx_plan_s* P, const T* maps, cudaStream_t s) {
     const auto& g = P->g;
     const auto& t = P->t;
-    const size_t smem = (size_t)g.smem_ring * sizeof(cplx<T>);
-    cudaFuncSetAttribute(ring_fft_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    dim3 grid(g.npairs, g.B);
-    ring_fft_kernel<T><<<grid, 256, smem, s>>>(
+    const size_t smem = (size_t)(g.smem_ring + g.smem_ring / 16) * sizeof(cplx<T>);
+    dim3 grid(g.B, g.npairs);
+    auto kern = g.smem_ring > 16 * kRingThreads ? ring_fft_kernel<T, 32> : ring_fft_kernel<T, 16>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    kern<<<grid, kRingThreads, smem, s>>>(
         maps, (cplx<T>*)P->Y, t.nphi, t.startN, t.startS, t.pow2, t.logn, t.fftL, t.logL, t.shOff,
         t.chOff, t.bhOff, (const cplx<T>*)t.shift, (const cplx<T>*)t.chirp, (const cplx<T>*)t.bhat,
         (const cplx<T>*)t.twid, g.Lmax, g.p, g.Q, g.npix, g.npairs);

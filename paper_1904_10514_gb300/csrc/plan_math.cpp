@@ -222,8 +222,8 @@ std::string build_tables(int nside, int lmax, bool fp64, PlanTables& t) {
             }
         }
     }
-    t.twid.assign(t.Lmax, 0.0);   // Lmax/2 complex
-    for (int k = 0; k < t.Lmax / 2; ++k) {
+    t.twid.assign(2 * (size_t)t.Lmax, 0.0);   // Lmax complex: the full circle
+    for (int k = 0; k < t.Lmax; ++k) {
         const double ang = -2.0 * kPi * (double)k / (double)t.Lmax;
         t.twid[2 * k] = std::cos(ang);
         t.twid[2 * k + 1] = std::sin(ang);
