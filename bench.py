@@ -212,7 +212,10 @@ def main():
         maps_np = skies.workload_maps(WORKLOAD, nmaps=nb, first=rank * nb, dtype=np.float32)
     else:
         maps_np = skies.small_powerlaw_maps(ns, nb, seed=6000 + rank, alpha=2.0, noise=1e-3)[0].astype(np.float32)
+    t_plan0 = time.perf_counter()
     plan = hp.Plan(ns, 2 * ns, nb, "fp32")
+    torch.cuda.synchronize()
+    plan_build_s = time.perf_counter() - t_plan0
     maps = torch.from_numpy(maps_np).cuda()
     alm = torch.empty((nb, plan.nalm), dtype=torch.complex64, device="cuda")
     cl = torch.empty((nb, plan.lmax + 1), dtype=torch.float64, device="cuda")
@@ -252,7 +255,8 @@ def main():
         if rank == 0:
             per_launch = {n: stage_ms[k] / max(ncalls, 1) for k, n in enumerate(plan.stages)}
             print(json.dumps({"nside": ns, "batch": nb, "value": value, "unit": "Gpix/s",
-                              "ms_per_step": t_step * 1e3, "stages_ms_per_launch": per_launch}), flush=True)
+                              "ms_per_step": t_step * 1e3, "stages_ms_per_launch": per_launch,
+                              "plan_build_s": plan_build_s, "plan_gb": plan.nbytes / 1e9}), flush=True)
         if world > 1:
             dist.destroy_process_group()
         return
@@ -357,7 +361,8 @@ def main():
             "config": config_dict(), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": (len(names) + 1) * args.steps, "clocks": clk, "fp64_single_map": fp64,
             "fp32_batched_over_fp64_single": value / world / fp64["value"],
-            "stages_ms_per_launch": per_launch}
+            "stages_ms_per_launch": per_launch, "plan_build_s": plan_build_s, "plan_gb": plan.nbytes / 1e9,
+            "plan_path": "sweeps" if plan.flags & hp.HPX_FLAG_SWEEPS else "per-order operators"}
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -61,6 +61,17 @@ extern "C" {
  *   applies those as one batched contraction; if that memory is not available
  *   the plan falls back to the sweeps and sets this flag (hpx_plan_flags). */
 #define HPX_FLAG_SWEEPS 1u
+/* HPX_FLAG_GRAPH: the first hpx_analyze call with a given (maps, alm) pair
+ *   captures the plan's whole launch sequence into a CUDA graph (on a stream of
+ *   the plan's own); later calls with the same pair replay it with one graph
+ *   launch on the plan's stream.  Must not be used while the caller is itself
+ *   capturing the plan's stream. */
+#define HPX_FLAG_GRAPH 2u
+/* HPX_FLAG_SIMT: apply the per-order operators of an FP32 plan on the FP32
+ *   pipes.  By default FP32 plans of 9 or more maps use the tensor cores
+ *   (tcgen05, 3xTF32: each operand split into two TF32 parts, three MMAs
+ *   accumulated in FP32). */
+#define HPX_FLAG_SIMT 4u
 
 typedef struct hpx_plan_s hpx_plan_s;
 
@@ -69,7 +80,16 @@ typedef struct hpx_plan_desc {
     int lmax;         /* largest degree returned, 0 <= lmax <= 2 nside; -1 = 2 nside */
     int batch;        /* number of maps processed per call, >= 1                  */
     int precision;    /* HPX_FP32 or HPX_FP64                                     */
-    unsigned flags;   /* 0 or HPX_FLAG_SWEEPS                                      */
+    unsigned flags;   /* HPX_FLAG_SWEEPS | HPX_FLAG_GRAPH | HPX_FLAG_SIMT, or 0    */
+    /* Uneven batches: NULL, or `batch` values giving the nside of every map
+     * (then `nside` is ignored).  Maps, coefficients and spectra are then
+     * concatenated in the given order: map i occupies 12 nside_i^2 elements of
+     * `maps`, n_alm(lmax_i) coefficients of `alm` and lmax_i + 1 values of `cl`,
+     * with lmax_i = 2 nside_i when lmax = -1, else lmax (<= 2 min nside_i).  The
+     * plan holds one uniform sub-plan per distinct nside; maps of one nside that
+     * are adjacent in the batch are used in place, others are gathered into
+     * plan-owned staging buffers.  The caller's array must outlive the call. */
+    const int* nsides;
 } hpx_plan_desc;
 
 /* Plan for `batch` real FP32 maps of one nside on the current CUDA device

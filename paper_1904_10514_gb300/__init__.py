@@ -34,6 +34,7 @@ EXPORTS = ["hpx_plan", "hpx_plan_ex", "hpx_set_stream", "hpx_analyze", "hpx_synt
            "hpx_last_error", "hpx_strerror", "hpx_set_profiling", "hpx_stage_times",
            "hpx_analyze_noalloc", "hpx_plan_flags"]
 HPX_FLAG_SWEEPS = 1
+HPX_FLAG_GRAPH = 2
 HPX_NOALLOC_MAX_NSIDE = 128
 HPX_NSTAGES = 5
 STAGES = ["ring_fft", "poles", "nufft", "lat_solve", "rot_sweep"]          # HPX_FLAG_SWEEPS plans
@@ -42,7 +43,8 @@ STAGES_FUSED = ["ring_fft", "poles", "nufft", "fused_fsht", "unused"]     # per-
 
 class hpx_plan_desc(ctypes.Structure):
     _fields_ = [("nside", ctypes.c_int), ("lmax", ctypes.c_int), ("batch", ctypes.c_int),
-                ("precision", ctypes.c_int), ("flags", ctypes.c_uint)]
+                ("precision", ctypes.c_int), ("flags", ctypes.c_uint),
+                ("nsides", ctypes.POINTER(ctypes.c_int))]
 
 
 class HpxError(RuntimeError):
@@ -105,8 +107,13 @@ def hpx_plan(nside, lmax, batch):
     return lib().hpx_plan(int(nside), int(lmax), int(batch))
 
 
-def hpx_plan_ex(nside, lmax=-1, batch=1, precision=HPX_FP32, flags=0):
-    d = hpx_plan_desc(int(nside), int(lmax), int(batch), int(precision), int(flags))
+def hpx_plan_ex(nside, lmax=-1, batch=1, precision=HPX_FP32, flags=0, nsides=None):
+    arr = None
+    if nsides is not None:
+        arr = (ctypes.c_int * len(nsides))(*[int(v) for v in nsides])
+        batch = len(nsides)
+    d = hpx_plan_desc(int(nside), int(lmax), int(batch), int(precision), int(flags),
+                      ctypes.cast(arr, ctypes.POINTER(ctypes.c_int)) if arr is not None else None)
     return lib().hpx_plan_ex(ctypes.byref(d))
 
 
@@ -165,17 +172,22 @@ def n_alm(lmax):
 class Plan:
     """Owns one C plan; tensors must live on the plan's CUDA device."""
 
-    def __init__(self, nside, lmax=-1, batch=1, precision="fp32", sweeps=False):
+    def __init__(self, nside=None, lmax=-1, batch=1, precision="fp32", sweeps=False, graph=False, nsides=None):
+        """Uniform batch (nside, batch) or uneven batch (nsides = nside of every map;
+        maps, alm and C_l are then 1-D tensors holding the maps concatenated)."""
         import torch
         self.torch = torch
-        self.nside = int(nside)
-        self.batch = int(batch)
+        self.nsides = None if nsides is None else [int(v) for v in nsides]
+        self.nside = int(nside) if nside is not None else 0
+        self.batch = len(self.nsides) if self.nsides is not None else int(batch)
         self.precision = HPX_FP64 if precision in ("fp64", "float64", HPX_FP64) else HPX_FP32
         self.device = torch.device("cuda", torch.cuda.current_device())
-        h = hpx_plan_ex(nside, lmax, batch, self.precision, HPX_FLAG_SWEEPS if sweeps else 0)
+        flags = (HPX_FLAG_SWEEPS if sweeps else 0) | (HPX_FLAG_GRAPH if graph else 0)
+        h = hpx_plan_ex(self.nside, lmax, self.batch, self.precision, flags, self.nsides)
         if not h:
             raise HpxError(hpx_last_error(), "hpx_plan_ex")
         self.handle = h
+        self._lmax_arg = int(lmax)
         self.lmax = lib().hpx_plan_lmax(h)
         self.flags = lib().hpx_plan_flags(h)
         self.stages = STAGES if self.flags & HPX_FLAG_SWEEPS else STAGES_FUSED
@@ -195,17 +207,26 @@ class Plan:
         if rc != HPX_OK:
             raise HpxError(rc, what)
 
+    def _shape(self, n):
+        return (n,) if self.nsides is not None else (self.batch, n)
+
     def _maps(self, maps):
-        t = self.torch
-        if maps.dtype != self.rdtype or maps.device.type != "cuda" or tuple(maps.shape) != (self.batch, self.npix):
-            raise ValueError("maps must be a CUDA %s tensor of shape (%d, %d)" % (self.rdtype, self.batch, self.npix))
+        shape = self._shape(self.npix)
+        if maps.dtype != self.rdtype or maps.device.type != "cuda" or tuple(maps.shape) != shape:
+            raise ValueError("maps must be a CUDA %s tensor of shape %s" % (self.rdtype, shape))
         return maps.contiguous()
+
+    @property
+    def ncl(self):
+        if self.nsides is None:
+            return self.lmax + 1
+        return sum((2 * n if self._lmax_arg < 0 else self._lmax_arg) + 1 for n in self.nsides)
 
     def analyze(self, maps, out=None):
         """maps (batch, npix) -> alm (batch, n_alm) complex, m-major packing."""
         maps = self._maps(maps)
         if out is None:
-            out = self.torch.empty((self.batch, self.nalm), dtype=self.cdtype, device=maps.device)
+            out = self.torch.empty(self._shape(self.nalm), dtype=self.cdtype, device=maps.device)
         self._stream()
         self._check(hpx_analyze(self.handle, maps.data_ptr(), out.data_ptr()), "hpx_analyze")
         return out
@@ -214,7 +235,7 @@ class Plan:
         """Exact adjoint of analyze: alm (batch, n_alm) complex -> maps (batch, npix)."""
         alm = alm.contiguous()
         if out is None:
-            out = self.torch.empty((self.batch, self.npix), dtype=self.rdtype, device=alm.device)
+            out = self.torch.empty(self._shape(self.npix), dtype=self.rdtype, device=alm.device)
         self._stream()
         self._check(hpx_synthesize(self.handle, alm.data_ptr(), out.data_ptr()), "hpx_synthesize")
         return out
@@ -223,7 +244,8 @@ class Plan:
         """C_l (batch, lmax+1) float64 of Eq. (APS)."""
         alm = alm.contiguous()
         if out is None:
-            out = self.torch.empty((self.batch, self.lmax + 1), dtype=self.torch.float64, device=alm.device)
+            out = self.torch.empty((self.ncl,) if self.nsides is not None else (self.batch, self.lmax + 1),
+                                   dtype=self.torch.float64, device=alm.device)
         self._stream()
         self._check(hpx_cl(self.handle, alm.data_ptr(), out.data_ptr()), "hpx_cl")
         return out

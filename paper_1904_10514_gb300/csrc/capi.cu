@@ -47,11 +47,18 @@ struct Uploader {
 
 void free_plan(hpx_plan_s* P) {
     if (!P) return;
+    for (auto& e : P->graphs) cudaGraphExecDestroy(e.exec);
+    if (P->cap) cudaStreamDestroy(P->cap);
+    if (P->group) {
+        hpx::group_free(P);
+        delete P;
+        return;
+    }
     auto& t = P->t;
     void* ptrs[] = {t.nphi, t.startN, t.startS, t.pow2, t.logn, t.fftL, t.logL, t.shOff, t.chOff,
                     t.bhOff, t.shift, t.chirp, t.bhat, t.twid, t.poleN, t.poleS, t.polew, t.rowptr,
-                    t.ent, t.entw, t.dec, t.D, t.angOff, t.ang, t.skOff, t.skew, t.skewT, t.nrowptr, t.nent, t.nentw, P->Y, P->bvec,
-                    P->fusedM, P->fusedOff, P->fusedTiles};
+                    t.ent, t.entw, t.dec, t.D, t.angOff, t.ang, t.skOff, t.skew, t.skewT, t.nrowptr, t.nent, t.nentw, t.nstart, t.swts, P->Y, P->bvec,
+                    P->fusedM, P->fusedOff, P->fusedTiles, P->d_status};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     if (P->ev) {
@@ -74,7 +81,12 @@ int analyze_impl(hpx_plan_s* P, const void* maps, void* alm) {
     hpx::launch_nufft<T>(P, s);
     if (ev) cudaEventRecord(ev[3], s);
     if (P->fusedM) {
-        hpx::launch_fused<T>(P, (T*)alm, s);
+        if constexpr (sizeof(T) == 4) {
+            if (P->use_tc) hpx::launch_fused_tc(P, (float*)alm, s);
+            else hpx::launch_fused<T>(P, (T*)alm, s);
+        } else {
+            hpx::launch_fused<T>(P, (T*)alm, s);
+        }
         if (ev) cudaEventRecord(ev[4], s);
     } else {
         hpx::launch_dense<T>(P, s);
@@ -94,10 +106,26 @@ extern "C" {
 
 hpx_plan_s* hpx_plan_ex(const hpx_plan_desc* d) {
     if (!d) { set_err(HPX_ERR_ARG); return nullptr; }
+    if ((d->flags & ~(unsigned)(HPX_FLAG_SWEEPS | HPX_FLAG_GRAPH | HPX_FLAG_SIMT)) != 0 || d->batch < 1) {
+        set_err(HPX_ERR_ARG);
+        return nullptr;
+    }
+    if (d->precision != HPX_FP32 && d->precision != HPX_FP64) { set_err(HPX_ERR_ARG); return nullptr; }
+    if (d->nsides) {
+        int err = HPX_OK;
+        hpx_plan_s* G = hpx::group_create(d, &err);
+        if (!G) { set_err(err); return nullptr; }
+        if ((d->flags & HPX_FLAG_GRAPH) && cudaStreamCreateWithFlags(&G->cap, cudaStreamNonBlocking) != cudaSuccess) {
+            free_plan(G);
+            set_err(HPX_ERR_CUDA);
+            return nullptr;
+        }
+        set_err(HPX_OK);
+        return G;
+    }
     const int ns = d->nside;
     const bool fp64 = d->precision == HPX_FP64;
     if (d->precision != HPX_FP32 && d->precision != HPX_FP64) { set_err(HPX_ERR_ARG); return nullptr; }
-    if ((d->flags & ~(unsigned)HPX_FLAG_SWEEPS) != 0 || d->batch < 1) { set_err(HPX_ERR_ARG); return nullptr; }
     if (!is_pow2(ns) || ns < 2 || ns > (fp64 ? 1024 : 2048)) { set_err(HPX_ERR_NSIDE); return nullptr; }
     const int L = d->lmax < 0 ? 2 * ns : d->lmax;
     if (L > 2 * ns) { set_err(HPX_ERR_LMAX); return nullptr; }
@@ -137,6 +165,7 @@ hpx_plan_s* hpx_plan_ex(const hpx_plan_desc* d) {
     t.npole = (int)tb.polew.size();
     t.rowptr = up.vec(tb.rowptr); t.ent = up.vec(tb.ent);
     t.entw = up.real(tb.entw, fp64); t.dec = up.real(tb.dec, fp64);
+    t.nstart = up.vec(tb.nstart); t.swts = up.real(tb.swts, fp64); t.spreadE = tb.spreadE;
     t.D = up.real(tb.D, fp64);
     t.angOff = up.vec(tb.angOff); t.ang = up.real(tb.ang, fp64);
     t.skOff = up.vec(tb.skOff); t.skew = up.real(tb.skew, fp64); t.nq = tb.nq;
@@ -152,24 +181,35 @@ hpx_plan_s* hpx_plan_ex(const hpx_plan_desc* d) {
     P->beta = P->Y;   // Y is dead once the NUFFT has read it
     P->bytes += (int64_t)(std::max(ySize, bSize) + bSize);
     P->flags = d->flags;
+    if (cudaMalloc(&P->d_status, sizeof(int)) != cudaSuccess) { free_plan(P); set_err(HPX_ERR_OOM); return nullptr; }
+    cudaMemset(P->d_status, 0, sizeof(int));
+    if ((d->flags & HPX_FLAG_GRAPH) && cudaStreamCreateWithFlags(&P->cap, cudaStreamNonBlocking) != cudaSuccess) {
+        free_plan(P);
+        set_err(HPX_ERR_CUDA);
+        return nullptr;
+    }
     if (!(d->flags & HPX_FLAG_SWEEPS)) {
         // per-order operators; without room for them the plan keeps the sweeps
         std::vector<int64_t> off((size_t)(L + 1) * 2 + 1, 0);
         std::vector<int> tiles;
+        const int rows = hpx::fused_tile_rows(g.B);
         for (int m = 0; m <= L; ++m)
             for (int c = 0; c < 2; ++c) {
                 const int n = hpx::chain_len(m, c, L);
                 off[(size_t)m * 2 + c + 1] = off[(size_t)m * 2 + c] + n;
-                for (int i0 = 0; i0 < n; i0 += 128) { tiles.push_back(m); tiles.push_back(c); tiles.push_back(i0); }
+                for (int i0 = 0; i0 < n; i0 += rows) { tiles.push_back(m); tiles.push_back(c); tiles.push_back(i0); }
             }
-        const size_t mBytes = (size_t)off.back() * g.P2 * (fp64 ? 8 : 4);
+        P->fused_ldm = (g.P2 + 3) / 4 * 4;
+        const size_t mBytes = (size_t)off.back() * P->fused_ldm * (fp64 ? 8 : 4);
         size_t freeB = 0, totalB = 0;
         cudaMemGetInfo(&freeB, &totalB);
         if (mBytes + ((size_t)1 << 30) < freeB && cudaMalloc(&P->fusedM, mBytes) == cudaSuccess) {
             P->bytes += (int64_t)mBytes;
+            cudaMemset(P->fusedM, 0, mBytes);   // zero the row padding
             P->fusedOff = up.vec(off);
             P->fusedTiles = up.vec(tiles);
             P->fused_ntiles = (int)(tiles.size() / 3);
+            P->use_tc = !fp64 && g.B > 8 && !(d->flags & HPX_FLAG_SIMT);
             double* D64 = (double*)t.D;
             hpx::cplx<double>* sk64 = (hpx::cplx<double>*)t.skew;
             if (!fp64) { D64 = up.vec(tb.D); sk64 = (hpx::cplx<double>*)up.vec(tb.skew); }
@@ -208,15 +248,56 @@ int hpx_set_stream(hpx_plan_s* P, void* stream) {
     return set_err(HPX_OK);
 }
 
+namespace {
+
+int analyze_direct(hpx_plan_s* P, const void* maps, void* alm) {
+    if (P->group) return hpx::group_analyze(P, maps, alm);
+    return P->precision == HPX_FP64 ? analyze_impl<double>(P, maps, alm) : analyze_impl<float>(P, maps, alm);
+}
+
+// HPX_FLAG_GRAPH: replay the graph captured for this (maps, alm) pair, or
+// capture the launch sequence on the plan's own stream first.
+int analyze_graph(hpx_plan_s* P, const void* maps, void* alm) {
+    for (auto& e : P->graphs)
+        if (e.maps == maps && e.alm == alm)
+            return cudaGraphLaunch(e.exec, P->stream) == cudaSuccess ? HPX_OK : HPX_ERR_CUDA;
+    cudaStream_t user = P->stream;
+    const bool prof = P->prof;
+    P->stream = P->cap;
+    P->prof = false;
+    if (cudaStreamBeginCapture(P->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        P->stream = user;
+        P->prof = prof;
+        return HPX_ERR_CUDA;
+    }
+    const int rc = analyze_direct(P, maps, alm);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(P->cap, &graph);
+    P->stream = user;
+    P->prof = prof;
+    if (rc != HPX_OK || ec != cudaSuccess || !graph) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc != HPX_OK ? rc : HPX_ERR_CUDA;
+    }
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) return HPX_ERR_CUDA;
+    P->graphs.push_back({maps, alm, exec});
+    return cudaGraphLaunch(exec, P->stream) == cudaSuccess ? HPX_OK : HPX_ERR_CUDA;
+}
+
+}  // namespace
+
 int hpx_analyze(hpx_plan_s* P, const void* maps, void* alm) {
     if (!P || !maps || !alm) return set_err(HPX_ERR_ARG);
-    const int rc = P->precision == HPX_FP64 ? analyze_impl<double>(P, maps, alm)
-                                            : analyze_impl<float>(P, maps, alm);
+    const int rc = (P->flags & HPX_FLAG_GRAPH) ? analyze_graph(P, maps, alm) : analyze_direct(P, maps, alm);
     return set_err(rc);
 }
 
 int hpx_synthesize(hpx_plan_s* P, const void* alm, void* maps) {
     if (!P || !alm || !maps) return set_err(HPX_ERR_ARG);
+    if (P->group) return set_err(hpx::group_synthesize(P, alm, maps));
     if (P->precision == HPX_FP64) hpx::launch_adjoint<double>(P, (const double*)alm, (double*)maps, P->stream);
     else hpx::launch_adjoint<float>(P, (const float*)alm, (float*)maps, P->stream);
     if (cudaGetLastError() != cudaSuccess) return set_err(HPX_ERR_CUDA);
@@ -225,6 +306,7 @@ int hpx_synthesize(hpx_plan_s* P, const void* alm, void* maps) {
 
 int hpx_set_profiling(hpx_plan_s* P, int enable) {
     if (!P) return set_err(HPX_ERR_ARG);
+    if (P->group) return set_err(HPX_ERR_STATE);
     if (enable && !P->ev) {
         const int n = hpx_plan_s::kMaxProf * (hpx_plan_s::kStages + 1);
         P->ev = new (std::nothrow) cudaEvent_t[n];
@@ -239,6 +321,7 @@ int hpx_set_profiling(hpx_plan_s* P, int enable) {
 
 int hpx_stage_times(hpx_plan_s* P, float* ms, int n, int* ncalls) {
     if (!P || !ms || n < hpx_plan_s::kStages) return set_err(HPX_ERR_ARG);
+    if (P->group) return set_err(HPX_ERR_STATE);
     for (int k = 0; k < n; ++k) ms[k] = 0.0f;
     for (int c = 0; c < P->nprof; ++c) {
         cudaEvent_t* ev = P->ev + (size_t)c * (hpx_plan_s::kStages + 1);
@@ -256,6 +339,7 @@ int hpx_stage_times(hpx_plan_s* P, float* ms, int n, int* ncalls) {
 
 int hpx_cl(hpx_plan_s* P, const void* alm, double* cl) {
     if (!P || !alm || !cl) return set_err(HPX_ERR_ARG);
+    if (P->group) return set_err(hpx::group_cl(P, alm, cl));
     if (P->precision == HPX_FP64) hpx::launch_cl<double>(P, (const double*)alm, cl, P->stream);
     else hpx::launch_cl<float>(P, (const float*)alm, cl, P->stream);
     if (cudaGetLastError() != cudaSuccess) return set_err(HPX_ERR_CUDA);
@@ -265,6 +349,14 @@ int hpx_cl(hpx_plan_s* P, const void* alm, double* cl) {
 int hpx_sync(hpx_plan_s* P) {
     if (!P) return set_err(HPX_ERR_ARG);
     if (cudaStreamSynchronize(P->stream) != cudaSuccess) return set_err(HPX_ERR_CUDA);
+    if (P->d_status) {
+        int st = 0;
+        if (cudaMemcpy(&st, P->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return set_err(HPX_ERR_CUDA);
+        if (st != 0) {
+            cudaMemset(P->d_status, 0, sizeof(int));
+            return set_err(st);
+        }
+    }
     if (P->status != 0) return set_err(P->status);
     return set_err(HPX_OK);
 }

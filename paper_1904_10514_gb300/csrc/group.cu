@@ -1,0 +1,220 @@
+// Uneven batches: maps of different nside analysed by one plan.
+//
+// A group plan holds one uniform sub-plan per distinct nside.  The caller's
+// maps, coefficients and spectra are concatenated in batch order; a sub-plan
+// whose maps are adjacent in the batch works on the caller's arrays in place,
+// otherwise its maps are gathered into a plan-owned staging buffer before the
+// launch and its results scattered back after it (segment_copy_kernel).  All
+// launches go to the group's stream, so HPX_FLAG_GRAPH captures the whole
+// batch -- every nside -- as one CUDA graph.
+#include <algorithm>
+#include <map>
+#include <new>
+
+#include "../../include/hpx.h"
+#include "plan.h"
+
+namespace hpx {
+
+// Copies `count` segments of `seg` bytes (a multiple of 8) between a packed
+// staging array and the caller's array, whose segment for batch index idx[k]
+// starts at byte off[idx[k]].  gather: caller -> staging; else staging -> caller.
+__global__ void segment_copy_kernel(const unsigned char* __restrict__ src, unsigned char* __restrict__ dst,
+                                    const int* __restrict__ idx, const int64_t* __restrict__ off, int64_t seg,
+                                    bool gather) {
+    const int k = blockIdx.y;
+    const int64_t caller = off[idx[k]];
+    const int64_t packed = (int64_t)k * seg;
+    const uint2* s = reinterpret_cast<const uint2*>(src + (gather ? caller : packed));
+    uint2* d = reinterpret_cast<uint2*>(dst + (gather ? packed : caller));
+    const int64_t n = seg / 8;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        d[e] = s[e];
+}
+
+namespace {
+
+void seg_copy(const hpx_plan_s* P, int s, const void* src, void* dst, const int64_t* off, int64_t seg, bool gather) {
+    dim3 grid((unsigned)std::min<int64_t>((seg / 8 + 255) / 256, 1024), P->sub_count[s]);
+    segment_copy_kernel<<<grid, 256, 0, P->stream>>>((const unsigned char*)src, (unsigned char*)dst,
+                                                     P->d_idx + P->sub_first[s], off, seg, gather);
+}
+
+int64_t nalm_of(int L) { return (int64_t)(L + 1) * (L + 2) / 2; }
+
+}  // namespace
+
+hpx_plan_s* group_create(const hpx_plan_desc* d, int* err) {
+    *err = HPX_ERR_ARG;
+    const int B = d->batch;
+    const bool fp64 = d->precision == HPX_FP64;
+    int nmin = 1 << 30;
+    for (int i = 0; i < B; ++i) {
+        const int ns = d->nsides[i];
+        if (ns < 2 || (ns & (ns - 1)) || ns > (fp64 ? 1024 : 2048)) { *err = HPX_ERR_NSIDE; return nullptr; }
+        nmin = std::min(nmin, ns);
+    }
+    if (d->lmax < -1 || (d->lmax >= 0 && d->lmax > 2 * nmin)) { *err = HPX_ERR_LMAX; return nullptr; }
+    hpx_plan_s* G = new (std::nothrow) hpx_plan_s();
+    if (!G) { *err = HPX_ERR_OOM; return nullptr; }
+    G->group = true;
+    G->precision = d->precision;
+    G->flags = d->flags;
+    G->stream = nullptr;
+    cudaGetDevice(&G->device);
+    const size_t es = fp64 ? 8 : 4;
+    // per-map offsets (bytes) in the caller's concatenated arrays
+    std::vector<int64_t> mapoff(B), almoff(B), cloff(B);
+    std::map<int, std::vector<int>> byNside;
+    int64_t om = 0, oa = 0, oc = 0;
+    int Lmax_all = 0;
+    for (int i = 0; i < B; ++i) {
+        const int ns = d->nsides[i];
+        const int L = d->lmax < 0 ? 2 * ns : d->lmax;
+        Lmax_all = std::max(Lmax_all, L);
+        mapoff[i] = om * (int64_t)es;
+        almoff[i] = oa * (int64_t)es * 2;
+        cloff[i] = oc * 8;
+        om += 12LL * ns * ns;
+        oa += nalm_of(L);
+        oc += L + 1;
+        byNside[ns].push_back(i);
+    }
+    G->total_npix = om;
+    G->total_nalm = oa;
+    G->total_ncl = oc;
+    G->g = Geometry{};
+    G->g.L = Lmax_all;
+    G->g.B = B;
+    G->g.npix = om;
+    G->g.nalm = oa;
+    std::vector<int> idx;
+    bool ok = true;
+    for (auto& kv : byNside) {
+        const int ns = kv.first;
+        const std::vector<int>& maps = kv.second;
+        hpx_plan_desc sd = *d;
+        sd.nside = ns;
+        sd.batch = (int)maps.size();
+        sd.flags = d->flags & ~(unsigned)HPX_FLAG_GRAPH;
+        sd.nsides = nullptr;
+        hpx_plan_s* S = hpx_plan_ex(&sd);
+        if (!S) { *err = hpx_last_error(); ok = false; break; }
+        G->subs.push_back(S);
+        G->bytes += S->bytes;
+        G->sub_count.push_back((int)maps.size());
+        G->sub_first.push_back((int)idx.size());
+        bool adj = true;
+        for (size_t k = 1; k < maps.size(); ++k) adj = adj && maps[k] == maps[k - 1] + 1;
+        G->sub_inplace.push_back(adj ? 1 : 0);
+        G->sub_mapoff.push_back(mapoff[maps[0]]);
+        G->sub_almoff.push_back(almoff[maps[0]]);
+        G->sub_cloff.push_back(cloff[maps[0]]);
+        void *sm = nullptr, *sa = nullptr, *sc = nullptr;
+        if (!adj) {
+            const size_t nm = maps.size();
+            if (cudaMalloc(&sm, nm * S->g.npix * es) != cudaSuccess ||
+                cudaMalloc(&sa, nm * S->g.nalm * es * 2) != cudaSuccess ||
+                cudaMalloc(&sc, nm * (S->g.L + 1) * 8) != cudaSuccess) {
+                *err = HPX_ERR_OOM;
+                ok = false;
+            }
+            G->bytes += (int64_t)(nm * (S->g.npix * es + S->g.nalm * es * 2 + (S->g.L + 1) * 8));
+        }
+        G->stage_maps.push_back(sm);
+        G->stage_alm.push_back(sa);
+        G->stage_cl.push_back(sc);
+        if (!ok) break;
+        idx.insert(idx.end(), maps.begin(), maps.end());
+    }
+    if (ok) {
+        ok = cudaMalloc(&G->d_idx, idx.size() * sizeof(int)) == cudaSuccess &&
+             cudaMalloc(&G->d_mapoff, B * sizeof(int64_t)) == cudaSuccess &&
+             cudaMalloc(&G->d_almoff, B * sizeof(int64_t)) == cudaSuccess &&
+             cudaMalloc(&G->d_cloff, B * sizeof(int64_t)) == cudaSuccess;
+        if (ok) {
+            cudaMemcpy(G->d_idx, idx.data(), idx.size() * sizeof(int), cudaMemcpyHostToDevice);
+            cudaMemcpy(G->d_mapoff, mapoff.data(), B * sizeof(int64_t), cudaMemcpyHostToDevice);
+            cudaMemcpy(G->d_almoff, almoff.data(), B * sizeof(int64_t), cudaMemcpyHostToDevice);
+            cudaMemcpy(G->d_cloff, cloff.data(), B * sizeof(int64_t), cudaMemcpyHostToDevice);
+        } else {
+            *err = HPX_ERR_OOM;
+        }
+    }
+    if (!ok) {
+        group_free(G);
+        return nullptr;
+    }
+    *err = HPX_OK;
+    return G;
+}
+
+void group_free(hpx_plan_s* G) {
+    for (hpx_plan_s* S : G->subs) hpx_destroy(S);
+    for (void* q : G->stage_maps) if (q) cudaFree(q);
+    for (void* q : G->stage_alm) if (q) cudaFree(q);
+    for (void* q : G->stage_cl) if (q) cudaFree(q);
+    if (G->d_idx) cudaFree(G->d_idx);
+    if (G->d_mapoff) cudaFree(G->d_mapoff);
+    if (G->d_almoff) cudaFree(G->d_almoff);
+    if (G->d_cloff) cudaFree(G->d_cloff);
+}
+
+int group_analyze(hpx_plan_s* G, const void* maps, void* alm) {
+    for (size_t s = 0; s < G->subs.size(); ++s) {
+        hpx_plan_s* S = G->subs[s];
+        hpx_set_stream(S, G->stream);
+        const size_t es = G->precision == HPX_FP64 ? 8 : 4;
+        if (G->sub_inplace[s]) {
+            const int rc = hpx_analyze(S, (const unsigned char*)maps + G->sub_mapoff[s],
+                                       (unsigned char*)alm + G->sub_almoff[s]);
+            if (rc != HPX_OK) return rc;
+        } else {
+            seg_copy(G, (int)s, maps, G->stage_maps[s], G->d_mapoff, S->g.npix * (int64_t)es, true);
+            const int rc = hpx_analyze(S, G->stage_maps[s], G->stage_alm[s]);
+            if (rc != HPX_OK) return rc;
+            seg_copy(G, (int)s, G->stage_alm[s], alm, G->d_almoff, S->g.nalm * (int64_t)es * 2, false);
+        }
+    }
+    return cudaGetLastError() == cudaSuccess ? HPX_OK : HPX_ERR_CUDA;
+}
+
+int group_synthesize(hpx_plan_s* G, const void* alm, void* maps) {
+    for (size_t s = 0; s < G->subs.size(); ++s) {
+        hpx_plan_s* S = G->subs[s];
+        hpx_set_stream(S, G->stream);
+        const size_t es = G->precision == HPX_FP64 ? 8 : 4;
+        if (G->sub_inplace[s]) {
+            const int rc = hpx_synthesize(S, (const unsigned char*)alm + G->sub_almoff[s],
+                                          (unsigned char*)maps + G->sub_mapoff[s]);
+            if (rc != HPX_OK) return rc;
+        } else {
+            seg_copy(G, (int)s, alm, G->stage_alm[s], G->d_almoff, S->g.nalm * (int64_t)es * 2, true);
+            const int rc = hpx_synthesize(S, G->stage_alm[s], G->stage_maps[s]);
+            if (rc != HPX_OK) return rc;
+            seg_copy(G, (int)s, G->stage_maps[s], maps, G->d_mapoff, S->g.npix * (int64_t)es, false);
+        }
+    }
+    return cudaGetLastError() == cudaSuccess ? HPX_OK : HPX_ERR_CUDA;
+}
+
+int group_cl(hpx_plan_s* G, const void* alm, double* cl) {
+    for (size_t s = 0; s < G->subs.size(); ++s) {
+        hpx_plan_s* S = G->subs[s];
+        hpx_set_stream(S, G->stream);
+        const size_t es = G->precision == HPX_FP64 ? 8 : 4;
+        if (G->sub_inplace[s]) {
+            const int rc = hpx_cl(S, (const unsigned char*)alm + G->sub_almoff[s],
+                                  (double*)((unsigned char*)cl + G->sub_cloff[s]));
+            if (rc != HPX_OK) return rc;
+        } else {
+            seg_copy(G, (int)s, alm, G->stage_alm[s], G->d_almoff, S->g.nalm * (int64_t)es * 2, true);
+            const int rc = hpx_cl(S, G->stage_alm[s], (double*)G->stage_cl[s]);
+            if (rc != HPX_OK) return rc;
+            seg_copy(G, (int)s, G->stage_cl[s], cl, G->d_cloff, (S->g.L + 1) * 8, false);
+        }
+    }
+    return cudaGetLastError() == cudaSuccess ? HPX_OK : HPX_ERR_CUDA;
+}
+
+}  // namespace hpx

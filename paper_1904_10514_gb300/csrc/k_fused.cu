@@ -26,7 +26,7 @@ __global__ void __launch_bounds__(64) build_fused_kernel(const double* __restric
                                                          const int64_t* __restrict__ moff,
                                                          const int64_t* __restrict__ skOff,
                                                          const cplx<double>* __restrict__ skew, int nq, int P2,
-                                                         int L, int m_lo, int m_cnt, int ngroups,
+                                                         int ldm, int L, int m_lo, int m_cnt, int ngroups,
                                                          cplx<double>* __restrict__ scratch) {
     constexpr int KMAX = 16;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -72,27 +72,28 @@ __global__ void __launch_bounds__(64) build_fused_kernel(const double* __restric
     HPX_SUBPASS(2)
     HPX_SUBPASS(1)
 #undef HPX_SUBPASS
-    T* out = Mout + moff[(size_t)m * 2 + c] * P2;
+    T* out = Mout + moff[(size_t)m * 2 + c] * ldm;
     for (int i = 0; i < n; ++i) {
         const cplx<double> v = chain[(int64_t)i * ldc];
-        out[(size_t)i * P2 + 2 * j] = (T)v.r;
-        if (2 * j + 1 < P2) out[(size_t)i * P2 + 2 * j + 1] = (T)v.i;
+        out[(size_t)i * ldm + 2 * j] = (T)v.r;
+        if (2 * j + 1 < P2) out[(size_t)i * ldm + 2 * j + 1] = (T)v.i;
     }
 }
 
 // ---------------------------------------------------------------- apply
-namespace {
-constexpr int FR = 128;   // rows (degrees of one chain) per block
-constexpr int FC = 32;    // maps per block (complex columns)
-constexpr int FK = 16;    // k per stage
-}  // namespace
 
-// Block = one (m, c, tile of 128 rows) x 32 maps; 256 threads, each 8 rows x 2 maps.
-template <class T>
-__global__ void __launch_bounds__(256) fused_apply_kernel(const T* __restrict__ M, const int64_t* __restrict__ moff,
-                                                          const int* __restrict__ tiles,
-                                                          const cplx<T>* __restrict__ bvec, cplx<T>* __restrict__ alm,
-                                                          int P2, int p, int L, int B, int64_t nalm) {
+// Block = one (m, c, tile of 8*TR rows) x 2*TC maps; TR*TC threads, each 8 rows x 2 maps.
+// M rows are padded to ldm (a multiple of 4, zero filled) so that they load as
+// 16-byte vectors.
+template <class T, int TR, int TC>
+__global__ void __launch_bounds__(TR* TC) fused_apply_kernel(const T* __restrict__ M, const int64_t* __restrict__ moff,
+                                                             const int* __restrict__ tiles,
+                                                             const cplx<T>* __restrict__ bvec,
+                                                             cplx<T>* __restrict__ alm, int P2, int ldm, int p,
+                                                             int L, int B, int64_t nalm) {
+    constexpr int FR = 8 * TR, FC = 2 * TC, NT = TR * TC;
+    constexpr int FK = sizeof(T) == 4 ? 16 : 8;   // k per stage
+    constexpr int VA = 16 / sizeof(T);            // elements per 16-byte vector
     __shared__ __align__(16) T As[FK][FR + 4];
     __shared__ __align__(16) cplx<T> Bs[FK][FC];
     const int m = tiles[3 * blockIdx.x], c = tiles[3 * blockIdx.x + 1], i0 = tiles[3 * blockIdx.x + 2];
@@ -100,9 +101,9 @@ __global__ void __launch_bounds__(256) fused_apply_kernel(const T* __restrict__ 
     const int par = (m0 + c) & 1;
     const int nrows = chain_len(m, c, L);
     const int b0 = blockIdx.y * FC;
-    const T* A = M + moff[(size_t)m * 2 + c] * P2;
+    const T* A = M + moff[(size_t)m * 2 + c] * ldm;
     const int tid = threadIdx.x;
-    const int tr = tid & 15, tc = tid >> 4;
+    const int tr = tid % TR, tc = tid / TR;
     T accr[8][2], acci[8][2];
 #pragma unroll
     for (int r = 0; r < 8; ++r)
@@ -110,14 +111,28 @@ __global__ void __launch_bounds__(256) fused_apply_kernel(const T* __restrict__ 
         for (int q = 0; q < 2; ++q) { accr[r][q] = T(0); acci[r][q] = T(0); }
 
     for (int k0 = 0; k0 < P2; k0 += FK) {
-        // A tile: 128 rows x 16 k, stored k-major
-        for (int e = tid; e < FR * FK; e += 256) {
-            const int rr = e / FK, kk = e % FK;
-            const int i = i0 + rr, k = k0 + kk;
-            As[kk][rr] = (i < nrows && k < P2) ? A[(size_t)i * P2 + k] : T(0);
+        // A tile: FR rows x 16 k as 16-byte vectors, stored k-major
+        for (int e = tid; e < FR * (FK / VA); e += NT) {
+            const int rr = e % FR, kv = e / FR;   // a warp stores 32 consecutive rows: no bank conflicts
+            const int i = i0 + rr, k = k0 + kv * VA;
+            T v[VA];
+            if (i < nrows && k < ldm) {
+                if constexpr (sizeof(T) == 4) {
+                    const float4 q4 = *reinterpret_cast<const float4*>(A + (size_t)i * ldm + k);
+                    v[0] = q4.x; v[1] = q4.y; v[2] = q4.z; v[3] = q4.w;
+                } else {
+                    const double2 q2 = *reinterpret_cast<const double2*>(A + (size_t)i * ldm + k);
+                    v[0] = q2.x; v[1] = q2.y;
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < VA; ++q) v[q] = T(0);
+            }
+#pragma unroll
+            for (int q = 0; q < VA; ++q) As[kv * VA + q][rr] = v[q];
         }
-        // B tile: 32 maps x 16 k (each map's column is contiguous in k)
-        for (int e = tid; e < FC * FK; e += 256) {
+        // B tile: FC maps x 16 k (each map's column is contiguous in k)
+        for (int e = tid; e < FC * FK; e += NT) {
             const int cc = e / FK, kk = e % FK;
             const int b = b0 + cc, k = k0 + kk;
             Bs[kk][cc] = (b < B && k < P2) ? bvec[(((int64_t)b * (p + 1) + m) * 2 + par) * P2 + k]
@@ -154,13 +169,30 @@ __global__ void __launch_bounds__(256) fused_apply_kernel(const T* __restrict__ 
     }
 }
 
+// Rows per block of the apply kernel for a batch of B maps (the plan builds its
+// tile list with this).
+int fused_tile_rows(int B) { return B > 8 ? 128 : (B > 2 ? 256 : 512); }
+
 template <class T>
 void launch_fused(const hpx_plan_s* P, T* alm, cudaStream_t s) {
     const auto& g = P->g;
-    dim3 grid(P->fused_ntiles, (g.B + FC - 1) / FC);
-    fused_apply_kernel<T><<<grid, 256, 0, s>>>((const T*)P->fusedM, P->fusedOff, P->fusedTiles,
-                                              (const cplx<T>*)P->bvec, (cplx<T>*)alm, g.P2, g.p, g.L, g.B,
-                                              g.nalm);
+    const int ldm = P->fused_ldm;
+    if (g.B > 8) {
+        dim3 grid(P->fused_ntiles, (g.B + 31) / 32);
+        fused_apply_kernel<T, 16, 16><<<grid, 256, 0, s>>>((const T*)P->fusedM, P->fusedOff, P->fusedTiles,
+                                                           (const cplx<T>*)P->bvec, (cplx<T>*)alm, g.P2, ldm,
+                                                           g.p, g.L, g.B, g.nalm);
+    } else if (g.B > 2) {
+        dim3 grid(P->fused_ntiles, (g.B + 7) / 8);
+        fused_apply_kernel<T, 32, 4><<<grid, 128, 0, s>>>((const T*)P->fusedM, P->fusedOff, P->fusedTiles,
+                                                          (const cplx<T>*)P->bvec, (cplx<T>*)alm, g.P2, ldm,
+                                                          g.p, g.L, g.B, g.nalm);
+    } else {
+        dim3 grid(P->fused_ntiles, (g.B + 1) / 2);
+        fused_apply_kernel<T, 64, 1><<<grid, 64, 0, s>>>((const T*)P->fusedM, P->fusedOff, P->fusedTiles,
+                                                         (const cplx<T>*)P->bvec, (cplx<T>*)alm, g.P2, ldm,
+                                                         g.p, g.L, g.B, g.nalm);
+    }
 }
 
 // Builds the per-order operators of a plan (called once by hpx_plan_ex).
@@ -179,7 +211,7 @@ int build_fused(hpx_plan_s* P, const double* D64, const cplx<double>* skew64, cu
         const int nitems = m_cnt * 2 * ngroups;
         const int blocks = (nitems * 32 + 63) / 64;
         build_fused_kernel<T><<<blocks, 64, 0, s>>>(D64, (T*)P->fusedM, P->fusedOff, P->t.skOff, skew64, P->t.nq,
-                                                    g.P2, g.L, m_lo, m_cnt, ngroups, scratch);
+                                                    g.P2, P->fused_ldm, g.L, m_lo, m_cnt, ngroups, scratch);
     }
     const cudaError_t e = cudaStreamSynchronize(s);
     cudaFree(scratch);

@@ -21,10 +21,10 @@
 namespace hpx {
 
 template <class T, int E>
-__global__ void __launch_bounds__(512, 1) nufft_kernel(
-    const cplx<T>* __restrict__ Y, cplx<T>* __restrict__ bvec, const int* __restrict__ rowptr,
-    const int* __restrict__ ent, const T* __restrict__ entw, const T* __restrict__ dec,
-    const cplx<T>* __restrict__ tw, int twlen, int M, int logM, int p, int Q, int P2, int mcount) {
+__global__ void __launch_bounds__(512, (E <= 16 ? 2 : 1)) nufft_kernel(
+    const cplx<T>* __restrict__ Y, cplx<T>* __restrict__ bvec, const int* __restrict__ nstart,
+    const T* __restrict__ swts, int nsw, const T* __restrict__ dec, const cplx<T>* __restrict__ tw, int twlen, int M,
+    int logM, int p, int Q, int P2) {
     extern __shared__ unsigned char smem_raw[];
     cplx<T>* u = reinterpret_cast<cplx<T>*>(smem_raw);   // M
     cplx<T>* y = u + M + M / 16;                           // Q (after the padded grid)
@@ -35,17 +35,21 @@ __global__ void __launch_bounds__(512, 1) nufft_kernel(
     for (int r = tid; r < Q; r += nt) y[r] = col[(int64_t)r * (p + 1)];
     __syncthreads();
     const bool odd = (m & 1) != 0;
+    // gather-spread: grid point t sees the DFS nodes nstart[t] .. nstart[t]+nsw-1
+    // (cyclically; node nu <= 4 Nside is theta_nu, beyond it is the mirror of
+    // ring 8 Nside - nu, whose data carry the sign (-1)^m); M = 8 Nside nodes.
+    const int half = M >> 1;
     for (int t = tid; t < M; t += nt) {
         T ar = T(0), ai = T(0);
-        const int e1 = rowptr[t + 1];
-        for (int e = rowptr[t]; e < e1; ++e) {
-            const int code = ent[e];
-            const int r = code & ((1 << 30) - 1);
-            T w = entw[e];
-            if (odd && (code >> 30)) w = -w;
-            const cplx<T> v = y[r];
-            ar += w * v.r;
-            ai += w * v.i;
+        int nu = nstart[t];
+        for (int e = 0; e < nsw; ++e) {
+            const T w = swts[(size_t)e * M + t];
+            const bool mir = nu > half;
+            const cplx<T> v = y[mir ? M - nu : nu];
+            const T ws = (odd && mir) ? -w : w;
+            ar += ws * v.r;
+            ai += ws * v.i;
+            nu = (nu + 1 == M) ? 0 : nu + 1;
         }
         u[pad(t)] = mk<T>(ar, ai);
     }
@@ -71,9 +75,8 @@ void launch_nufft(const hpx_plan_s* P, cudaStream_t s) {
     auto kern = g.M > 16 * 512 ? nufft_kernel<T, 32> : nufft_kernel<T, 16>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     dim3 grid(g.L + 1, g.B);
-    kern<<<grid, 512, smem, s>>>((const cplx<T>*)P->Y, (cplx<T>*)P->bvec, t.rowptr, t.ent,
-                                            (const T*)t.entw, (const T*)t.dec, (const cplx<T>*)t.twid,
-                                            g.Lmax, g.M, logM, g.p, g.Q, g.P2, g.L + 1);
+    kern<<<grid, 512, smem, s>>>((const cplx<T>*)P->Y, (cplx<T>*)P->bvec, t.nstart, (const T*)t.swts, t.spreadE,
+                                 (const T*)t.dec, (const cplx<T>*)t.twid, g.Lmax, g.M, logM, g.p, g.Q, g.P2);
 }
 
 template void launch_nufft<float>(const hpx_plan_s*, cudaStream_t);

@@ -23,7 +23,7 @@ namespace hpx {
 constexpr int kRingThreads = 512;
 
 template <class T, int E>
-__global__ void __launch_bounds__(kRingThreads, 1) ring_fft_kernel(
+__global__ void __launch_bounds__(kRingThreads, (E <= 16 ? 2 : 1)) ring_fft_kernel(
     const T* __restrict__ maps, cplx<T>* __restrict__ Y, const int* __restrict__ nphi_t,
     const int* __restrict__ startN_t, const int* __restrict__ startS_t,
     const int* __restrict__ pow2_t, const int* __restrict__ logn_t, const int* __restrict__ fftL_t,

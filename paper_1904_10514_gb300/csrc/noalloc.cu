@@ -37,7 +37,7 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Offsets {
     size_t nphi, startN, startS, pow2, logn, fftL, logL, shOff, chOff, bhOff, shift, chirp, bhat, twid,
-        poleN, poleS, polew, rowptr, ent, entw, dec, D, angOff, ang, skOff, skew;
+        poleN, poleS, polew, rowptr, ent, entw, dec, D, angOff, ang, skOff, skew, nstart, swts;
     size_t Y, bvec;
     int npole;
 };
@@ -46,6 +46,7 @@ struct DevState {
     unsigned char* base = nullptr;   // device address of g_noalloc_scratch
     int nside = -1, lmax = -1;       // size whose tables the array currently holds
     int nq = 0;
+    int spreadE = 0;
     Offsets off;
     hpx::Geometry geo;
 };
@@ -114,6 +115,7 @@ extern "C" int hpx_analyze_noalloc(int nside, int lmax, const float* maps, float
         o.rowptr = img.vec(tb.rowptr); o.ent = img.vec(tb.ent); o.entw = img.real(tb.entw);
         o.dec = img.real(tb.dec); o.D = img.real(tb.D); o.angOff = img.vec(tb.angOff); o.ang = img.real(tb.ang);
         o.skOff = img.vec(tb.skOff); o.skew = img.real(tb.skew); st.nq = tb.nq;
+        o.nstart = img.vec(tb.nstart); o.swts = img.real(tb.swts); st.spreadE = tb.spreadE;
         const size_t ySize = (size_t)tb.Q * (tb.p + 1) * 8;    // step-1 coefficients (complex FP32)
         const size_t bSize = (size_t)(tb.p + 1) * 2 * tb.P2 * 8;
         o.Y = align256(img.bytes.size());
@@ -146,6 +148,7 @@ extern "C" int hpx_analyze_noalloc(int nside, int lmax, const float* maps, float
     t.ent = (int*)(b + o.ent); t.entw = b + o.entw; t.dec = b + o.dec; t.D = b + o.D;
     t.angOff = (int64_t*)(b + o.angOff); t.ang = b + o.ang;
     t.skOff = (int64_t*)(b + o.skOff); t.skew = b + o.skew; t.nq = st.nq;
+    t.nstart = (int*)(b + o.nstart); t.swts = b + o.swts; t.spreadE = st.spreadE;
     P.g = st.geo;
     P.precision = HPX_FP32;
     P.device = dev;

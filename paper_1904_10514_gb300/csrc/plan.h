@@ -2,7 +2,9 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <vector>
 
+#include "../../include/hpx.h"
 #include "common.cuh"
 
 struct hpx_plan_s;
@@ -21,6 +23,9 @@ struct DevTables {
     int npole = 0;
     int *rowptr = nullptr, *ent = nullptr;
     void *entw = nullptr, *dec = nullptr;   // T
+    int* nstart = nullptr;                  // dense spreading table: first node per grid point
+    void* swts = nullptr;                   // T [spreadE][M]
+    int spreadE = 0;
     void* D = nullptr;                      // T [2][2][P2][P2]
     int64_t* angOff = nullptr;
     void* ang = nullptr;                    // cplx<T> (cos, sin)
@@ -63,6 +68,31 @@ struct hpx_plan_s {
     int64_t* fusedOff = nullptr;   // first row of (m, c)
     int* fusedTiles = nullptr;     // (m, c, first row) per block of the apply kernel
     int fused_ntiles = 0;
+    int fused_ldm = 0;             // row stride of M (P2 rounded up to a multiple of 4)
+    bool use_tc = false;           // FP32: apply M with tcgen05 3xTF32 MMAs
+    int* d_status = nullptr;       // device status word (bounded waits that timed out)
+
+    // uneven batches (group plans): one uniform sub-plan per distinct nside
+    bool group = false;
+    std::vector<hpx_plan_s*> subs;
+    std::vector<int> sub_count, sub_first;   // maps per sub-plan, first entry in d_idx
+    std::vector<int> sub_inplace;            // 1: the sub-plan's maps are adjacent in the batch
+    std::vector<int64_t> sub_mapoff, sub_almoff, sub_cloff;   // byte offsets of an in-place run
+    int* d_idx = nullptr;                    // batch index of every map, grouped by sub-plan
+    int64_t* d_mapoff = nullptr;             // byte offset of map i in the caller's arrays
+    int64_t* d_almoff = nullptr;
+    int64_t* d_cloff = nullptr;
+    std::vector<void*> stage_maps, stage_alm, stage_cl;   // per sub-plan staging (gathered runs)
+    int64_t total_npix = 0, total_nalm = 0, total_ncl = 0;
+
+    // CUDA graphs of hpx_analyze (HPX_FLAG_GRAPH)
+    cudaStream_t cap = nullptr;
+    struct GraphEntry {
+        const void* maps;
+        void* alm;
+        cudaGraphExec_t exec;
+    };
+    std::vector<GraphEntry> graphs;
 };
 
 namespace hpx {
@@ -72,9 +102,17 @@ template <class T> void launch_poles(const hpx_plan_s* P, const T* maps, cudaStr
 template <class T> void launch_nufft(const hpx_plan_s* P, cudaStream_t s);
 template <class T> void launch_dense(const hpx_plan_s* P, cudaStream_t s);
 template <class T> void launch_rot(const hpx_plan_s* P, T* alm, cudaStream_t s);
+int fused_tile_rows(int B);
 template <class T> void launch_fused(const hpx_plan_s* P, T* alm, cudaStream_t s);
+void launch_fused_tc(const hpx_plan_s* P, float* alm, cudaStream_t s);
 template <class T> int build_fused(hpx_plan_s* P, const double* D64, const cplx<double>* skew64, cudaStream_t s);
 template <class T> void launch_adjoint(const hpx_plan_s* P, const T* alm, T* maps, cudaStream_t s);
+// uneven batches (group.cu)
+hpx_plan_s* group_create(const hpx_plan_desc* d, int* err);
+int group_analyze(hpx_plan_s* P, const void* maps, void* alm);
+int group_synthesize(hpx_plan_s* P, const void* alm, void* maps);
+int group_cl(hpx_plan_s* P, const void* alm, double* cl);
+void group_free(hpx_plan_s* P);
 template <class T> void launch_cl(const hpx_plan_s* P, const T* alm, double* cl, cudaStream_t s);
 
 }  // namespace hpx

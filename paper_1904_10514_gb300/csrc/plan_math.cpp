@@ -321,6 +321,36 @@ std::string build_tables(int nside, int lmax, bool fp64, PlanTables& t) {
                 t.ent[t.rowptr[i] + e] = rows[i][e].first;
                 t.entw[t.rowptr[i] + e] = rows[i][e].second;
             }
+        // The same weights as a dense "first node + E weights" table: the DFS nodes
+        // nu = 0 .. 8 Nside - 1 (nu <= 4 Nside: theta_nu; beyond: 2 pi - theta_{8 Nside - nu})
+        // are sorted, so the nodes seen by one grid point form a cyclic run.
+        {
+            const int NN = 8 * ns;
+            int E = 0;
+            for (int i = 0; i < M; ++i) E = std::max(E, (int)rows[i].size());
+            E = (E + 1) & ~1;
+            t.spreadE = E;
+            t.nstart.assign(M, 0);
+            t.swts.assign((size_t)E * M, 0.0);
+            for (int i = 0; i < M; ++i) {
+                std::vector<std::pair<int, double>> nu;
+                for (const auto& e : rows[i]) {
+                    const int r = e.first & ((1 << 30) - 1);
+                    nu.push_back({(e.first >> 30) ? NN - r : r, e.second});
+                }
+                if (nu.empty()) continue;
+                std::sort(nu.begin(), nu.end());
+                int start = nu.front().first;
+                for (size_t k = 1; k < nu.size(); ++k)   // a wrap-around run starts after the gap
+                    if (nu[k].first != nu[k - 1].first + 1) start = nu[k].first;
+                t.nstart[i] = start;
+                for (const auto& e : nu) {
+                    const int off = ((e.first - start) % NN + NN) % NN;
+                    if (off >= E) return "NUFFT spreading run is not contiguous";
+                    t.swts[(size_t)off * M + i] = e.second;
+                }
+            }
+        }
         // the same entries grouped by latitude node (for the transposed NUFFT)
         std::vector<std::vector<std::pair<int, double>>> byNode(Q);
         for (int i = 0; i < M; ++i)

@@ -36,6 +36,9 @@ struct PlanTables {
     std::vector<int> ent;        // node index r | (mirrored << 30)
     std::vector<double> entw;    // kernel weight
     std::vector<double> dec;     // h / Phi(j), j = 0..p (deconvolution)
+    int spreadE = 0;             // weights per grid point in the dense spreading table
+    std::vector<int> nstart;     // first DFS node seen by grid point t (cyclic run of spreadE)
+    std::vector<double> swts;    // [spreadE][M] weights, zero past the end of a run
 
     // ---- latitude least squares + Chebyshev -> order-0/1 Legendre (Sec. 3.2.2, 3.3)
     int P2 = 0;                  // p/2 + 1

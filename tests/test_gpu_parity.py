@@ -140,3 +140,50 @@ def test_bench_workload_sampled(hp):
             l = np.arange(max(m, 2), L + 1)
             d = np.abs(got[m][l - m] - ref[m][0][l - m]) / norms[l]
             assert d.max() < TOL["fp32"], (b, m, d.max())
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("graph", [False, True], ids=["eager", "graph"])
+def test_uneven_batch(hp, prec, graph):
+    """Maps of different nside in one plan (concatenated layout), gathered
+    (interleaved nsides) and in place (adjacent runs), optionally replayed as
+    one CUDA graph; every map against the oracle."""
+    nsides = [8, 4, 16, 8, 32, 4, 4, 16]
+    maps = []
+    for k, ns in enumerate(nsides):
+        mp, _ = skies.small_powerlaw_maps(ns, 1, seed=300 + k, alpha=2.0, noise=1e-3)
+        maps.append(mp[0].astype(np.float32).astype(np.float64) if prec == "fp32" else mp[0])
+    plan = hp.Plan(nsides=nsides, precision=prec, graph=graph)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    x = torch.as_tensor(np.concatenate(maps), dtype=dt, device="cuda")
+    for rep in range(2):            # the second call replays the captured graph
+        alm = plan.analyze(x)
+        cl = plan.cl(alm)
+        plan.sync()
+    a = alm.cpu().numpy().astype(np.complex128)
+    c = cl.cpu().numpy()
+    oa = oc = 0
+    for ns, mp in zip(nsides, maps):
+        L = 2 * ns
+        na = (L + 1) * (L + 2) // 2
+        ref = hp2sph.analyze(mp, ns, L)
+        assert per_l_error(a[oa:oa + na], ref, L).max() < TOL[prec]
+        clr = hp2sph.cl(ref, L)
+        assert (np.abs(c[oc:oc + L + 1] - clr) / clr)[2:].max() < 2.5 * TOL[prec]
+        oa += na
+        oc += L + 1
+    assert oa == plan.nalm and oc == plan.ncl
+
+
+def test_graph_uniform_plan_matches_eager(hp):
+    ns = 32
+    maps, _ = skies.small_powerlaw_maps(ns, 4, seed=41)
+    x = torch.as_tensor(maps.astype(np.float32), device="cuda")
+    eager = hp.Plan(ns, -1, 4, "fp32").analyze(x)
+    gp = hp.Plan(ns, -1, 4, "fp32", graph=True)
+    out1 = gp.analyze(x)
+    out2 = torch.empty_like(out1)
+    gp.analyze(x, out=out2)          # new output pointer: a second capture
+    gp.analyze(x, out=out1)          # replay of the first graph
+    torch.cuda.synchronize()
+    assert torch.equal(eager, out1) and torch.equal(eager, out2)
