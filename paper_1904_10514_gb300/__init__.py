@@ -35,6 +35,7 @@ EXPORTS = ["hpx_plan", "hpx_plan_ex", "hpx_set_stream", "hpx_analyze", "hpx_synt
            "hpx_analyze_noalloc", "hpx_plan_flags"]
 HPX_FLAG_SWEEPS = 1
 HPX_FLAG_GRAPH = 2
+HPX_FLAG_SIMT = 4
 HPX_NOALLOC_MAX_NSIDE = 128
 HPX_NSTAGES = 5
 STAGES = ["ring_fft", "poles", "nufft", "lat_solve", "rot_sweep"]          # HPX_FLAG_SWEEPS plans
@@ -172,7 +173,8 @@ def n_alm(lmax):
 class Plan:
     """Owns one C plan; tensors must live on the plan's CUDA device."""
 
-    def __init__(self, nside=None, lmax=-1, batch=1, precision="fp32", sweeps=False, graph=False, nsides=None):
+    def __init__(self, nside=None, lmax=-1, batch=1, precision="fp32", sweeps=False, graph=False, nsides=None,
+                 simt=False):
         """Uniform batch (nside, batch) or uneven batch (nsides = nside of every map;
         maps, alm and C_l are then 1-D tensors holding the maps concatenated)."""
         import torch
@@ -182,7 +184,7 @@ class Plan:
         self.batch = len(self.nsides) if self.nsides is not None else int(batch)
         self.precision = HPX_FP64 if precision in ("fp64", "float64", HPX_FP64) else HPX_FP32
         self.device = torch.device("cuda", torch.cuda.current_device())
-        flags = (HPX_FLAG_SWEEPS if sweeps else 0) | (HPX_FLAG_GRAPH if graph else 0)
+        flags = (HPX_FLAG_SWEEPS if sweeps else 0) | (HPX_FLAG_GRAPH if graph else 0) | (HPX_FLAG_SIMT if simt else 0)
         h = hpx_plan_ex(self.nside, lmax, self.batch, self.precision, flags, self.nsides)
         if not h:
             raise HpxError(hpx_last_error(), "hpx_plan_ex")

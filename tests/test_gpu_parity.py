@@ -27,9 +27,9 @@ def hp():
     return hp
 
 
-def _run(hp, maps, nside, lmax, prec, sweeps=False):
+def _run(hp, maps, nside, lmax, prec, sweeps=False, simt=False):
     B = maps.shape[0]
-    plan = hp.Plan(nside, lmax, B, prec, sweeps=sweeps)
+    plan = hp.Plan(nside, lmax, B, prec, sweeps=sweeps, simt=simt)
     assert bool(plan.flags & hp.HPX_FLAG_SWEEPS) == sweeps
     dt = torch.float64 if prec == "fp64" else torch.float32
     x = torch.as_tensor(maps, dtype=dt, device="cuda")
@@ -39,15 +39,19 @@ def _run(hp, maps, nside, lmax, prec, sweeps=False):
     return alm.cpu().numpy().astype(np.complex128), cl.cpu().numpy(), plan
 
 
-@pytest.mark.parametrize("sweeps", [False, True], ids=["fused", "sweeps"])
+@pytest.mark.parametrize("path", ["fused", "sweeps", "simt"])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 @pytest.mark.parametrize("nside,lmax,B", [(2, 4, 3), (4, 8, 3), (4, 5, 3), (8, 16, 3), (16, 32, 3), (16, 29, 17),
-                                          (32, 64, 3), (64, 128, 33)])
-def test_parity_full(hp, prec, nside, lmax, B, sweeps):
+                                          (32, 64, 3), (64, 128, 33), (128, 256, 20)])
+def test_parity_full(hp, prec, nside, lmax, B, path):
+    """fused: per-order operators (tensor cores for FP32 batches of 9+ maps);
+    simt: the same on the FP32 pipes; sweeps: D and the Givens sweeps at run time."""
+    if path == "simt" and (prec == "fp64" or B <= 8):
+        pytest.skip("the tensor-core variant only exists for FP32 batches of 9+ maps")
     maps, _ = skies.small_powerlaw_maps(nside, B, seed=100 + nside, alpha=2.0, noise=1e-3, lmax=2 * nside)
     if prec == "fp32":
         maps = maps.astype(np.float32).astype(np.float64)   # the oracle sees the same inputs
-    a, cl, _ = _run(hp, maps, nside, lmax, prec, sweeps)
+    a, cl, _ = _run(hp, maps, nside, lmax, prec, path == "sweeps", path == "simt")
     ref = hp2sph.analyze(maps, nside, lmax)
     for b in range(maps.shape[0]):
         e = per_l_error(a[b], ref[b], lmax)
