@@ -58,7 +58,7 @@ void free_plan(hpx_plan_s* P) {
     void* ptrs[] = {t.nphi, t.startN, t.startS, t.pow2, t.logn, t.fftL, t.logL, t.shOff, t.chOff,
                     t.bhOff, t.shift, t.chirp, t.bhat, t.twid, t.poleN, t.poleS, t.polew, t.rowptr,
                     t.ent, t.entw, t.dec, t.D, t.angOff, t.ang, t.skOff, t.skew, t.skewT, t.nrowptr, t.nent, t.nentw, t.nstart, t.swts, P->Y, P->bvec,
-                    P->fusedM, P->fusedOff, P->fusedTiles, P->d_status};
+                    P->fusedM, P->fusedOff, P->fusedTiles, P->tcOff, P->tcFirst, P->d_status};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     if (P->ev) {
@@ -200,7 +200,23 @@ hpx_plan_s* hpx_plan_ex(const hpx_plan_desc* d) {
                 for (int i0 = 0; i0 < n; i0 += rows) { tiles.push_back(m); tiles.push_back(c); tiles.push_back(i0); }
             }
         P->fused_ldm = (g.P2 + 3) / 4 * 4;
-        const size_t mBytes = (size_t)off.back() * P->fused_ldm * (fp64 ? 8 : 4);
+        size_t mBytes = (size_t)off.back() * P->fused_ldm * (fp64 ? 8 : 4);
+        P->use_tc = !fp64 && g.B > 8 && !(d->flags & HPX_FLAG_SIMT);
+        std::vector<int64_t> tcOff;
+        std::vector<int> tcFirst;
+        if (P->use_tc) {   // tiles of 128 rows, K-chunks of 32 in the MMA's layout
+            const int64_t nch = (g.P2 + 31) / 32;
+            int64_t o = 0;
+            tcFirst.assign((size_t)(L + 1) * 2, 0);
+            for (size_t q = 0; q < tiles.size(); q += 3) {
+                const int m = tiles[q], c = tiles[q + 1], i0 = tiles[q + 2];
+                if (i0 == 0) tcFirst[(size_t)m * 2 + c] = (int)(q / 3);
+                const int rows = std::min(128, hpx::chain_len(m, c, L) - i0);
+                tcOff.push_back(o);
+                o += nch * ((rows + 7) & ~7) * 32;
+            }
+            mBytes = (size_t)o * 4;
+        }
         size_t freeB = 0, totalB = 0;
         cudaMemGetInfo(&freeB, &totalB);
         if (mBytes + ((size_t)1 << 30) < freeB && cudaMalloc(&P->fusedM, mBytes) == cudaSuccess) {
@@ -209,7 +225,10 @@ hpx_plan_s* hpx_plan_ex(const hpx_plan_desc* d) {
             P->fusedOff = up.vec(off);
             P->fusedTiles = up.vec(tiles);
             P->fused_ntiles = (int)(tiles.size() / 3);
-            P->use_tc = !fp64 && g.B > 8 && !(d->flags & HPX_FLAG_SIMT);
+            if (P->use_tc) {
+                P->tcOff = up.vec(tcOff);
+                P->tcFirst = up.vec(tcFirst);
+            }
             double* D64 = (double*)t.D;
             hpx::cplx<double>* sk64 = (hpx::cplx<double>*)t.skew;
             if (!fp64) { D64 = up.vec(tb.D); sk64 = (hpx::cplx<double>*)up.vec(tb.skew); }
@@ -349,14 +368,19 @@ int hpx_cl(hpx_plan_s* P, const void* alm, double* cl) {
 int hpx_sync(hpx_plan_s* P) {
     if (!P) return set_err(HPX_ERR_ARG);
     if (cudaStreamSynchronize(P->stream) != cudaSuccess) return set_err(HPX_ERR_CUDA);
-    if (P->d_status) {
+    // device status words: the plan's own, or those of a group plan's sub-plans
+    int first = HPX_OK;
+    std::vector<hpx_plan_s*> own{P};
+    for (hpx_plan_s* Q : (P->group ? P->subs : own)) {
+        if (!Q->d_status) continue;
         int st = 0;
-        if (cudaMemcpy(&st, P->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return set_err(HPX_ERR_CUDA);
+        if (cudaMemcpy(&st, Q->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return set_err(HPX_ERR_CUDA);
         if (st != 0) {
-            cudaMemset(P->d_status, 0, sizeof(int));
-            return set_err(st);
+            cudaMemset(Q->d_status, 0, sizeof(int));
+            if (first == HPX_OK) first = st;
         }
     }
+    if (first != HPX_OK) return set_err(first);
     if (P->status != 0) return set_err(P->status);
     return set_err(HPX_OK);
 }

@@ -27,7 +27,9 @@ __global__ void __launch_bounds__(64) build_fused_kernel(const double* __restric
                                                          const int64_t* __restrict__ skOff,
                                                          const cplx<double>* __restrict__ skew, int nq, int P2,
                                                          int ldm, int L, int m_lo, int m_cnt, int ngroups,
-                                                         cplx<double>* __restrict__ scratch) {
+                                                         cplx<double>* __restrict__ scratch,
+                                                         const int64_t* __restrict__ tcOff,
+                                                         const int* __restrict__ tcFirst) {
     constexpr int KMAX = 16;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
@@ -72,6 +74,16 @@ __global__ void __launch_bounds__(64) build_fused_kernel(const double* __restric
     HPX_SUBPASS(2)
     HPX_SUBPASS(1)
 #undef HPX_SUBPASS
+    if (tcOff) {   // tensor-core layout (FP32 plans)
+        for (int i = 0; i < n; ++i) {
+            const cplx<double> v = chain[(int64_t)i * ldc];
+            const int rp = (min(128, n - (i & ~127)) + 7) & ~7;
+            T* out = Mout + tcOff[tcFirst[m * 2 + c] + (i >> 7)];
+            out[tc_elem(rp, i & 127, 2 * j)] = (T)v.r;
+            if (2 * j + 1 < P2) out[tc_elem(rp, i & 127, 2 * j + 1)] = (T)v.i;
+        }
+        return;
+    }
     T* out = Mout + moff[(size_t)m * 2 + c] * ldm;
     for (int i = 0; i < n; ++i) {
         const cplx<double> v = chain[(int64_t)i * ldc];
@@ -211,7 +223,8 @@ int build_fused(hpx_plan_s* P, const double* D64, const cplx<double>* skew64, cu
         const int nitems = m_cnt * 2 * ngroups;
         const int blocks = (nitems * 32 + 63) / 64;
         build_fused_kernel<T><<<blocks, 64, 0, s>>>(D64, (T*)P->fusedM, P->fusedOff, P->t.skOff, skew64, P->t.nq,
-                                                    g.P2, P->fused_ldm, g.L, m_lo, m_cnt, ngroups, scratch);
+                                                    g.P2, P->fused_ldm, g.L, m_lo, m_cnt, ngroups, scratch,
+                                                    P->use_tc ? P->tcOff : nullptr, P->tcFirst);
     }
     const cudaError_t e = cudaStreamSynchronize(s);
     cudaFree(scratch);

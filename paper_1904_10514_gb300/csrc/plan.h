@@ -70,6 +70,11 @@ struct hpx_plan_s {
     int fused_ntiles = 0;
     int fused_ldm = 0;             // row stride of M (P2 rounded up to a multiple of 4)
     bool use_tc = false;           // FP32: apply M with tcgen05 3xTF32 MMAs
+    // tensor-core layout of M (use_tc): tile t (128 rows of one chain, rows
+    // padded to a multiple of 8 = rp) is stored as consecutive K-chunks of
+    // rp x 32 floats in the MMA's core-matrix order, from float offset tcOff[t]
+    int64_t* tcOff = nullptr;
+    int* tcFirst = nullptr;        // first tile of (m, c)
     int* d_status = nullptr;       // device status word (bounded waits that timed out)
 
     // uneven batches (group plans): one uniform sub-plan per distinct nside
@@ -106,6 +111,11 @@ int fused_tile_rows(int B);
 template <class T> void launch_fused(const hpx_plan_s* P, T* alm, cudaStream_t s);
 void launch_fused_tc(const hpx_plan_s* P, float* alm, cudaStream_t s);
 template <class T> int build_fused(hpx_plan_s* P, const double* D64, const cplx<double>* skew64, cudaStream_t s);
+// float offset of element (row r of a tile with rp rows, column k) in the
+// tensor-core layout of M, relative to the tile's first chunk
+__host__ __device__ inline int64_t tc_elem(int rp, int r, int k) {
+    return (int64_t)(k >> 5) * rp * 32 + (r >> 3) * 256 + ((k & 31) >> 2) * 32 + (r & 7) * 4 + (k & 3);
+}
 template <class T> void launch_adjoint(const hpx_plan_s* P, const T* alm, T* maps, cudaStream_t s);
 // uneven batches (group.cu)
 hpx_plan_s* group_create(const hpx_plan_desc* d, int* err);
