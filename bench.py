@@ -74,11 +74,15 @@ def stage_work(ns, L, B, es=8):
     return {
         "ring_fft": ("hbm", B * (npix * es // 2 + Q * (p + 1) * es)),
         "poles": ("hbm", B * 2 * 36 * 4),
-        "nufft": ("hbm", B * (L + 1) * (Q * es + 2 * P2 * es)),
+        # half-grid spreading: read the L+1 used columns of Y, write U (M/2 + 1 per column)
+        "spread": ("hbm", B * (L + 1) * (Q * es + (4 * ns + 1) * es)),
+        # grid FFT: read U, write the right-hand sides
+        "lat_fft": ("hbm", B * (L + 1) * ((4 * ns + 1) * es + 2 * P2 * es)),
         "lat_solve": ("alu", B * dense),
         "rot_sweep": ("alu", B * rotation_count(L) * 12),
-        # per-order operators: n_alm x P2 real matrix entries, each applied to B complex columns
-        "fused_fsht": ("alu", B * nalm * P2 * 4),
+        # per-order operators on the tensor cores: read M (n_alm x P2 FP32 entries, once per
+        # launch for up to 32 maps) and the right-hand sides, write the coefficients
+        "fused_fsht": ("hbm", ((B + 31) // 32) * nalm * P2 * 4 + B * (L + 1) * 2 * P2 * es + B * nalm * es),
         "unused": ("alu", 0),
     }
 

@@ -140,12 +140,13 @@ int hpx_plan_flags(const hpx_plan_s* plan);
 
 /* Stage timing for profiling.  With profiling enabled (enable = 1) every
  * hpx_analyze records CUDA events on the plan's stream around each of its
- * kernels (ring FFT, poles, latitude NUFFT, latitude operator, rotation sweeps;
- * up to 256 calls are kept).  hpx_stage_times waits for those events, writes
+ * kernels (ring FFT, poles, NUFFT spreading, NUFFT grid FFT, then either the
+ * per-order operators and an empty stage, or with HPX_FLAG_SWEEPS the latitude
+ * operator D and the rotation sweeps; up to 256 calls are kept).  hpx_stage_times waits for those events, writes
  * the summed device time of each stage in milliseconds to ms[0..n-1]
  * (n >= HPX_NSTAGES), sets *ncalls to the number of calls summed, and clears
  * the record. */
-#define HPX_NSTAGES 5
+#define HPX_NSTAGES 6
 int hpx_set_profiling(hpx_plan_s* plan, int enable);
 int hpx_stage_times(hpx_plan_s* plan, float* ms, int n, int* ncalls);
 

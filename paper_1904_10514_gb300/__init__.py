@@ -37,9 +37,9 @@ HPX_FLAG_SWEEPS = 1
 HPX_FLAG_GRAPH = 2
 HPX_FLAG_SIMT = 4
 HPX_NOALLOC_MAX_NSIDE = 128
-HPX_NSTAGES = 5
-STAGES = ["ring_fft", "poles", "nufft", "lat_solve", "rot_sweep"]          # HPX_FLAG_SWEEPS plans
-STAGES_FUSED = ["ring_fft", "poles", "nufft", "fused_fsht", "unused"]     # per-order operators
+HPX_NSTAGES = 6
+STAGES = ["ring_fft", "poles", "spread", "lat_fft", "lat_solve", "rot_sweep"]   # HPX_FLAG_SWEEPS plans
+STAGES_FUSED = ["ring_fft", "poles", "spread", "lat_fft", "fused_fsht", "unused"]   # per-order operators
 
 
 class hpx_plan_desc(ctypes.Structure):

@@ -57,7 +57,7 @@ void free_plan(hpx_plan_s* P) {
     auto& t = P->t;
     void* ptrs[] = {t.nphi, t.startN, t.startS, t.pow2, t.logn, t.fftL, t.logL, t.shOff, t.chOff,
                     t.bhOff, t.shift, t.chirp, t.bhat, t.twid, t.poleN, t.poleS, t.polew, t.rowptr,
-                    t.ent, t.entw, t.dec, t.D, t.angOff, t.ang, t.skOff, t.skew, t.skewT, t.nrowptr, t.nent, t.nentw, t.nstart, t.swts, P->Y, P->bvec,
+                    t.ent, t.entw, t.dec, t.D, t.angOff, t.ang, t.skOff, t.skew, t.skewT, t.nrowptr, t.nent, t.nentw, t.nstart, t.swts, t.hstart, t.hwts, P->Y, P->U, P->bvec,
                     P->fusedM, P->fusedOff, P->fusedTiles, P->tcOff, P->tcFirst, P->d_status};
     for (void* q : ptrs)
         if (q) cudaFree(q);
@@ -78,8 +78,10 @@ int analyze_impl(hpx_plan_s* P, const void* maps, void* alm) {
     if (ev) cudaEventRecord(ev[1], s);
     hpx::launch_poles<T>(P, (const T*)maps, s);
     if (ev) cudaEventRecord(ev[2], s);
-    hpx::launch_nufft<T>(P, s);
+    hpx::launch_spread<T>(P, s);
     if (ev) cudaEventRecord(ev[3], s);
+    hpx::launch_lat_fft<T>(P, s);
+    if (ev) cudaEventRecord(ev[4], s);
     if (P->fusedM) {
         if constexpr (sizeof(T) == 4) {
             if (P->use_tc) hpx::launch_fused_tc(P, (float*)alm, s);
@@ -87,13 +89,13 @@ int analyze_impl(hpx_plan_s* P, const void* maps, void* alm) {
         } else {
             hpx::launch_fused<T>(P, (T*)alm, s);
         }
-        if (ev) cudaEventRecord(ev[4], s);
+        if (ev) cudaEventRecord(ev[5], s);
     } else {
         hpx::launch_dense<T>(P, s);
-        if (ev) cudaEventRecord(ev[4], s);
+        if (ev) cudaEventRecord(ev[5], s);
         hpx::launch_rot<T>(P, (T*)alm, s);
     }
-    if (ev) cudaEventRecord(ev[5], s);
+    if (ev) cudaEventRecord(ev[6], s);
     if (cudaGetLastError() != cudaSuccess) return HPX_ERR_CUDA;
     return HPX_OK;
 }
@@ -166,6 +168,8 @@ hpx_plan_s* hpx_plan_ex(const hpx_plan_desc* d) {
     t.rowptr = up.vec(tb.rowptr); t.ent = up.vec(tb.ent);
     t.entw = up.real(tb.entw, fp64); t.dec = up.real(tb.dec, fp64);
     t.nstart = up.vec(tb.nstart); t.swts = up.real(tb.swts, fp64); t.spreadE = tb.spreadE;
+    t.hstart = up.vec(tb.hstart); t.hwts = up.real(tb.hwts, fp64); t.spreadH = tb.spreadH;
+    t.spreadRows = tb.spreadRows;
     t.D = up.real(tb.D, fp64);
     t.angOff = up.vec(tb.angOff); t.ang = up.real(tb.ang, fp64);
     t.skOff = up.vec(tb.skOff); t.skew = up.real(tb.skew, fp64); t.nq = tb.nq;
@@ -179,7 +183,10 @@ hpx_plan_s* hpx_plan_ex(const hpx_plan_desc* d) {
     if (cudaMalloc(&P->Y, std::max(ySize, bSize)) != cudaSuccess) { free_plan(P); set_err(HPX_ERR_OOM); return nullptr; }
     if (cudaMalloc(&P->bvec, bSize) != cudaSuccess) { free_plan(P); set_err(HPX_ERR_OOM); return nullptr; }
     P->beta = P->Y;   // Y is dead once the NUFFT has read it
-    P->bytes += (int64_t)(std::max(ySize, bSize) + bSize);
+    P->ldu = (g.M / 2 + 2) & ~1;
+    const size_t uSize = (size_t)g.B * (g.L + 1) * P->ldu * es;
+    if (cudaMalloc(&P->U, uSize) != cudaSuccess) { free_plan(P); set_err(HPX_ERR_OOM); return nullptr; }
+    P->bytes += (int64_t)(std::max(ySize, bSize) + bSize + uSize);
     P->flags = d->flags;
     if (cudaMalloc(&P->d_status, sizeof(int)) != cudaSuccess) { free_plan(P); set_err(HPX_ERR_OOM); return nullptr; }
     cudaMemset(P->d_status, 0, sizeof(int));

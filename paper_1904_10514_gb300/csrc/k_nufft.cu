@@ -16,6 +16,9 @@
 //     even m:  b_j = sum_r w_r y_r cos(j theta_r)          = B_j
 //     odd m:   b_j = sum_{interior r} y_r sin(j theta_r)   = (i/2) B_j
 // stored as bvec[b][m][j & 1][j >> 1].
+//
+// nufft_kernel does the whole step per column (used by the allocation-free
+// entry point); plans run it as spread_kernel + lat_fft_kernel below.
 #include "plan.h"
 
 namespace hpx {
@@ -64,6 +67,120 @@ __global__ void __launch_bounds__(512, (E <= 16 ? 2 : 1)) nufft_kernel(
     // the odd-parity block has one slot fewer (j = p + 1 would be index p/2)
     if (tid == 0) out[P2 + (P2 - 1)] = mk<T>(T(0), T(0));
 }
+
+// ---------------------------------------------------------------------------
+// The same step as two kernels (the analysis path of plans):
+//
+// spread_kernel: the grid values obey u[M - t] = (-1)^m u[t], so only the half
+// grid t = 0..M/2 is spread, with every mirrored node folded into its latitude
+// node (weights hwts, one per parity of m).  A block takes 32 grid points x 32
+// consecutive orders of one map: the ring coefficients of the latitude nodes it
+// needs are read row by row (32 orders = 256 contiguous bytes), the 12 or so
+// taps per grid point are summed from shared memory, and the 32 x 32 results
+// are written transposed, as 32 contiguous half-grid segments of U[b][m][t].
+template <class T>
+__global__ void __launch_bounds__(256) spread_kernel(const cplx<T>* __restrict__ Y, cplx<T>* __restrict__ U,
+                                                     const int* __restrict__ hstart, const T* __restrict__ hwts,
+                                                     int E, int H, int p, int Q, int L, int ldu) {
+    extern __shared__ unsigned char smem_raw[];
+    cplx<T>* out = reinterpret_cast<cplx<T>*>(smem_raw);   // [32 orders][33]
+    cplx<T>* ys = out + 32 * 33;                           // [rows][32 orders]
+    const int t0 = blockIdx.x * 32, m0 = blockIdx.y * 32, b = blockIdx.z;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int R0 = hstart[t0];
+    const int nr = hstart[min(t0 + 31, H)] + E - R0;
+    const cplx<T>* yb = Y + (int64_t)b * Q * (p + 1);
+    for (int idx = tid; idx < nr * 32; idx += 256) {
+        const int r = idx >> 5, ml = idx & 31;
+        const int m = m0 + ml;
+        ys[idx] = (m <= L) ? yb[(int64_t)(R0 + r) * (p + 1) + m] : mk<T>(T(0), T(0));
+    }
+    __syncthreads();
+    const int odd = (m0 + lane) & 1;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int tl = 4 * warp + j, t = t0 + tl;
+        T ar = T(0), ai = T(0);
+        if (t <= H) {
+            const cplx<T>* yr = ys + (hstart[t] - R0) * 32 + lane;
+            const T* w = hwts + 2 * t + odd;
+            for (int e = 0; e < E; ++e) {
+                const T we = w[(size_t)e * 2 * (H + 1)];
+                const cplx<T> v = yr[32 * e];
+                ar += we * v.r;
+                ai += we * v.i;
+            }
+        }
+        out[lane * 33 + tl] = mk<T>(ar, ai);
+    }
+    __syncthreads();
+    for (int idx = tid; idx < 32 * 32; idx += 256) {
+        const int ml = idx >> 5, tl = idx & 31;
+        const int m = m0 + ml, t = t0 + tl;
+        if (m <= L && t <= H) U[((int64_t)b * (L + 1) + m) * ldu + t] = out[ml * 33 + tl];
+    }
+}
+
+// lat_fft_kernel: one block per (order m, map): the half grid is mirrored into
+// the full M-point grid in shared memory, transformed, deconvolved and written
+// as the normal-equation right-hand sides (same output as nufft_kernel).
+template <class T, int E>
+__global__ void __launch_bounds__(512, (E <= 16 ? 2 : 1)) lat_fft_kernel(
+    const cplx<T>* __restrict__ U, cplx<T>* __restrict__ bvec, const T* __restrict__ dec,
+    const cplx<T>* __restrict__ tw, int twlen, int M, int logM, int p, int L, int P2, int ldu) {
+    extern __shared__ unsigned char smem_raw[];
+    cplx<T>* u = reinterpret_cast<cplx<T>*>(smem_raw);   // M (padded)
+    const int m = blockIdx.x;
+    const int b = blockIdx.y;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int H = M >> 1;
+    const bool odd = (m & 1) != 0;
+    const cplx<T>* src = U + ((int64_t)b * (L + 1) + m) * ldu;
+    for (int t = tid; t <= H; t += nt) {
+        const cplx<T> v = src[t];
+        u[pad(t)] = v;
+        if (t > 0 && t < H) u[pad(M - t)] = odd ? mk<T>(-v.r, -v.i) : v;
+    }
+    __syncthreads();
+    block_fft_pad<T, E>(u, logM, tw, twlen, false);
+    cplx<T>* out = bvec + ((int64_t)b * (p + 1) + m) * 2 * P2;
+    for (int j = tid; j <= p; j += nt) {
+        cplx<T> v = scale(u[pad(j)], dec[j]);
+        if (odd) v = mk<T>(T(-0.5) * v.i, T(0.5) * v.r);
+        out[(j & 1) * P2 + (j >> 1)] = v;
+    }
+    if (tid == 0) out[P2 + (P2 - 1)] = mk<T>(T(0), T(0));
+}
+
+template <class T>
+void launch_spread(const hpx_plan_s* P, cudaStream_t s) {
+    const auto& g = P->g;
+    const auto& t = P->t;
+    const int H = g.M / 2;
+    const size_t smem = (size_t)(32 * 33 + 32 * t.spreadRows) * sizeof(cplx<T>);
+    cudaFuncSetAttribute(spread_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    dim3 grid((H + 32) / 32, (g.L + 32) / 32, g.B);
+    spread_kernel<T><<<grid, 256, smem, s>>>((const cplx<T>*)P->Y, (cplx<T>*)P->U, t.hstart, (const T*)t.hwts,
+                                             t.spreadH, H, g.p, g.Q, g.L, P->ldu);
+}
+
+template <class T>
+void launch_lat_fft(const hpx_plan_s* P, cudaStream_t s) {
+    const auto& g = P->g;
+    int logM = 0;
+    while ((1 << logM) < g.M) ++logM;
+    const size_t smem = (size_t)(g.M + g.M / 16) * sizeof(cplx<T>);
+    auto kern = g.M > 16 * 512 ? lat_fft_kernel<T, 32> : lat_fft_kernel<T, 16>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    dim3 grid(g.L + 1, g.B);
+    kern<<<grid, 512, smem, s>>>((const cplx<T>*)P->U, (cplx<T>*)P->bvec, (const T*)P->t.dec,
+                                 (const cplx<T>*)P->t.twid, g.Lmax, g.M, logM, g.p, g.L, g.P2, P->ldu);
+}
+
+template void launch_spread<float>(const hpx_plan_s*, cudaStream_t);
+template void launch_spread<double>(const hpx_plan_s*, cudaStream_t);
+template void launch_lat_fft<float>(const hpx_plan_s*, cudaStream_t);
+template void launch_lat_fft<double>(const hpx_plan_s*, cudaStream_t);
 
 template <class T>
 void launch_nufft(const hpx_plan_s* P, cudaStream_t s) {

@@ -26,6 +26,9 @@ struct DevTables {
     int* nstart = nullptr;                  // dense spreading table: first node per grid point
     void* swts = nullptr;                   // T [spreadE][M]
     int spreadE = 0;
+    int* hstart = nullptr;                  // half-grid spreading with folded mirrors
+    void* hwts = nullptr;                   // T [spreadH][M/2 + 1][2]
+    int spreadH = 0, spreadRows = 0;
     void* D = nullptr;                      // T [2][2][P2][P2]
     int64_t* angOff = nullptr;
     void* ang = nullptr;                    // cplx<T> (cos, sin)
@@ -52,13 +55,15 @@ struct hpx_plan_s {
     hpx::DevTables t;
     // workspace
     void* Y = nullptr;      // cplx<T> [B][Q][p+1]: step-1 ring coefficients per latitude node
+    void* U = nullptr;      // cplx<T> [B][L+1][ldu]: spread half grids (t = 0..M/2) per column
+    int ldu = 0;
     void* bvec = nullptr;   // cplx<T> [B][p+1][2][P2]: latitude NUFFT right-hand sides
     void* beta = nullptr;   // cplx<T> [B][p+1][2][P2]: order-0/1 Legendre coefficients (aliases Y)
     int64_t bytes = 0;
     int status = 0;
     // profiling: events around the kernels of each recorded hpx_analyze call
     static constexpr int kMaxProf = 256;
-    static constexpr int kStages = 5;
+    static constexpr int kStages = 6;
     bool prof = false;
     int nprof = 0;
     cudaEvent_t* ev = nullptr;   // [kMaxProf][kStages + 1]
@@ -105,6 +110,8 @@ namespace hpx {
 template <class T> void launch_ring_fft(const hpx_plan_s* P, const T* maps, cudaStream_t s);
 template <class T> void launch_poles(const hpx_plan_s* P, const T* maps, cudaStream_t s);
 template <class T> void launch_nufft(const hpx_plan_s* P, cudaStream_t s);
+template <class T> void launch_spread(const hpx_plan_s* P, cudaStream_t s);
+template <class T> void launch_lat_fft(const hpx_plan_s* P, cudaStream_t s);
 template <class T> void launch_dense(const hpx_plan_s* P, cudaStream_t s);
 template <class T> void launch_rot(const hpx_plan_s* P, T* alm, cudaStream_t s);
 int fused_tile_rows(int B);

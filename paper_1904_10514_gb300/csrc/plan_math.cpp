@@ -351,6 +351,44 @@ std::string build_tables(int nside, int lmax, bool fp64, PlanTables& t) {
                 }
             }
         }
+        // half grid with folded mirrors
+        {
+            const int H = M / 2;
+            std::vector<std::vector<std::pair<int, std::pair<double, double>>>> hrow(H + 1);
+            int E = 0;
+            std::vector<int> rlo(H + 1, 0);
+            for (int i = 0; i <= H; ++i) {
+                int lo = Q, hi = -1;
+                for (const auto& e : rows[i]) {
+                    const int r = e.first & ((1 << 30) - 1);
+                    lo = std::min(lo, r);
+                    hi = std::max(hi, r);
+                }
+                if (hi < 0) { lo = 0; hi = 0; }
+                rlo[i] = lo;
+                E = std::max(E, hi - lo + 1);
+            }
+            t.spreadH = E;
+            t.hstart.assign(H + 1, 0);
+            t.hwts.assign((size_t)E * (H + 1) * 2, 0.0);
+            for (int i = 0; i <= H; ++i) {
+                const int st = std::min(rlo[i], Q - E);
+                t.hstart[i] = st;
+                for (const auto& e : rows[i]) {
+                    const int r = e.first & ((1 << 30) - 1);
+                    const bool mir = (e.first >> 30) != 0;
+                    const size_t k = ((size_t)(r - st) * (H + 1) + i) * 2;
+                    t.hwts[k] += e.second;
+                    t.hwts[k + 1] += mir ? -e.second : e.second;
+                }
+            }
+            for (int i = 1; i <= H; ++i)   // the spreading kernel relies on this
+                if (t.hstart[i] < t.hstart[i - 1]) return "half-grid spreading starts are not monotone";
+            int rows32 = 0;
+            for (int t0 = 0; t0 <= H; t0 += 32)
+                rows32 = std::max(rows32, t.hstart[std::min(t0 + 31, H)] + E - t.hstart[t0]);
+            t.spreadRows = rows32;
+        }
         // the same entries grouped by latitude node (for the transposed NUFFT)
         std::vector<std::vector<std::pair<int, double>>> byNode(Q);
         for (int i = 0; i < M; ++i)

@@ -39,6 +39,14 @@ struct PlanTables {
     int spreadE = 0;             // weights per grid point in the dense spreading table
     std::vector<int> nstart;     // first DFS node seen by grid point t (cyclic run of spreadE)
     std::vector<double> swts;    // [spreadE][M] weights, zero past the end of a run
+    // The same spreading on the half grid t = 0..M/2 with the mirrored nodes
+    // folded in (the grid values obey u[M - t] = (-1)^m u[t]): grid point t sees
+    // the latitude nodes r = hstart[t] .. hstart[t] + spreadH - 1 with weights
+    // hwts[e][t] = (w(even m), w(odd m)); spreadRows bounds the nodes seen by 32
+    // consecutive grid points.
+    int spreadH = 0, spreadRows = 0;
+    std::vector<int> hstart;
+    std::vector<double> hwts;    // [spreadH][M/2 + 1][2]
 
     // ---- latitude least squares + Chebyshev -> order-0/1 Legendre (Sec. 3.2.2, 3.3)
     int P2 = 0;                  // p/2 + 1
