@@ -121,6 +121,13 @@ __device__ __forceinline__ void reg_dft(cplx<T>* x) {
                 const cplx<T> d = sub(u, v);
                 if (pos == 0) {
                     x[i + half] = d;
+                } else if (k16 == 4) {   // w = -i (forward) or +i (inverse)
+                    x[i + half] = INV ? mk<T>(-d.i, d.r) : mk<T>(d.i, -d.r);
+                } else if (k16 == 2 || k16 == 6) {   // w = (+-1 -+ i) / sqrt 2
+                    const T h = sizeof(T) == 4 ? (T)c16f(2) : (T)c16d(2);
+                    const T pr = d.r + d.i, mr = d.r - d.i;
+                    if (k16 == 2) x[i + half] = INV ? mk<T>(h * mr, h * pr) : mk<T>(h * pr, -h * mr);
+                    else x[i + half] = INV ? mk<T>(-h * pr, h * mr) : mk<T>(-h * mr, -h * pr);
                 } else {
                     const T c = sizeof(T) == 4 ? (T)c16f(k16) : (T)c16d(k16);
                     const T s = sizeof(T) == 4 ? (T)s16f(k16) : (T)s16d(k16);
@@ -167,13 +174,20 @@ __device__ __forceinline__ void stockham_pass(cplx<T>* a, int N, int logS, const
             const int j = k & (S - 1);
             const int g = k >> logS;
             if (S > 1) {
-                const int step = twlen / (S * R);   // w^(r j) = tw[r j step]
+                // w^(r j) = tw[r j step]: w^j, w^2j, w^4j, w^8j from the table,
+                // the other powers as products of at most three of them
+                const int step = twlen / (S * R);
+                cplx<T> wp[R];
 #pragma unroll
-                for (int r = 1; r < R; ++r) {
-                    cplx<T> w = tw[r * j * step];
-                    if (INV) w.i = -w.i;
-                    x[gg][r] = mul(x[gg][r], w);
+                for (int r = 1; r < R; r <<= 1) {
+                    wp[r] = tw[r * j * step];
+                    if (INV) wp[r].i = -wp[r].i;
                 }
+#pragma unroll
+                for (int r = 3; r < R; ++r)
+                    if (r & (r - 1)) wp[r] = mul(wp[r & (r - 1)], wp[r & -r]);
+#pragma unroll
+                for (int r = 1; r < R; ++r) x[gg][r] = mul(x[gg][r], wp[r]);
             }
             reg_dft<T, R, INV>(x[gg]);
             const int base = g * S * R + j;
