@@ -170,6 +170,7 @@ hpx_plan_s* hpx_plan_ex(const hpx_plan_desc* d) {
     t.nstart = up.vec(tb.nstart); t.swts = up.real(tb.swts, fp64); t.spreadE = tb.spreadE;
     t.hstart = up.vec(tb.hstart); t.hwts = up.real(tb.hwts, fp64); t.spreadH = tb.spreadH;
     t.spreadRows = tb.spreadRows;
+    t.spreadD = tb.spreadD;
     t.D = up.real(tb.D, fp64);
     t.angOff = up.vec(tb.angOff); t.ang = up.real(tb.ang, fp64);
     t.skOff = up.vec(tb.skOff); t.skew = up.real(tb.skew, fp64); t.nq = tb.nq;

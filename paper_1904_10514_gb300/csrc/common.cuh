@@ -174,20 +174,30 @@ __device__ __forceinline__ void stockham_pass(cplx<T>* a, int N, int logS, const
             const int j = k & (S - 1);
             const int g = k >> logS;
             if (S > 1) {
-                // w^(r j) = tw[r j step]: w^j, w^2j, w^4j, w^8j from the table,
-                // the other powers as products of at most three of them
+                // w^(r j) = tw[r j step]: w^j, w^2j, w^4j, w^8j from the table; for
+                // r = 4 hi + lo the power is (w^4j)^hi (w^j)^lo, with w^3j and w^12j
+                // formed once (at most two products per power)
                 const int step = twlen / (S * R);
-                cplx<T> wp[R];
+                auto ld = [&](int r) {
+                    cplx<T> w = tw[r * j * step];
+                    if (INV) w.i = -w.i;
+                    return w;
+                };
+                const cplx<T> b1 = ld(1);
+                const cplx<T> b2 = R > 2 ? ld(2) : b1;
+                const cplx<T> w3 = R > 2 ? mul(b1, b2) : b1;
+                const cplx<T> b4 = R > 4 ? ld(4) : b1;
+                const cplx<T> b8 = R > 8 ? ld(8) : b1;
+                const cplx<T> w12 = R > 8 ? mul(b4, b8) : b1;
 #pragma unroll
-                for (int r = 1; r < R; r <<= 1) {
-                    wp[r] = tw[r * j * step];
-                    if (INV) wp[r].i = -wp[r].i;
+                for (int r = 1; r < R; ++r) {
+                    const int hi = r >> 2, lo = r & 3;
+                    const cplx<T> wl = lo == 1 ? b1 : lo == 2 ? b2 : w3;
+                    const cplx<T> wh = hi == 1 ? b4 : hi == 2 ? b8 : w12;
+                    if (hi == 0) x[gg][r] = mul(x[gg][r], wl);
+                    else if (lo == 0) x[gg][r] = mul(x[gg][r], wh);
+                    else x[gg][r] = mul(mul(x[gg][r], wh), wl);
                 }
-#pragma unroll
-                for (int r = 3; r < R; ++r)
-                    if (r & (r - 1)) wp[r] = mul(wp[r & (r - 1)], wp[r & -r]);
-#pragma unroll
-                for (int r = 1; r < R; ++r) x[gg][r] = mul(x[gg][r], wp[r]);
             }
             reg_dft<T, R, INV>(x[gg]);
             const int base = g * S * R + j;

@@ -121,6 +121,94 @@ __global__ void __launch_bounds__(256) spread_kernel(const cplx<T>* __restrict__
     }
 }
 
+// 8-byte asynchronous global -> shared copy; src_bytes = 0 writes zeros.
+__device__ __forceinline__ void cp_async8(void* dst, const void* src, int src_bytes) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Register-blocked form for FP32 (at most EW taps, consecutive groups of 4 grid
+// points starting at most DM latitude nodes apart): a block takes 32 grid points
+// of one map and loops over all orders 32 at a time.  Warp w owns grid points
+// t0 + 4w .. t0 + 4w + 3 and lane l order m0 + l; the thread keeps its 4 x EW
+// weights (for the parity of its order) in registers, aligned to a common
+// window of EW + DM latitude nodes, so every node value read from shared
+// memory feeds four grid points.  The node values of the next 32 orders are
+// copied into the other half of a double buffer (cp.async) while the current
+// ones are used.
+template <int EW, int DM>
+__global__ void __launch_bounds__(256, 2) spread_rb_kernel(const cplx<float>* __restrict__ Y,
+                                                           cplx<float>* __restrict__ U,
+                                                           const int* __restrict__ hstart,
+                                                           const float* __restrict__ hwts, int E, int H, int p,
+                                                           int Q, int L, int ldu, int nrw) {
+    constexpr int W = EW + DM;
+    extern __shared__ unsigned char smem_raw[];
+    cplx<float>* out = reinterpret_cast<cplx<float>*>(smem_raw);   // [32 orders][33]
+    cplx<float>* ys0 = out + 32 * 33;                              // 2 x [nrw rows][32 orders]
+    const int t0 = blockIdx.x * 32, b = blockIdx.y;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int R0 = hstart[t0];
+    const int tf = min(t0 + 4 * warp, H);
+    const int base = hstart[tf] - R0;   // window start, relative to R0
+    const int par = lane & 1;           // m0 is a multiple of 32
+    float w[4][W];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int t = t0 + 4 * warp + j;
+        const int off = (t <= H) ? hstart[t] - hstart[tf] : 0;
+#pragma unroll
+        for (int q = 0; q < W; ++q) {
+            const int e = q - off;
+            w[j][q] = (t <= H && e >= 0 && e < E) ? hwts[((size_t)e * (H + 1) + t) * 2 + par] : 0.f;
+        }
+    }
+    const cplx<float>* yb = Y + (int64_t)b * Q * (p + 1);
+    auto fetch = [&](int m0, cplx<float>* ys) {
+        for (int idx = tid; idx < nrw * 32; idx += 256) {
+            const int r = idx >> 5, m = m0 + (idx & 31);
+            const bool ok = m <= L && R0 + r < Q;
+            cp_async8(ys + idx, ok ? yb + (int64_t)(R0 + r) * (p + 1) + m : yb, ok ? 8 : 0);
+        }
+        cp_async_commit();
+    };
+    const int ntiles = (L + 32) / 32;
+    fetch(0, ys0);
+    for (int it = 0; it < ntiles; ++it) {
+        const int m0 = 32 * it;
+        cplx<float>* ys = ys0 + (it & 1) * nrw * 32;
+        if (it + 1 < ntiles) {
+            fetch(m0 + 32, ys0 + ((it + 1) & 1) * nrw * 32);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();
+        float ar[4] = {0.f, 0.f, 0.f, 0.f}, ai[4] = {0.f, 0.f, 0.f, 0.f};
+        const cplx<float>* yr = ys + base * 32 + lane;
+#pragma unroll
+        for (int q = 0; q < W; ++q) {
+            const cplx<float> v = yr[32 * q];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                ar[j] += w[j][q] * v.r;
+                ai[j] += w[j][q] * v.i;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) out[lane * 33 + 4 * warp + j] = mk<float>(ar[j], ai[j]);
+        __syncthreads();
+        for (int idx = tid; idx < 32 * 32; idx += 256) {
+            const int ml = idx >> 5, tl = idx & 31;
+            const int m = m0 + ml, t = t0 + tl;
+            if (m <= L && t <= H) U[((int64_t)b * (L + 1) + m) * ldu + t] = out[ml * 33 + tl];
+        }
+    }
+}
+
 // lat_fft_kernel: one block per (order m, map): the half grid is mirrored into
 // the full M-point grid in shared memory, transformed, deconvolved and written
 // as the normal-equation right-hand sides (same output as nufft_kernel).
@@ -157,6 +245,18 @@ void launch_spread(const hpx_plan_s* P, cudaStream_t s) {
     const auto& g = P->g;
     const auto& t = P->t;
     const int H = g.M / 2;
+    constexpr int EW = 12, DM = 4;
+    if (sizeof(T) == 4 && t.spreadH <= EW && t.spreadD <= DM) {
+        // rows a block needs: its first window start .. the last window end
+        const int nrw = t.spreadRows - t.spreadH + EW + DM;
+        const size_t smem = (size_t)(32 * 33 + 2 * 32 * nrw) * sizeof(cplx<float>);
+        cudaFuncSetAttribute(spread_rb_kernel<EW, DM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        dim3 grid((H + 32) / 32, g.B);
+        spread_rb_kernel<EW, DM><<<grid, 256, smem, s>>>((const cplx<float>*)P->Y, (cplx<float>*)P->U, t.hstart,
+                                                         (const float*)t.hwts, t.spreadH, H, g.p, g.Q, g.L,
+                                                         P->ldu, nrw);
+        return;
+    }
     const size_t smem = (size_t)(32 * 33 + 32 * t.spreadRows) * sizeof(cplx<T>);
     cudaFuncSetAttribute(spread_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     dim3 grid((H + 32) / 32, (g.L + 32) / 32, g.B);

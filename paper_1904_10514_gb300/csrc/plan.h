@@ -28,7 +28,7 @@ struct DevTables {
     int spreadE = 0;
     int* hstart = nullptr;                  // half-grid spreading with folded mirrors
     void* hwts = nullptr;                   // T [spreadH][M/2 + 1][2]
-    int spreadH = 0, spreadRows = 0;
+    int spreadH = 0, spreadRows = 0, spreadD = 0;
     void* D = nullptr;                      // T [2][2][P2][P2]
     int64_t* angOff = nullptr;
     void* ang = nullptr;                    // cplx<T> (cos, sin)

@@ -45,6 +45,7 @@ struct PlanTables {
     // hwts[e][t] = (w(even m), w(odd m)); spreadRows bounds the nodes seen by 32
     // consecutive grid points.
     int spreadH = 0, spreadRows = 0;
+    int spreadD = 0;             // max of hstart[t + 3] - hstart[t] over t = 0, 4, 8, ..
     std::vector<int> hstart;
     std::vector<double> hwts;    // [spreadH][M/2 + 1][2]
 
