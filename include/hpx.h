@@ -119,7 +119,10 @@ int hpx_synthesize(hpx_plan_s* plan, const void* alm, void* maps);
 
 /* Angular power spectrum of Eq. (APS) for real maps,
  * C_l = (|a_l0|^2 + 2 sum_{m=1}^{l} |a_lm|^2) / (2l + 1),
- * accumulated in double with compensated summation.  alm in the plan's layout
+ * squares summed in groups of 4 in the plan precision, the group sums in
+ * double, partial sums combined with compensated summation (all terms are
+ * positive; the result is within about 3e-7 relative for FP32 plans and
+ * 1e-13 for FP64 plans).  alm in the plan's layout
  * and precision, cl = [batch][lmax + 1] double (device).  Asynchronous. */
 int hpx_cl(hpx_plan_s* plan, const void* alm, double* cl);
 

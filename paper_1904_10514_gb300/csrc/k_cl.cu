@@ -2,9 +2,14 @@
 //     C_l = (|a_l^0|^2 + 2 sum_{m=1}^{l} |a_l^m|^2) / (2l + 1).
 // A block covers 32 consecutive degrees of one map; its 8 warps split the orders
 // m between them (warp w takes m = w, w+8, ...), so each load instruction reads
-// 32 consecutive degrees at one m -- adjacent in the m-major packing.  Each
-// partial sum is accumulated in FP64 with Neumaier compensation and the 8
-// partials of a degree are combined the same way.
+// 32 consecutive degrees at one m -- adjacent in the m-major packing.  All terms
+// are positive, so plain sums lose at most n u of the total: a thread squares
+// in the plan precision, adds groups of 4 squares in that precision and the
+// group sums in double (for FP32 plans each group sum is within about 3e-7 of
+// its exact value, and the double partial within about 1e-13); the 8 partials of a
+// degree are then combined with Neumaier's compensated summation.  (Doing all
+// of it in FP64 with compensation per term made this kernel FP64-bound on a
+// GPU with low FP64 throughput.)
 #include "plan.h"
 
 namespace hpx {
@@ -27,16 +32,25 @@ __global__ void __launch_bounds__(32 * kSlices) cl_kernel(const cplx<T>* __restr
     const int l = blockIdx.x * 32 + lane;
     const int b = blockIdx.y;
     const cplx<T>* a = alm + (int64_t)b * nalm;
-    double s = 0.0, comp = 0.0;
+    double s = 0.0;
     if (l <= L) {
-        for (int m = slice; m <= l; m += kSlices) {
+        auto sq = [&](int m) {
             const cplx<T> v = a[(int64_t)m * (2 * L + 1 - m) / 2 + l];
-            const double re = (double)v.r, im = (double)v.i;
-            neumaier(s, comp, (m == 0 ? 1.0 : 2.0) * (re * re + im * im));
+            return v.r * v.r + v.i * v.i;
+        };
+        int m = slice;
+        if (m == 0) {   // the m = 0 term has weight 1, all others 2
+            s = (double)sq(0);
+            m += kSlices;
         }
+        double s2 = 0.0;
+        for (; m + 3 * kSlices <= l; m += 4 * kSlices)
+            s2 += (double)((sq(m) + sq(m + kSlices)) + (sq(m + 2 * kSlices) + sq(m + 3 * kSlices)));
+        for (; m <= l; m += kSlices) s2 += (double)sq(m);
+        s += 2.0 * s2;
     }
     part[slice][lane][0] = s;
-    part[slice][lane][1] = comp;
+    part[slice][lane][1] = 0.0;
     __syncthreads();
     if (slice == 0 && l <= L) {
         double S = 0.0, C = 0.0;
