@@ -177,6 +177,15 @@ int hpx_stage_times(hpx_plan_s* plan, float* ms, int n, int* ncalls);
 #define HPX_NOALLOC_MAX_NSIDE 128
 int hpx_analyze_noalloc(int nside, int lmax, const float* maps, float* alm, void* cuda_stream);
 
+/* Self-test of the failure path (the paper has no counterpart).  Launches one
+ * kernel on the plan's stream whose bounded wait on an mbarrier that nothing
+ * completes gives up after `spins` polls (1 <= spins <= 2^20) and records
+ * HPX_ERR_TIMEOUT in the plan's device status word, exactly as a timed-out
+ * wait of the tensor-core kernel does; the next hpx_sync returns
+ * HPX_ERR_TIMEOUT and clears the word.  Nothing faults and the context stays
+ * usable.  Returns HPX_ERR_ARG for a NULL plan or spins out of range. */
+int hpx_selftest_timeout(hpx_plan_s* plan, int spins);
+
 /* Last error code of the calling thread and its message. */
 int hpx_last_error(void);
 const char* hpx_strerror(int code);

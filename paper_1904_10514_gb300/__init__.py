@@ -32,7 +32,7 @@ HPX_FP64 = 1
 EXPORTS = ["hpx_plan", "hpx_plan_ex", "hpx_set_stream", "hpx_analyze", "hpx_synthesize", "hpx_cl",
            "hpx_sync", "hpx_destroy", "hpx_npix", "hpx_nalm", "hpx_plan_lmax", "hpx_plan_bytes",
            "hpx_last_error", "hpx_strerror", "hpx_set_profiling", "hpx_stage_times",
-           "hpx_analyze_noalloc", "hpx_plan_flags"]
+           "hpx_analyze_noalloc", "hpx_plan_flags", "hpx_selftest_timeout"]
 HPX_FLAG_SWEEPS = 1
 HPX_FLAG_GRAPH = 2
 HPX_FLAG_SIMT = 4
@@ -89,6 +89,7 @@ def lib():
             "hpx_strerror": (ctypes.c_char_p, [i32]),
             "hpx_set_profiling": (i32, [vp, i32]),
             "hpx_analyze_noalloc": (i32, [i32, i32, vp, vp, vp]),
+            "hpx_selftest_timeout": (i32, [vp, i32]),
             "hpx_stage_times": (i32, [vp, ctypes.POINTER(ctypes.c_float), i32, ctypes.POINTER(ctypes.c_int)]),
         }
         for name, (res, args) in sig.items():
@@ -116,6 +117,10 @@ def hpx_plan_ex(nside, lmax=-1, batch=1, precision=HPX_FP32, flags=0, nsides=Non
     d = hpx_plan_desc(int(nside), int(lmax), int(batch), int(precision), int(flags),
                       ctypes.cast(arr, ctypes.POINTER(ctypes.c_int)) if arr is not None else None)
     return lib().hpx_plan_ex(ctypes.byref(d))
+
+
+def hpx_selftest_timeout(plan, spins):
+    return lib().hpx_selftest_timeout(plan, int(spins))
 
 
 def hpx_set_stream(plan, stream):

@@ -405,6 +405,14 @@ int hpx_plan_lmax(const hpx_plan_s* P) { return P ? P->g.L : -1; }
 int64_t hpx_plan_bytes(const hpx_plan_s* P) { return P ? P->bytes : 0; }
 int hpx_plan_flags(const hpx_plan_s* P) { return P ? (int)P->flags : -1; }
 
+int hpx_selftest_timeout(hpx_plan_s* P, int spins) {
+    if (!P || spins < 1 || spins > (1 << 20)) return set_err(HPX_ERR_ARG);
+    hpx_plan_s* Q = P->group ? P->subs[0] : P;   // a group reports through its sub-plans
+    cudaSetDevice(P->device);
+    hpx::launch_timeout_selftest(Q, spins, P->stream);
+    return set_err(cudaGetLastError() == cudaSuccess ? HPX_OK : HPX_ERR_CUDA);
+}
+
 int hpx_last_error(void) { return g_last_error; }
 
 const char* hpx_strerror(int code) {

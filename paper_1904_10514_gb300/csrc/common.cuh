@@ -151,6 +151,33 @@ __device__ __forceinline__ void reg_dft(cplx<T>* x) {
     for (int q = 0; q < R; ++q) x[q] = y[q];
 }
 
+// x[r] *= w^(r j), w^(r j) = tw[r j step] (conjugated for INV): w^j, w^2j,
+// w^4j, w^8j from the table; for r = 4 hi + lo the power is (w^4j)^hi (w^j)^lo,
+// with w^3j and w^12j formed once (at most two products per power).
+template <class T, int R, bool INV>
+__device__ __forceinline__ void twiddle(cplx<T>* x, int j, int step, const cplx<T>* __restrict__ tw) {
+    auto ld = [&](int r) {
+        cplx<T> w = tw[r * j * step];
+        if (INV) w.i = -w.i;
+        return w;
+    };
+    const cplx<T> b1 = ld(1);
+    const cplx<T> b2 = R > 2 ? ld(2) : b1;
+    const cplx<T> w3 = R > 2 ? mul(b1, b2) : b1;
+    const cplx<T> b4 = R > 4 ? ld(4) : b1;
+    const cplx<T> b8 = R > 8 ? ld(8) : b1;
+    const cplx<T> w12 = R > 8 ? mul(b4, b8) : b1;
+#pragma unroll
+    for (int r = 1; r < R; ++r) {
+        const int hi = r >> 2, lo = r & 3;
+        const cplx<T> wl = lo == 1 ? b1 : lo == 2 ? b2 : w3;
+        const cplx<T> wh = hi == 1 ? b4 : hi == 2 ? b8 : w12;
+        if (hi == 0) x[r] = mul(x[r], wl);
+        else if (lo == 0) x[r] = mul(x[r], wh);
+        else x[r] = mul(mul(x[r], wh), wl);
+    }
+}
+
 template <class T, int R, int G, bool INV>
 __device__ __forceinline__ void stockham_pass(cplx<T>* a, int N, int logS, const cplx<T>* __restrict__ tw,
                                               int twlen) {
@@ -173,32 +200,7 @@ __device__ __forceinline__ void stockham_pass(cplx<T>* a, int N, int logS, const
         if (k < ngroups) {
             const int j = k & (S - 1);
             const int g = k >> logS;
-            if (S > 1) {
-                // w^(r j) = tw[r j step]: w^j, w^2j, w^4j, w^8j from the table; for
-                // r = 4 hi + lo the power is (w^4j)^hi (w^j)^lo, with w^3j and w^12j
-                // formed once (at most two products per power)
-                const int step = twlen / (S * R);
-                auto ld = [&](int r) {
-                    cplx<T> w = tw[r * j * step];
-                    if (INV) w.i = -w.i;
-                    return w;
-                };
-                const cplx<T> b1 = ld(1);
-                const cplx<T> b2 = R > 2 ? ld(2) : b1;
-                const cplx<T> w3 = R > 2 ? mul(b1, b2) : b1;
-                const cplx<T> b4 = R > 4 ? ld(4) : b1;
-                const cplx<T> b8 = R > 8 ? ld(8) : b1;
-                const cplx<T> w12 = R > 8 ? mul(b4, b8) : b1;
-#pragma unroll
-                for (int r = 1; r < R; ++r) {
-                    const int hi = r >> 2, lo = r & 3;
-                    const cplx<T> wl = lo == 1 ? b1 : lo == 2 ? b2 : w3;
-                    const cplx<T> wh = hi == 1 ? b4 : hi == 2 ? b8 : w12;
-                    if (hi == 0) x[gg][r] = mul(x[gg][r], wl);
-                    else if (lo == 0) x[gg][r] = mul(x[gg][r], wh);
-                    else x[gg][r] = mul(mul(x[gg][r], wh), wl);
-                }
-            }
+            if (S > 1) twiddle<T, R, INV>(x[gg], j, twlen / (S * R), tw);
             reg_dft<T, R, INV>(x[gg]);
             const int base = g * S * R + j;
 #pragma unroll
@@ -206,6 +208,69 @@ __device__ __forceinline__ void stockham_pass(cplx<T>* a, int N, int logS, const
         }
     }
     __syncthreads();
+}
+
+// First pass (span 1, no twiddles) with the inputs taken from ld(i), i < N,
+// instead of shared memory; its outputs go to the padded array a.  Ends with a
+// barrier.
+template <class T, int R, int G, class LD>
+__device__ __forceinline__ void stockham_first(cplx<T>* a, int N, LD ld) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int ngroups = N / R;
+#pragma unroll
+    for (int gg = 0; gg < G; ++gg) {
+        const int k = tid + gg * nt;
+        if (k < ngroups) {
+            cplx<T> x[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) x[r] = ld(k + r * ngroups);
+            reg_dft<T, R, false>(x);
+#pragma unroll
+            for (int q = 0; q < R; ++q) a[pad(k * R + q)] = x[q];
+        }
+    }
+    __syncthreads();
+}
+
+// Last pass (span S = N / R) reading a and handing output j (natural order,
+// all j < N) to st(j, value) instead of storing it.  No barrier.
+template <class T, int R, int G, class ST>
+__device__ __forceinline__ void stockham_last(const cplx<T>* a, int N, const cplx<T>* __restrict__ tw, int twlen,
+                                              ST st) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int S = N / R;
+#pragma unroll
+    for (int gg = 0; gg < G; ++gg) {
+        const int j = tid + gg * nt;
+        if (j < S) {
+            cplx<T> x[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) x[r] = a[pad(j + r * S)];
+            twiddle<T, R, false>(x, j, twlen / N, tw);
+            reg_dft<T, R, false>(x);
+#pragma unroll
+            for (int q = 0; q < R; ++q) st(j + q * S, x[q]);
+        }
+    }
+}
+
+// Forward DFT of length N = 2^logn (5 <= logn, N <= E * blockDim) whose input
+// element i is ld(i) and whose output element j is handed to st(j, value): the
+// first pass reads through ld, the last pass writes through st, the passes in
+// between run in the padded shared array a.
+template <class T, int E, class LD, class ST>
+__device__ __forceinline__ void block_fft_io(cplx<T>* a, int logn, const cplx<T>* __restrict__ tw, int twlen, LD ld,
+                                             ST st) {
+    const int N = 1 << logn;
+    stockham_first<T, 16, E / 16>(a, N, ld);
+    int logS = 4;
+    const int lr = logn & 3;   // radix of the last pass: 16 if lr == 0, else 2^lr
+    const int last = lr == 0 ? logn - 4 : logn - lr;   // logS of the last pass
+    for (; logS < last; logS += 4) stockham_pass<T, 16, E / 16, false>(a, N, logS, tw, twlen);
+    if (lr == 0) stockham_last<T, 16, E / 16>(a, N, tw, twlen, st);
+    else if (lr == 3) stockham_last<T, 8, E / 8>(a, N, tw, twlen, st);
+    else if (lr == 2) stockham_last<T, 4, E / 4>(a, N, tw, twlen, st);
+    else stockham_last<T, 2, E / 2>(a, N, tw, twlen, st);
 }
 
 // DFT of length N = 2^logn (forward sign -1, or inverse +1 unnormalised) of the

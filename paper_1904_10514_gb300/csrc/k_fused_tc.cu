@@ -84,8 +84,8 @@ __device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count) {
 }
 
 // Bounded wait for the given phase parity; returns false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
-    for (uint32_t it = 0; it < kSpinLimit; ++it) {
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, uint32_t limit = kSpinLimit) {
+    for (uint32_t it = 0; it < limit; ++it) {
         uint32_t done = 0;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
@@ -292,6 +292,20 @@ __global__ void __launch_bounds__(NT, 2) fused_tc_kernel(const float* __restrict
     __syncthreads();
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(dtmem), "r"(2 * TN) : "memory");
+}
+
+// Failure-path self-test: a wait on an mbarrier that nothing completes gives up
+// after `spins` polls and reports like the operator kernel does.
+__global__ void timeout_selftest_kernel(int* __restrict__ status, uint32_t spins) {
+    __shared__ __align__(8) uint64_t mbar;
+    if (threadIdx.x != 0) return;
+    mbar_init(smem_u32(&mbar), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    if (!mbar_wait(smem_u32(&mbar), 0u, spins)) atomicExch(status, HPX_ERR_TIMEOUT);
+}
+
+void launch_timeout_selftest(const hpx_plan_s* P, int spins, cudaStream_t s) {
+    timeout_selftest_kernel<<<1, 32, 0, s>>>(P->d_status, (uint32_t)spins);
 }
 
 void launch_fused_tc(const hpx_plan_s* P, float* alm, cudaStream_t s) {

@@ -209,9 +209,10 @@ __global__ void __launch_bounds__(256, 2) spread_rb_kernel(const cplx<float>* __
     }
 }
 
-// lat_fft_kernel: one block per (order m, map): the half grid is mirrored into
-// the full M-point grid in shared memory, transformed, deconvolved and written
-// as the normal-equation right-hand sides (same output as nufft_kernel).
+// lat_fft_kernel: one block per (order m, map): M-point FFT of the grid whose
+// first pass reads the half grid from U (mirrored past M/2) and whose last pass
+// deconvolves and writes the modes j <= p as the normal-equation right-hand
+// sides (same output as nufft_kernel); the passes between run in shared memory.
 template <class T, int E>
 __global__ void __launch_bounds__(512, (E <= 16 ? 2 : 1)) lat_fft_kernel(
     const cplx<T>* __restrict__ U, cplx<T>* __restrict__ bvec, const T* __restrict__ dec,
@@ -224,18 +225,27 @@ __global__ void __launch_bounds__(512, (E <= 16 ? 2 : 1)) lat_fft_kernel(
     const int H = M >> 1;
     const bool odd = (m & 1) != 0;
     const cplx<T>* src = U + ((int64_t)b * (L + 1) + m) * ldu;
-    for (int t = tid; t <= H; t += nt) {
-        const cplx<T> v = src[t];
-        u[pad(t)] = v;
-        if (t > 0 && t < H) u[pad(M - t)] = odd ? mk<T>(-v.r, -v.i) : v;
-    }
-    __syncthreads();
-    block_fft_pad<T, E>(u, logM, tw, twlen, false);
     cplx<T>* out = bvec + ((int64_t)b * (p + 1) + m) * 2 * P2;
-    for (int j = tid; j <= p; j += nt) {
-        cplx<T> v = scale(u[pad(j)], dec[j]);
+    // grid value t: the half grid, mirrored with the sign (-1)^m past M/2
+    auto ld = [&](int t) {
+        if (t <= H) return src[t];
+        const cplx<T> v = src[M - t];
+        return odd ? mk<T>(-v.r, -v.i) : v;
+    };
+    // mode j <= p: deconvolve and store as a right-hand side
+    auto st = [&](int j, cplx<T> v) {
+        if (j > p) return;
+        v = scale(v, dec[j]);
         if (odd) v = mk<T>(T(-0.5) * v.i, T(0.5) * v.r);
         out[(j & 1) * P2 + (j >> 1)] = v;
+    };
+    if (logM >= 5) {
+        block_fft_io<T, E>(u, logM, tw, twlen, ld, st);
+    } else {
+        for (int t = tid; t < M; t += nt) u[pad(t)] = ld(t);
+        __syncthreads();
+        block_fft_pad<T, E>(u, logM, tw, twlen, false);
+        for (int j = tid; j < M; j += nt) st(j, u[pad(j)]);
     }
     if (tid == 0) out[P2 + (P2 - 1)] = mk<T>(T(0), T(0));
 }

@@ -117,6 +117,7 @@ template <class T> void launch_rot(const hpx_plan_s* P, T* alm, cudaStream_t s);
 int fused_tile_rows(int B);
 template <class T> void launch_fused(const hpx_plan_s* P, T* alm, cudaStream_t s);
 void launch_fused_tc(const hpx_plan_s* P, float* alm, cudaStream_t s);
+void launch_timeout_selftest(const hpx_plan_s* P, int spins, cudaStream_t s);
 template <class T> int build_fused(hpx_plan_s* P, const double* D64, const cplx<double>* skew64, cudaStream_t s);
 // float offset of element (row r of a tile with rp rows, column k) in the
 // tensor-core layout of M, relative to the tile's first chunk
