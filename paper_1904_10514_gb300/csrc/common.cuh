@@ -211,25 +211,80 @@ __device__ __forceinline__ void stockham_pass(cplx<T>* a, int N, int logS, const
 }
 
 // First pass (span 1, no twiddles) with the inputs taken from ld(i), i < N,
-// instead of shared memory; its outputs go to the padded array a.  Ends with a
+// instead of read directly; its outputs go to the padded array a.  SYNC: ld
+// reads a itself, so every thread loads before any thread stores.  Ends with a
 // barrier.
-template <class T, int R, int G, class LD>
+template <class T, int R, int G, bool INV, bool SYNC, class LD>
 __device__ __forceinline__ void stockham_first(cplx<T>* a, int N, LD ld) {
     const int tid = threadIdx.x, nt = blockDim.x;
     const int ngroups = N / R;
+    cplx<T> x[G][R];
 #pragma unroll
     for (int gg = 0; gg < G; ++gg) {
         const int k = tid + gg * nt;
         if (k < ngroups) {
-            cplx<T> x[R];
 #pragma unroll
-            for (int r = 0; r < R; ++r) x[r] = ld(k + r * ngroups);
-            reg_dft<T, R, false>(x);
+            for (int r = 0; r < R; ++r) x[gg][r] = ld(k + r * ngroups);
+        }
+    }
+    if (SYNC) __syncthreads();
 #pragma unroll
-            for (int q = 0; q < R; ++q) a[pad(k * R + q)] = x[q];
+    for (int gg = 0; gg < G; ++gg) {
+        const int k = tid + gg * nt;
+        if (k < ngroups) {
+            reg_dft<T, R, INV>(x[gg]);
+#pragma unroll
+            for (int q = 0; q < R; ++q) a[pad(k * R + q)] = x[gg][q];
         }
     }
     __syncthreads();
+}
+
+// Last pass (span S = N / R) in place in a, storing f(j, value) for output j
+// (natural order).  Ends with a barrier.
+template <class T, int R, int G, bool INV, class F>
+__device__ __forceinline__ void stockham_last_f(cplx<T>* a, int N, const cplx<T>* __restrict__ tw, int twlen, F f) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int S = N / R;
+    cplx<T> x[G][R];
+#pragma unroll
+    for (int gg = 0; gg < G; ++gg) {
+        const int j = tid + gg * nt;
+        if (j < S) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) x[gg][r] = a[pad(j + r * S)];
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int gg = 0; gg < G; ++gg) {
+        const int j = tid + gg * nt;
+        if (j < S) {
+            twiddle<T, R, INV>(x[gg], j, twlen / N, tw);
+            reg_dft<T, R, INV>(x[gg]);
+#pragma unroll
+            for (int q = 0; q < R; ++q) a[pad(j + q * S)] = f(j + q * S, x[gg][q]);
+        }
+    }
+    __syncthreads();
+}
+
+// DFT of length N = 2^logn (5 <= logn, N <= E * blockDim; forward, or inverse
+// unnormalised) in the padded shared array a, whose input element i is ld(i)
+// (SYNC: ld reads a) and whose output element j is stored as f(j, value).
+template <class T, int E, bool INV, bool SYNC, class LD, class F>
+__device__ __forceinline__ void block_fft_pad_io(cplx<T>* a, int logn, const cplx<T>* __restrict__ tw, int twlen,
+                                                 LD ld, F f) {
+    const int N = 1 << logn;
+    stockham_first<T, 16, E / 16, INV, SYNC>(a, N, ld);
+    int logS = 4;
+    const int lr = logn & 3;
+    const int last = lr == 0 ? logn - 4 : logn - lr;
+    for (; logS < last; logS += 4) stockham_pass<T, 16, E / 16, INV>(a, N, logS, tw, twlen);
+    if (lr == 0) stockham_last_f<T, 16, E / 16, INV>(a, N, tw, twlen, f);
+    else if (lr == 3) stockham_last_f<T, 8, E / 8, INV>(a, N, tw, twlen, f);
+    else if (lr == 2) stockham_last_f<T, 4, E / 4, INV>(a, N, tw, twlen, f);
+    else stockham_last_f<T, 2, E / 2, INV>(a, N, tw, twlen, f);
 }
 
 // Last pass (span S = N / R) reading a and handing output j (natural order,
@@ -262,7 +317,7 @@ template <class T, int E, class LD, class ST>
 __device__ __forceinline__ void block_fft_io(cplx<T>* a, int logn, const cplx<T>* __restrict__ tw, int twlen, LD ld,
                                              ST st) {
     const int N = 1 << logn;
-    stockham_first<T, 16, E / 16>(a, N, ld);
+    stockham_first<T, 16, E / 16, false, false>(a, N, ld);
     int logS = 4;
     const int lr = logn & 3;   // radix of the last pass: 16 if lr == 0, else 2^lr
     const int last = lr == 0 ? logn - 4 : logn - lr;   // logS of the last pass

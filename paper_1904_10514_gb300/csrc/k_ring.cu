@@ -43,8 +43,27 @@ __global__ void __launch_bounds__(kRingThreads, (E <= 16 ? 2 : 1)) ring_fft_kern
     const T* f = maps + (int64_t)b * npix;
     const int tid = threadIdx.x, nt = blockDim.x;
 
-    if (pow2_t[i]) {
-        for (int k = tid; k < n; k += nt) buf[pad(k)] = mk<T>(f[sN + k], equator ? T(0) : f[sS + k]);
+    auto sample = [&](int k) { return mk<T>(f[sN + k], equator ? T(0) : f[sS + k]); };
+    auto same = [](int, cplx<T> v) { return v; };
+    if (pow2_t[i] && logn_t[i] >= 5) {
+        // the first FFT pass reads the rings from the map
+        block_fft_pad_io<T, E, false, false>(buf, logn_t[i], tw, twlen, sample, same);
+    } else if (!pow2_t[i] && logL_t[i] >= 5) {
+        // Bluestein: the forward transform reads the chirped samples and its last
+        // pass multiplies by the transformed kernel; the inverse transform's last
+        // pass applies the output chirp
+        const int L = fftL_t[i];
+        const cplx<T>* ch = chirp + chOff_t[i];
+        const cplx<T>* bh = bhat + bhOff_t[i];
+        auto chirped = [&](int k) { return k < n ? mul(sample(k), ch[k]) : mk<T>(T(0), T(0)); };
+        auto kern = [&](int j, cplx<T> v) { return mul(v, bh[j]); };
+        auto fromsmem = [&](int k) { return buf[pad(k)]; };
+        auto unchirp = [&](int j, cplx<T> v) { return j < n ? mul(v, ch[j]) : v; };
+        (void)L;
+        block_fft_pad_io<T, E, false, false>(buf, logL_t[i], tw, twlen, chirped, kern);
+        block_fft_pad_io<T, E, true, true>(buf, logL_t[i], tw, twlen, fromsmem, unchirp);
+    } else if (pow2_t[i]) {
+        for (int k = tid; k < n; k += nt) buf[pad(k)] = sample(k);
         __syncthreads();
         block_fft_pad<T, E>(buf, logn_t[i], tw, twlen, false);
     } else {
