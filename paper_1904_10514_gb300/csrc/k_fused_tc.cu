@@ -18,9 +18,10 @@
 //     lo copies in shared memory (bank-conflict-free 16-byte stores);
 //   * one thread issues 4 K-steps x 3 tcgen05.mma (M=128, N=64, K=8) into a
 //     fresh accumulator and commits them to the stage's mbarrier;
-//   * meanwhile the threads load the next chunk into registers, then wait for
-//     the previous chunk's MMAs and add its accumulator (tcgen05.ld; warp w owns
-//     TMEM lanes 32 (w mod 4) .. +31) to FP32 registers.
+//   * meanwhile the threads load the chunk after next into registers (two
+//     register sets), then wait for the previous chunk's MMAs and add its
+//     accumulator (tcgen05.ld; warp w owns TMEM lanes 32 (w mod 4) .. +31) to
+//     FP32 registers.
 // Summing chunk partials in registers keeps every tensor-core accumulation
 // step at the size of one chunk's partial sum; the registers add 1 + K/32
 // terms with round-to-nearest.
@@ -99,6 +100,17 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, uint32
     return false;
 }
 
+// 16 consecutive FP32 columns of this warp's 32 TMEM lanes (one per thread).
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
 // 32 consecutive FP32 columns of this warp's 32 TMEM lanes (one per thread).
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
     asm volatile(
@@ -170,9 +182,10 @@ __global__ void __launch_bounds__(NT, 2) fused_tc_kernel(const float* __restrict
     const int bmap = b0 + bl;
     const cplx<float>* bsrc = bvec + (((int64_t)min(bmap, B - 1) * (p + 1) + m) * 2 + par) * P2;
 
-    float4 ra[AU];
-    float2 rb[4];
-    auto load_chunk = [&](int ch) {
+    // two register sets: the chunk after next is in flight while a chunk is split
+    float4 raA[AU], raB[AU];
+    float2 rbA[4], rbB[4];
+    auto load_chunk = [&](int ch, float4 (&ra)[AU], float2 (&rb)[4]) {
         const float4* src = reinterpret_cast<const float4*>(At + (int64_t)ch * rp * 32);
 #pragma unroll
         for (int j = 0; j < AU; ++j) {
@@ -187,7 +200,7 @@ __global__ void __launch_bounds__(NT, 2) fused_tc_kernel(const float* __restrict
     };
     // split the registers into the hi / lo tiles of stage st (rows of A past rp
     // keep stale values: they only feed accumulator rows that are not stored)
-    auto store_chunk = [&](int st) {
+    auto store_chunk = [&](int st, const float4 (&ra)[AU], const float2 (&rb)[4]) {
         unsigned char* Ahi = smem + st * STAGE;
         unsigned char* Alo = Ahi + TILE_A;
         unsigned char* Bhi = Ahi + 2 * TILE_A;
@@ -219,24 +232,31 @@ __global__ void __launch_bounds__(NT, 2) fused_tc_kernel(const float* __restrict
     for (int q = 0; q < 32; ++q) acc[q] = 0.f;
     const uint32_t tsub = dtmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(32 * (warp >> 2));
     auto drain = [&](int st) {
-        uint32_t v[32];
-        tmem_ld32(tsub + (uint32_t)(st * TN), v);
 #pragma unroll
-        for (int q = 0; q < 32; ++q) acc[q] += __uint_as_float(v[q]);
+        for (int h = 0; h < 2; ++h) {
+            uint32_t v[16];
+            tmem_ld16(tsub + (uint32_t)(st * TN + 16 * h), v);
+#pragma unroll
+            for (int q = 0; q < 16; ++q) acc[16 * h + q] += __uint_as_float(v[q]);
+        }
     };
 
     const int nchunks = (P2 + KC - 1) / KC;
     bool ok = true;
     int issued = 0;   // chunks whose MMAs were committed
-    load_chunk(0);
-    for (int ch = 0; ch < nchunks; ++ch) {
+    // one chunk: split it into stage ch & 1, issue its MMAs, start loading chunk
+    // ch + 2 into the same registers, then drain the accumulator of chunk ch - 1
+    auto step = [&](int ch, float4 (&ra)[AU], float2 (&rb)[4]) {
         const int st = ch & 1;
         // stage st was read by the MMAs of chunk ch - 2, which completed before
-        // their accumulator was drained in the previous iteration
-        store_chunk(st);
+        // their accumulator was drained in the previous step
+        store_chunk(st, ra, rb);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic smem writes -> tensor core
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        if (__syncthreads_or(!ok)) { ok = false; break; }
+        if (__syncthreads_or(!ok)) {
+            ok = false;
+            return false;
+        }
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t aH = smem_u32(smem + st * STAGE), aL = aH + TILE_A, bH = aH + 2 * TILE_A, bL = bH + TILE_B;
@@ -258,7 +278,7 @@ __global__ void __launch_bounds__(NT, 2) fused_tc_kernel(const float* __restrict
             mma_commit(smem_u32(&mbar[st]));
         }
         issued = ch + 1;
-        if (ch + 1 < nchunks) load_chunk(ch + 1);   // in flight during the MMAs
+        if (ch + 2 < nchunks) load_chunk(ch + 2, ra, rb);   // in flight during the next two steps
         if (ch > 0) {
             // chunk ch - 1: wait for its MMAs, add its accumulator to the registers
             const int sp = st ^ 1;
@@ -266,6 +286,13 @@ __global__ void __launch_bounds__(NT, 2) fused_tc_kernel(const float* __restrict
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             if (ok) drain(sp);
         }
+        return true;
+    };
+    load_chunk(0, raA, rbA);
+    if (nchunks > 1) load_chunk(1, raB, rbB);
+    for (int ch = 0; ch < nchunks; ch += 2) {
+        if (!step(ch, raA, rbA)) break;
+        if (ch + 1 < nchunks && !step(ch + 1, raB, rbB)) break;
     }
     if (ok) {
         const int cl = nchunks - 1;
