@@ -48,6 +48,7 @@ extern "C" {
 #define HPX_ERR_OOM -5      /* device memory for tables / workspace not available */
 #define HPX_ERR_TIMEOUT -6  /* a bounded device-side wait gave up                 */
 #define HPX_ERR_STATE -7    /* call not valid for this plan                       */
+#define HPX_ERR_NONFINITE -8 /* HPX_FLAG_CHECKED: an input held NaN or infinity   */
 
 #define HPX_FP32 0
 #define HPX_FP64 1
@@ -72,6 +73,19 @@ extern "C" {
  *   (tcgen05, 3xTF32: each operand split into two TF32 parts, three MMAs
  *   accumulated in FP32). */
 #define HPX_FLAG_SIMT 4u
+/* HPX_FLAG_CHECKED: every hpx_analyze / hpx_synthesize first checks on the host
+ *   that its two pointers are device (or managed) memory of the plan's device
+ *   (else HPX_ERR_ARG, nothing is launched), and on the device that the input
+ *   holds only finite values (else HPX_ERR_NONFINITE is recorded in the plan's
+ *   status word and reported by the next hpx_sync; the outputs are then
+ *   undefined).  Costs one extra read of the input. */
+#define HPX_FLAG_CHECKED 8u
+/* HPX_FLAG_AUTOTUNE: at plan creation, when the per-order operators were built,
+ *   time one analysis of a batch through them and through the run-time sweeps
+ *   (on scratch buffers allocated and freed inside hpx_plan_ex) and keep the
+ *   faster path; if that is the sweeps the operators are freed and
+ *   HPX_FLAG_SWEEPS is set (hpx_plan_flags). */
+#define HPX_FLAG_AUTOTUNE 16u
 
 typedef struct hpx_plan_s hpx_plan_s;
 
@@ -80,16 +94,22 @@ typedef struct hpx_plan_desc {
     int lmax;         /* largest degree returned, 0 <= lmax <= 2 nside; -1 = 2 nside */
     int batch;        /* number of maps processed per call, >= 1                  */
     int precision;    /* HPX_FP32 or HPX_FP64                                     */
-    unsigned flags;   /* HPX_FLAG_SWEEPS | HPX_FLAG_GRAPH | HPX_FLAG_SIMT, or 0    */
+    unsigned flags;   /* HPX_FLAG_* (SWEEPS, GRAPH, SIMT, CHECKED, AUTOTUNE), or 0  */
     /* Uneven batches: NULL, or `batch` values giving the nside of every map
      * (then `nside` is ignored).  Maps, coefficients and spectra are then
      * concatenated in the given order: map i occupies 12 nside_i^2 elements of
      * `maps`, n_alm(lmax_i) coefficients of `alm` and lmax_i + 1 values of `cl`,
      * with lmax_i = 2 nside_i when lmax = -1, else lmax (<= 2 min nside_i).  The
-     * plan holds one uniform sub-plan per distinct nside; maps of one nside that
-     * are adjacent in the batch are used in place, others are gathered into
-     * plan-owned staging buffers.  The caller's array must outlive the call. */
+     * plan holds one uniform sub-plan per distinct (nside, lmax); maps of one
+     * sub-plan that are adjacent in the batch are used in place, others are
+     * gathered into plan-owned staging buffers.  The caller's array must
+     * outlive the call. */
     const int* nsides;
+    /* Per-map degrees: NULL, or `batch` values lmax_i (-1 = 2 nside_i, else
+     * 0 <= lmax_i <= 2 nside_i) overriding `lmax`; the layouts are then
+     * concatenated as for `nsides` (with n_alm(lmax_i) and lmax_i + 1 entries per
+     * map), also when `nsides` is NULL (every map then has `nside`). */
+    const int* lmaxs;
 } hpx_plan_desc;
 
 /* Plan for `batch` real FP32 maps of one nside on the current CUDA device

@@ -36,6 +36,9 @@ EXPORTS = ["hpx_plan", "hpx_plan_ex", "hpx_set_stream", "hpx_analyze", "hpx_synt
 HPX_FLAG_SWEEPS = 1
 HPX_FLAG_GRAPH = 2
 HPX_FLAG_SIMT = 4
+HPX_FLAG_CHECKED = 8
+HPX_FLAG_AUTOTUNE = 16
+HPX_ERR_NONFINITE = -8
 HPX_NOALLOC_MAX_NSIDE = 128
 HPX_NSTAGES = 6
 STAGES = ["ring_fft", "poles", "spread", "lat_fft", "lat_solve", "rot_sweep"]   # HPX_FLAG_SWEEPS plans
@@ -45,7 +48,7 @@ STAGES_FUSED = ["ring_fft", "poles", "spread", "lat_fft", "fused_fsht", "unused"
 class hpx_plan_desc(ctypes.Structure):
     _fields_ = [("nside", ctypes.c_int), ("lmax", ctypes.c_int), ("batch", ctypes.c_int),
                 ("precision", ctypes.c_int), ("flags", ctypes.c_uint),
-                ("nsides", ctypes.POINTER(ctypes.c_int))]
+                ("nsides", ctypes.POINTER(ctypes.c_int)), ("lmaxs", ctypes.POINTER(ctypes.c_int))]
 
 
 class HpxError(RuntimeError):
@@ -109,13 +112,18 @@ def hpx_plan(nside, lmax, batch):
     return lib().hpx_plan(int(nside), int(lmax), int(batch))
 
 
-def hpx_plan_ex(nside, lmax=-1, batch=1, precision=HPX_FP32, flags=0, nsides=None):
-    arr = None
+def hpx_plan_ex(nside, lmax=-1, batch=1, precision=HPX_FP32, flags=0, nsides=None, lmaxs=None):
+    def arr(v):
+        return (ctypes.c_int * len(v))(*[int(x) for x in v]) if v is not None else None
+    ns_arr, l_arr = arr(nsides), arr(lmaxs)
     if nsides is not None:
-        arr = (ctypes.c_int * len(nsides))(*[int(v) for v in nsides])
         batch = len(nsides)
+    elif lmaxs is not None:
+        batch = len(lmaxs)
+    ptr = ctypes.POINTER(ctypes.c_int)
     d = hpx_plan_desc(int(nside), int(lmax), int(batch), int(precision), int(flags),
-                      ctypes.cast(arr, ctypes.POINTER(ctypes.c_int)) if arr is not None else None)
+                      ctypes.cast(ns_arr, ptr) if ns_arr is not None else None,
+                      ctypes.cast(l_arr, ptr) if l_arr is not None else None)
     return lib().hpx_plan_ex(ctypes.byref(d))
 
 
@@ -179,18 +187,28 @@ class Plan:
     """Owns one C plan; tensors must live on the plan's CUDA device."""
 
     def __init__(self, nside=None, lmax=-1, batch=1, precision="fp32", sweeps=False, graph=False, nsides=None,
-                 simt=False):
-        """Uniform batch (nside, batch) or uneven batch (nsides = nside of every map;
-        maps, alm and C_l are then 1-D tensors holding the maps concatenated)."""
+                 simt=False, lmaxs=None, checked=False, autotune=False):
+        """Uniform batch (nside, batch), or uneven batch (nsides = nside of every map
+        and/or lmaxs = lmax of every map; maps, alm and C_l are then 1-D tensors
+        holding the maps concatenated)."""
         import torch
         self.torch = torch
         self.nsides = None if nsides is None else [int(v) for v in nsides]
+        self.lmaxs = None if lmaxs is None else [int(v) for v in lmaxs]
         self.nside = int(nside) if nside is not None else 0
-        self.batch = len(self.nsides) if self.nsides is not None else int(batch)
+        if self.nsides is not None:
+            self.batch = len(self.nsides)
+        elif self.lmaxs is not None:
+            self.batch = len(self.lmaxs)
+        else:
+            self.batch = int(batch)
+        self.concat = self.nsides is not None or self.lmaxs is not None
         self.precision = HPX_FP64 if precision in ("fp64", "float64", HPX_FP64) else HPX_FP32
         self.device = torch.device("cuda", torch.cuda.current_device())
-        flags = (HPX_FLAG_SWEEPS if sweeps else 0) | (HPX_FLAG_GRAPH if graph else 0) | (HPX_FLAG_SIMT if simt else 0)
-        h = hpx_plan_ex(self.nside, lmax, self.batch, self.precision, flags, self.nsides)
+        flags = ((HPX_FLAG_SWEEPS if sweeps else 0) | (HPX_FLAG_GRAPH if graph else 0) |
+                 (HPX_FLAG_SIMT if simt else 0) | (HPX_FLAG_CHECKED if checked else 0) |
+                 (HPX_FLAG_AUTOTUNE if autotune else 0))
+        h = hpx_plan_ex(self.nside, lmax, self.batch, self.precision, flags, self.nsides, self.lmaxs)
         if not h:
             raise HpxError(hpx_last_error(), "hpx_plan_ex")
         self.handle = h
@@ -215,7 +233,7 @@ class Plan:
             raise HpxError(rc, what)
 
     def _shape(self, n):
-        return (n,) if self.nsides is not None else (self.batch, n)
+        return (n,) if self.concat else (self.batch, n)
 
     def _maps(self, maps):
         shape = self._shape(self.npix)
@@ -223,11 +241,17 @@ class Plan:
             raise ValueError("maps must be a CUDA %s tensor of shape %s" % (self.rdtype, shape))
         return maps.contiguous()
 
+    def map_lmax(self, i):
+        """lmax of map i."""
+        ns = self.nsides[i] if self.nsides is not None else self.nside
+        lm = self.lmaxs[i] if self.lmaxs is not None else self._lmax_arg
+        return 2 * ns if lm < 0 else lm
+
     @property
     def ncl(self):
-        if self.nsides is None:
+        if not self.concat:
             return self.lmax + 1
-        return sum((2 * n if self._lmax_arg < 0 else self._lmax_arg) + 1 for n in self.nsides)
+        return sum(self.map_lmax(i) + 1 for i in range(self.batch))
 
     def analyze(self, maps, out=None):
         """maps (batch, npix) -> alm (batch, n_alm) complex, m-major packing."""
@@ -251,7 +275,7 @@ class Plan:
         """C_l (batch, lmax+1) float64 of Eq. (APS)."""
         alm = alm.contiguous()
         if out is None:
-            out = self.torch.empty((self.ncl,) if self.nsides is not None else (self.batch, self.lmax + 1),
+            out = self.torch.empty((self.ncl,) if self.concat else (self.batch, self.lmax + 1),
                                    dtype=self.torch.float64, device=alm.device)
         self._stream()
         self._check(hpx_cl(self.handle, alm.data_ptr(), out.data_ptr()), "hpx_cl")

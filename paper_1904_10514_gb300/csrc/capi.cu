@@ -104,19 +104,31 @@ int analyze_impl(hpx_plan_s* P, const void* maps, void* alm) {
 
 int hpx_internal_set_error(int code) { return set_err(code); }
 
+namespace {
+int autotune(hpx_plan_s* P);
+}  // namespace
+
 extern "C" {
 
 hpx_plan_s* hpx_plan_ex(const hpx_plan_desc* d) {
     if (!d) { set_err(HPX_ERR_ARG); return nullptr; }
-    if ((d->flags & ~(unsigned)(HPX_FLAG_SWEEPS | HPX_FLAG_GRAPH | HPX_FLAG_SIMT)) != 0 || d->batch < 1) {
+    if ((d->flags & ~(unsigned)(HPX_FLAG_SWEEPS | HPX_FLAG_GRAPH | HPX_FLAG_SIMT | HPX_FLAG_CHECKED |
+                                HPX_FLAG_AUTOTUNE)) != 0 ||
+        d->batch < 1) {
         set_err(HPX_ERR_ARG);
         return nullptr;
     }
     if (d->precision != HPX_FP32 && d->precision != HPX_FP64) { set_err(HPX_ERR_ARG); return nullptr; }
-    if (d->nsides) {
+    if (d->nsides || d->lmaxs) {
         int err = HPX_OK;
         hpx_plan_s* G = hpx::group_create(d, &err);
         if (!G) { set_err(err); return nullptr; }
+        if (cudaMalloc(&G->d_status, sizeof(int)) != cudaSuccess) {
+            free_plan(G);
+            set_err(HPX_ERR_OOM);
+            return nullptr;
+        }
+        cudaMemset(G->d_status, 0, sizeof(int));
         if ((d->flags & HPX_FLAG_GRAPH) && cudaStreamCreateWithFlags(&G->cap, cudaStreamNonBlocking) != cudaSuccess) {
             free_plan(G);
             set_err(HPX_ERR_CUDA);
@@ -229,6 +241,7 @@ hpx_plan_s* hpx_plan_ex(const hpx_plan_desc* d) {
         cudaMemGetInfo(&freeB, &totalB);
         if (mBytes + ((size_t)1 << 30) < freeB && cudaMalloc(&P->fusedM, mBytes) == cudaSuccess) {
             P->bytes += (int64_t)mBytes;
+            P->fused_bytes = (int64_t)mBytes;
             cudaMemset(P->fusedM, 0, mBytes);   // zero the row padding
             P->fusedOff = up.vec(off);
             P->fusedTiles = up.vec(tiles);
@@ -255,6 +268,10 @@ hpx_plan_s* hpx_plan_ex(const hpx_plan_desc* d) {
         }
     }
     if (cudaDeviceSynchronize() != cudaSuccess) { free_plan(P); set_err(HPX_ERR_CUDA); return nullptr; }
+    if ((d->flags & HPX_FLAG_AUTOTUNE) && P->fusedM) {
+        const int rc = autotune(P);
+        if (rc != HPX_OK) { free_plan(P); set_err(rc); return nullptr; }
+    }
     set_err(HPX_OK);
     return P;
 }
@@ -275,11 +292,78 @@ int hpx_set_stream(hpx_plan_s* P, void* stream) {
     return set_err(HPX_OK);
 }
 
+}  // extern "C"
+
 namespace {
 
 int analyze_direct(hpx_plan_s* P, const void* maps, void* alm) {
+    if (P->flags & HPX_FLAG_CHECKED) {
+        const int64_t n = P->group ? P->total_npix : P->g.npix * P->g.B;
+        hpx::launch_finite_check(maps, n, P->precision == HPX_FP64, P->d_status, P->stream);
+    }
     if (P->group) return hpx::group_analyze(P, maps, alm);
     return P->precision == HPX_FP64 ? analyze_impl<double>(P, maps, alm) : analyze_impl<float>(P, maps, alm);
+}
+
+// HPX_FLAG_AUTOTUNE: time the operator path and the run-time sweeps on scratch
+// buffers (3 analyses each after one warm-up) and keep the faster.
+int autotune(hpx_plan_s* P) {
+    const size_t es = P->precision == HPX_FP64 ? 8 : 4;
+    void *maps = nullptr, *alm = nullptr;
+    if (cudaMalloc(&maps, (size_t)P->g.B * P->g.npix * es) != cudaSuccess) return HPX_ERR_OOM;
+    if (cudaMalloc(&alm, (size_t)P->g.B * P->g.nalm * es * 2) != cudaSuccess) {
+        cudaFree(maps);
+        return HPX_ERR_OOM;
+    }
+    cudaMemset(maps, 0, (size_t)P->g.B * P->g.npix * es);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float ms[2] = {0.f, 0.f};
+    void* M = P->fusedM;
+    for (int path = 0; path < 2; ++path) {   // 0: operators, 1: sweeps
+        P->fusedM = path == 0 ? M : nullptr;
+        analyze_direct(P, maps, alm);
+        cudaEventRecord(e0, P->stream);
+        for (int r = 0; r < 3; ++r) analyze_direct(P, maps, alm);
+        cudaEventRecord(e1, P->stream);
+        cudaEventSynchronize(e1);
+        cudaEventElapsedTime(&ms[path], e0, e1);
+    }
+    P->fusedM = M;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(maps);
+    cudaFree(alm);
+    if (cudaGetLastError() != cudaSuccess) return HPX_ERR_CUDA;
+    P->tuned_ms[0] = ms[0] / 3;
+    P->tuned_ms[1] = ms[1] / 3;
+    if (ms[1] < ms[0]) {   // keep the sweeps: release the operators
+        void* ptrs[] = {P->fusedM, P->fusedOff, P->fusedTiles, P->tcOff, P->tcFirst};
+        for (void* q : ptrs)
+            if (q) cudaFree(q);
+        P->fusedM = nullptr;
+        P->fusedOff = nullptr;
+        P->fusedTiles = nullptr;
+        P->tcOff = nullptr;
+        P->tcFirst = nullptr;
+        P->bytes -= P->fused_bytes;
+        P->fused_bytes = 0;
+        P->use_tc = false;
+        P->flags |= HPX_FLAG_SWEEPS;
+    }
+    return HPX_OK;
+}
+
+// HPX_FLAG_CHECKED, host side: both pointers must be device (or managed) memory
+// of the plan's device.
+bool device_pointer(const hpx_plan_s* P, const void* ptr) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) && a.device == P->device;
 }
 
 // HPX_FLAG_GRAPH: replay the graph captured for this (maps, alm) pair, or
@@ -316,14 +400,23 @@ int analyze_graph(hpx_plan_s* P, const void* maps, void* alm) {
 
 }  // namespace
 
+extern "C" {
+
 int hpx_analyze(hpx_plan_s* P, const void* maps, void* alm) {
     if (!P || !maps || !alm) return set_err(HPX_ERR_ARG);
+    if ((P->flags & HPX_FLAG_CHECKED) && (!device_pointer(P, maps) || !device_pointer(P, alm)))
+        return set_err(HPX_ERR_ARG);
     const int rc = (P->flags & HPX_FLAG_GRAPH) ? analyze_graph(P, maps, alm) : analyze_direct(P, maps, alm);
     return set_err(rc);
 }
 
 int hpx_synthesize(hpx_plan_s* P, const void* alm, void* maps) {
     if (!P || !alm || !maps) return set_err(HPX_ERR_ARG);
+    if (P->flags & HPX_FLAG_CHECKED) {
+        if (!device_pointer(P, maps) || !device_pointer(P, alm)) return set_err(HPX_ERR_ARG);
+        const int64_t n = 2 * (P->group ? P->total_nalm : P->g.nalm * P->g.B);
+        hpx::launch_finite_check(alm, n, P->precision == HPX_FP64, P->d_status, P->stream);
+    }
     if (P->group) return set_err(hpx::group_synthesize(P, alm, maps));
     if (P->precision == HPX_FP64) hpx::launch_adjoint<double>(P, (const double*)alm, (double*)maps, P->stream);
     else hpx::launch_adjoint<float>(P, (const float*)alm, (float*)maps, P->stream);
@@ -378,8 +471,9 @@ int hpx_sync(hpx_plan_s* P) {
     if (cudaStreamSynchronize(P->stream) != cudaSuccess) return set_err(HPX_ERR_CUDA);
     // device status words: the plan's own, or those of a group plan's sub-plans
     int first = HPX_OK;
-    std::vector<hpx_plan_s*> own{P};
-    for (hpx_plan_s* Q : (P->group ? P->subs : own)) {
+    std::vector<hpx_plan_s*> all{P};
+    if (P->group) all.insert(all.end(), P->subs.begin(), P->subs.end());
+    for (hpx_plan_s* Q : all) {
         if (!Q->d_status) continue;
         int st = 0;
         if (cudaMemcpy(&st, Q->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return set_err(HPX_ERR_CUDA);
@@ -425,6 +519,7 @@ const char* hpx_strerror(int code) {
         case HPX_ERR_OOM: return "out of device memory";
         case HPX_ERR_TIMEOUT: return "a bounded device-side wait timed out";
         case HPX_ERR_STATE: return "operation not valid for this plan";
+        case HPX_ERR_NONFINITE: return "an input held NaN or infinity";
         default: return "unknown error";
     }
 }

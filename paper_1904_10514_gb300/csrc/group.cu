@@ -1,6 +1,6 @@
-// Uneven batches: maps of different nside analysed by one plan.
+// Uneven batches: maps of different nside (or lmax) analysed by one plan.
 //
-// A group plan holds one uniform sub-plan per distinct nside.  The caller's
+// A group plan holds one uniform sub-plan per distinct (nside, lmax).  The caller's
 // maps, coefficients and spectra are concatenated in batch order; a sub-plan
 // whose maps are adjacent in the batch works on the caller's arrays in place,
 // otherwise its maps are gathered into a plan-owned staging buffer before the
@@ -48,13 +48,18 @@ hpx_plan_s* group_create(const hpx_plan_desc* d, int* err) {
     *err = HPX_ERR_ARG;
     const int B = d->batch;
     const bool fp64 = d->precision == HPX_FP64;
-    int nmin = 1 << 30;
+    // nside and lmax of map i
+    auto nside_of = [&](int i) { return d->nsides ? d->nsides[i] : d->nside; };
+    auto lmax_of = [&](int i) {
+        const int l = d->lmaxs ? d->lmaxs[i] : d->lmax;
+        return l < 0 ? 2 * nside_of(i) : l;
+    };
     for (int i = 0; i < B; ++i) {
-        const int ns = d->nsides[i];
+        const int ns = nside_of(i);
         if (ns < 2 || (ns & (ns - 1)) || ns > (fp64 ? 1024 : 2048)) { *err = HPX_ERR_NSIDE; return nullptr; }
-        nmin = std::min(nmin, ns);
+        const int l = d->lmaxs ? d->lmaxs[i] : d->lmax;
+        if (l < -1 || lmax_of(i) > 2 * ns) { *err = HPX_ERR_LMAX; return nullptr; }
     }
-    if (d->lmax < -1 || (d->lmax >= 0 && d->lmax > 2 * nmin)) { *err = HPX_ERR_LMAX; return nullptr; }
     hpx_plan_s* G = new (std::nothrow) hpx_plan_s();
     if (!G) { *err = HPX_ERR_OOM; return nullptr; }
     G->group = true;
@@ -65,12 +70,12 @@ hpx_plan_s* group_create(const hpx_plan_desc* d, int* err) {
     const size_t es = fp64 ? 8 : 4;
     // per-map offsets (bytes) in the caller's concatenated arrays
     std::vector<int64_t> mapoff(B), almoff(B), cloff(B);
-    std::map<int, std::vector<int>> byNside;
+    std::map<std::pair<int, int>, std::vector<int>> byNside;   // (nside, lmax) -> maps
     int64_t om = 0, oa = 0, oc = 0;
     int Lmax_all = 0;
     for (int i = 0; i < B; ++i) {
-        const int ns = d->nsides[i];
-        const int L = d->lmax < 0 ? 2 * ns : d->lmax;
+        const int ns = nside_of(i);
+        const int L = lmax_of(i);
         Lmax_all = std::max(Lmax_all, L);
         mapoff[i] = om * (int64_t)es;
         almoff[i] = oa * (int64_t)es * 2;
@@ -78,7 +83,7 @@ hpx_plan_s* group_create(const hpx_plan_desc* d, int* err) {
         om += 12LL * ns * ns;
         oa += nalm_of(L);
         oc += L + 1;
-        byNside[ns].push_back(i);
+        byNside[{ns, L}].push_back(i);
     }
     G->total_npix = om;
     G->total_nalm = oa;
@@ -91,13 +96,16 @@ hpx_plan_s* group_create(const hpx_plan_desc* d, int* err) {
     std::vector<int> idx;
     bool ok = true;
     for (auto& kv : byNside) {
-        const int ns = kv.first;
+        const int ns = kv.first.first;
         const std::vector<int>& maps = kv.second;
         hpx_plan_desc sd = *d;
         sd.nside = ns;
+        sd.lmax = kv.first.second;
         sd.batch = (int)maps.size();
-        sd.flags = d->flags & ~(unsigned)HPX_FLAG_GRAPH;
+        // the group checks its inputs itself; sub-plans get the rest of the flags
+        sd.flags = d->flags & ~(unsigned)(HPX_FLAG_GRAPH | HPX_FLAG_CHECKED);
         sd.nsides = nullptr;
+        sd.lmaxs = nullptr;
         hpx_plan_s* S = hpx_plan_ex(&sd);
         if (!S) { *err = hpx_last_error(); ok = false; break; }
         G->subs.push_back(S);

@@ -10,6 +10,8 @@
 // degree are then combined with Neumaier's compensated summation.  (Doing all
 // of it in FP64 with compensation per term made this kernel FP64-bound on a
 // GPU with low FP64 throughput.)
+#include <algorithm>
+
 #include "plan.h"
 
 namespace hpx {
@@ -67,6 +69,23 @@ void launch_cl(const hpx_plan_s* P, const T* alm, double* cl, cudaStream_t s) {
     const auto& g = P->g;
     dim3 grid((g.L + 1 + 31) / 32, g.B);
     cl_kernel<T><<<grid, 32 * kSlices, 0, s>>>((const cplx<T>*)alm, cl, g.L, g.nalm);
+}
+
+template <class T>
+__global__ void finite_check_kernel(const T* __restrict__ x, int64_t n, int* __restrict__ status) {
+    bool bad = false;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        bad |= !isfinite(x[i]);
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicExch(status, HPX_ERR_NONFINITE);
+}
+
+void launch_finite_check(const void* x, int64_t n, bool fp64, int* status, cudaStream_t s) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int blocks = std::max(1, std::min<int>(sms * 8, (int)((n + 255) / 256)));
+    if (fp64) finite_check_kernel<double><<<blocks, 256, 0, s>>>((const double*)x, n, status);
+    else finite_check_kernel<float><<<blocks, 256, 0, s>>>((const float*)x, n, status);
 }
 
 template void launch_cl<float>(const hpx_plan_s*, const float*, double*, cudaStream_t);

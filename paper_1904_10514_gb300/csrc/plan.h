@@ -80,7 +80,9 @@ struct hpx_plan_s {
     // rp x 32 floats in the MMA's core-matrix order, from float offset tcOff[t]
     int64_t* tcOff = nullptr;
     int* tcFirst = nullptr;        // first tile of (m, c)
-    int* d_status = nullptr;       // device status word (bounded waits that timed out)
+    int* d_status = nullptr;       // device status word (timed-out waits, non-finite inputs)
+    int64_t fused_bytes = 0;       // bytes of M
+    float tuned_ms[2] = {0.f, 0.f};   // HPX_FLAG_AUTOTUNE: ms per analysis, operators / sweeps
 
     // uneven batches (group plans): one uniform sub-plan per distinct nside
     bool group = false;
@@ -118,6 +120,9 @@ int fused_tile_rows(int B);
 template <class T> void launch_fused(const hpx_plan_s* P, T* alm, cudaStream_t s);
 void launch_fused_tc(const hpx_plan_s* P, float* alm, cudaStream_t s);
 void launch_timeout_selftest(const hpx_plan_s* P, int spins, cudaStream_t s);
+// HPX_FLAG_CHECKED: records HPX_ERR_NONFINITE in *status if any of the n reals
+// (float or double) at x is NaN or infinite.
+void launch_finite_check(const void* x, int64_t n, bool fp64, int* status, cudaStream_t s);
 template <class T> int build_fused(hpx_plan_s* P, const double* D64, const cplx<double>* skew64, cudaStream_t s);
 // float offset of element (row r of a tile with rp rows, column k) in the
 // tensor-core layout of M, relative to the tile's first chunk

@@ -235,3 +235,96 @@ def test_cl_same_coefficients(hp, prec, tol):
     for b in range(B):
         ref = hp2sph.cl(a[b].astype(np.complex128), L)
         assert np.max(np.abs(got[b] - ref) / ref) < tol
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("graph", [False, True], ids=["eager", "graph"])
+def test_per_map_lmax(hp, prec, graph):
+    """Per-map degrees (descriptor field lmaxs), with and without per-map nside:
+    one sub-plan per (nside, lmax); every map against the oracle at its lmax."""
+    cases = [([8, 16, 8, 16, 4], [5, -1, 16, 7, -1]), (None, [3, 32, -1, 3])]
+    for nsides, lmaxs in cases:
+        ns_list = nsides if nsides is not None else [16] * len(lmaxs)
+        maps = []
+        for k, ns in enumerate(ns_list):
+            mp, _ = skies.small_powerlaw_maps(ns, 1, seed=500 + k, alpha=2.0, noise=1e-3)
+            maps.append(mp[0].astype(np.float32).astype(np.float64) if prec == "fp32" else mp[0])
+        plan = hp.Plan(16 if nsides is None else None, -1, precision=prec, graph=graph, nsides=nsides,
+                       lmaxs=lmaxs)
+        dt = torch.float64 if prec == "fp64" else torch.float32
+        x = torch.as_tensor(np.concatenate(maps), dtype=dt, device="cuda")
+        for _ in range(2):
+            alm = plan.analyze(x)
+            cl = plan.cl(alm)
+            plan.sync()
+        a = alm.cpu().numpy().astype(np.complex128)
+        c = cl.cpu().numpy()
+        oa = oc = 0
+        for i, (ns, mp) in enumerate(zip(ns_list, maps)):
+            L = plan.map_lmax(i)
+            na = (L + 1) * (L + 2) // 2
+            ref = hp2sph.analyze(mp, ns, L)
+            assert per_l_error(a[oa:oa + na], ref, L).max() < TOL[prec], (nsides, lmaxs, i)
+            clr = hp2sph.cl(ref, L)
+            if L >= 2:
+                assert (np.abs(c[oc:oc + L + 1] - clr) / clr)[2:].max() < 2.5 * TOL[prec]
+            oa += na
+            oc += L + 1
+        assert oa == plan.nalm and oc == plan.ncl
+
+
+@pytest.mark.parametrize("uneven", [False, True], ids=["uniform", "group"])
+def test_checked_flag(hp, uneven):
+    """HPX_FLAG_CHECKED: a NaN or an infinity in the input is reported by the next
+    hpx_sync as HPX_ERR_NONFINITE (once); host pointers are refused before any
+    launch; clean inputs analyse as without the flag."""
+    ns = 16
+    nsides = [16, 8] if uneven else None
+    plan = hp.Plan(None if uneven else ns, -1, 2, "fp32", nsides=nsides, checked=True)
+    ref_plan = hp.Plan(None if uneven else ns, -1, 2, "fp32", nsides=nsides)
+    npix = plan.npix
+    rng = np.random.default_rng(1)
+    clean = rng.standard_normal(npix if uneven else (2, 12 * ns * ns)).astype(np.float32)
+    x = torch.as_tensor(clean, device="cuda")
+    a = plan.analyze(x)
+    plan.sync()
+    assert torch.equal(a, ref_plan.analyze(x))
+    for bad in (np.nan, np.inf, -np.inf):
+        y = x.clone()
+        y.view(-1)[y.numel() // 3] = float(bad)
+        plan.analyze(y)
+        with pytest.raises(hp.HpxError) as ei:
+            plan.sync()
+        assert ei.value.code == hp.HPX_ERR_NONFINITE
+        plan.sync()                      # reported once
+    # adjoint input checked too
+    g = torch.zeros_like(a)
+    g.view(-1)[5] = complex(float("nan"), 0.0)
+    plan.synthesize(g)
+    with pytest.raises(hp.HpxError):
+        plan.sync()
+    # host memory is refused before anything is launched
+    host_maps = np.zeros(x.numel(), dtype=np.float32)
+    host_alm = np.zeros(2 * a.numel(), dtype=np.float32)
+    rc = hp.lib().hpx_analyze(plan.handle, host_maps.ctypes.data, host_alm.ctypes.data)
+    assert rc == hp.HPX_ERR_ARG
+    rc = hp.lib().hpx_analyze(plan.handle, x.data_ptr(), host_alm.ctypes.data)
+    assert rc == hp.HPX_ERR_ARG
+    plan.sync()
+
+
+@pytest.mark.parametrize("prec,nside,B", [("fp32", 32, 12), ("fp64", 16, 1)])
+def test_autotune_keeps_a_correct_path(hp, prec, nside, B):
+    """HPX_FLAG_AUTOTUNE picks the operators or the sweeps; either way the
+    result matches the oracle."""
+    maps, _ = skies.small_powerlaw_maps(nside, B, seed=61, alpha=2.0, noise=1e-3)
+    if prec == "fp32":
+        maps = maps.astype(np.float32).astype(np.float64)
+    plan = hp.Plan(nside, -1, B, prec, autotune=True)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    a = plan.analyze(torch.as_tensor(maps, dtype=dt, device="cuda"))
+    plan.sync()
+    a = a.cpu().numpy().astype(np.complex128)
+    ref = hp2sph.analyze(maps, nside, 2 * nside)
+    for b in range(B):
+        assert per_l_error(a[b], ref[b], 2 * nside).max() < TOL[prec]

@@ -60,3 +60,16 @@ def test_invalid_arguments_rejected_before_any_cuda_call(hp):
     assert hp.hpx_cl(None, None, None) == hp.HPX_ERR_ARG
     assert hp.hpx_sync(None) == hp.HPX_ERR_ARG
     assert "nside" in hp.strerror(hp.HPX_ERR_NSIDE)
+
+
+def test_descriptor_fields_rejected_before_any_cuda_call(hp):
+    assert not hp.hpx_plan_ex(8, -1, 1, hp.HPX_FP32, 32)                  # unknown flag
+    assert hp.hpx_last_error() == hp.HPX_ERR_ARG
+    assert not hp.hpx_plan_ex(8, -1, 2, hp.HPX_FP32, 0, None, [16, 17])   # lmax_1 > 2 nside
+    assert hp.hpx_last_error() == hp.HPX_ERR_LMAX
+    assert not hp.hpx_plan_ex(8, -1, 2, hp.HPX_FP32, 0, None, [-2, 4])    # lmax_0 < -1
+    assert hp.hpx_last_error() == hp.HPX_ERR_LMAX
+    assert not hp.hpx_plan_ex(0, -1, 2, hp.HPX_FP32, 0, [8, 4], [16, 9])  # lmax_1 > 2 nside_1
+    assert hp.hpx_last_error() == hp.HPX_ERR_LMAX
+    assert not hp.hpx_plan_ex(0, -1, 2, hp.HPX_FP32, 0, [8, 12], None)    # nside not a power of two
+    assert hp.hpx_last_error() == hp.HPX_ERR_NSIDE
