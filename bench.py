@@ -296,6 +296,27 @@ def main():
            "h2d_bytes_per_step": int(host_maps.numel() * 4),
            "d2h_bytes_per_step": int(host_alm.numel() * 8 + host_cl.numel() * 8)}
 
+    # spherical-harmonic synthesis of the same batch (the inverse direction): alm -> maps
+    t_syn0 = time.perf_counter()
+    plan_syn = hp.Plan(NSIDE, LMAX, nb, "fp32", sweeps=True, synthesis=True)
+    torch.cuda.synchronize()
+    syn_build_s = time.perf_counter() - t_syn0
+    maps_syn = torch.empty_like(maps)
+    for _ in range(2):
+        plan_syn.sh_synthesis(alm, out=maps_syn)
+    torch.cuda.synchronize()
+    nsyn = max(2, min(args.steps, 5))
+    e0.record(stream)
+    for _ in range(nsyn):
+        plan_syn.sh_synthesis(alm, out=maps_syn)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_syn = e0.elapsed_time(e1) / nsyn / 1e3
+    synthesis = {"value": npix_step / t_syn / 1e9, "unit": "Gpix/s", "ms_per_step": t_syn * 1e3,
+                 "plan_build_s": syn_build_s}
+    plan_syn.close()
+    del maps_syn
+
     # the plain FP64 single-map form on the same GPU
     plan64 = hp.Plan(NSIDE, LMAX, 1, "fp64")
     m64 = maps[:1].double().contiguous()
@@ -363,7 +384,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": config_dict(), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": (len(names) + 1) * args.steps, "clocks": clk, "fp64_single_map": fp64,
+            "gpu_launches": (len(names) + 1) * args.steps, "clocks": clk, "fp64_single_map": fp64, "sh_synthesis_fp32": synthesis,
             "fp32_batched_over_fp64_single": value / world / fp64["value"],
             "stages_ms_per_launch": per_launch, "plan_build_s": plan_build_s, "plan_gb": plan.nbytes / 1e9,
             "plan_path": "sweeps" if plan.flags & hp.HPX_FLAG_SWEEPS else "per-order operators"}

@@ -86,6 +86,10 @@ extern "C" {
  *   faster path; if that is the sweeps the operators are freed and
  *   HPX_FLAG_SWEEPS is set (hpx_plan_flags). */
 #define HPX_FLAG_AUTOTUNE 16u
+/* HPX_FLAG_SYNTHESIS: also build the table of hpx_sh_synthesis (the expansion
+ *   of the order-0/1 Legendre functions in the latitude Fourier basis, FP64 on
+ *   the host at plan time, 4 (nside + 1)^2 entries). */
+#define HPX_FLAG_SYNTHESIS 32u
 
 typedef struct hpx_plan_s hpx_plan_s;
 
@@ -94,7 +98,7 @@ typedef struct hpx_plan_desc {
     int lmax;         /* largest degree returned, 0 <= lmax <= 2 nside; -1 = 2 nside */
     int batch;        /* number of maps processed per call, >= 1                  */
     int precision;    /* HPX_FP32 or HPX_FP64                                     */
-    unsigned flags;   /* HPX_FLAG_* (SWEEPS, GRAPH, SIMT, CHECKED, AUTOTUNE), or 0  */
+    unsigned flags;   /* HPX_FLAG_* (SWEEPS, GRAPH, SIMT, CHECKED, AUTOTUNE, SYNTHESIS), or 0 */
     /* Uneven batches: NULL, or `batch` values giving the nside of every map
      * (then `nside` is ignored).  Maps, coefficients and spectra are then
      * concatenated in the given order: map i occupies 12 nside_i^2 elements of
@@ -136,6 +140,19 @@ int hpx_analyze(hpx_plan_s* plan, const void* maps, void* alm);
  * of an input a_l0 is ignored (the analysis always returns a real a_l0).
  * Asynchronous. */
 int hpx_synthesize(hpx_plan_s* plan, const void* alm, void* maps);
+
+/* Spherical-harmonic synthesis of real maps (the direction the paper names as
+ * future work; Appendix A conventions):
+ *     f(theta_p, phi_p) = sum_{l <= lmax} sum_{|m| <= l} a_l^m Y_l^m(theta_p, phi_p)
+ * at every pixel centre, with a_l^{-m} = (-1)^m conj(a_l^m) and the imaginary
+ * part of a_l0 ignored.  alm -> maps in the layouts above.  Exact up to rounding
+ * and the NUFFT accuracy for any coefficients (it is not the inverse of
+ * hpx_analyze, which is a least-squares approximation).  The orders are
+ * converted to order 0/1 by the transposed Givens sweeps (Sec. 3.3), expanded in
+ * cos/sin(j theta), evaluated at the ring latitudes by a type-2 NUFFT and folded
+ * into each ring's nphi frequencies before an inverse FFT per ring.  Requires a
+ * plan made with HPX_FLAG_SYNTHESIS (else HPX_ERR_STATE).  Asynchronous. */
+int hpx_sh_synthesis(hpx_plan_s* plan, const void* alm, void* maps);
 
 /* Angular power spectrum of Eq. (APS) for real maps,
  * C_l = (|a_l0|^2 + 2 sum_{m=1}^{l} |a_lm|^2) / (2l + 1),

@@ -287,3 +287,35 @@ def cl(alm, lmax):
             terms += [2.0 * abs(alm[b, alm_index(l, m, lmax)]) ** 2 for m in range(1, l + 1)]
             out[b, l] = neumaier_sum(terms) / (2 * l + 1)
     return out[0] if single else out
+
+
+def synthesize(alm, nside, lmax):
+    """Spherical-harmonic synthesis at the pixel centres (Appendix A conventions):
+    f(theta, phi) = sum_{l <= lmax, |m| <= l} a_l^m Y_l^m(theta, phi) for a real map,
+    i.e. a_l^{-m} = (-1)^m conj(a_l^m), with Re(a_l0) used for m = 0.  Plain sums:
+    F_m(theta) = (1/sqrt(2 pi)) sum_l a_l^m Pbar_l^m(cos theta) per ring, then
+    f = Re F_0 + 2 Re sum_{m >= 1} F_m e^{i m phi} at every pixel of the ring.
+    ``alm`` (n_alm,) or (B, n_alm); returns (N,) or (B, N) float64."""
+    a = np.asarray(alm, dtype=np.complex128)
+    single = a.ndim == 1
+    a = a[None] if single else a
+    B = a.shape[0]
+    rings = geometry.ring_table(nside)
+    th = np.array([r["theta"] for r in rings])
+    x, st = np.cos(th), np.sin(th)
+    F = np.zeros((B, lmax + 1, len(rings)), dtype=np.complex128)
+    for m in range(lmax + 1):
+        tab = pbar_table(m, lmax, x, st)                      # (lmax - m + 1, rings)
+        i0 = alm_index(m, m, lmax)
+        am = a[:, i0:i0 + lmax - m + 1]                       # (B, lmax - m + 1)
+        F[:, m, :] = am @ tab / np.sqrt(2.0 * np.pi)
+    F[:, 0, :] = F[:, 0, :].real
+    out = np.zeros((B, geometry.npix(nside)))
+    m = np.arange(lmax + 1)
+    wm = np.where(m == 0, 1.0, 2.0)
+    for i, r in enumerate(rings):
+        phi = r["phi0"] + 2.0 * np.pi * np.arange(r["nphi"]) / r["nphi"]
+        E = np.exp(1j * np.outer(m, phi))                     # (lmax + 1, nphi)
+        out[:, r["start"]:r["start"] + r["nphi"]] = ((F[:, :, i] * wm) @ E).real
+    return out[0] if single else out
+

@@ -32,12 +32,13 @@ HPX_FP64 = 1
 EXPORTS = ["hpx_plan", "hpx_plan_ex", "hpx_set_stream", "hpx_analyze", "hpx_synthesize", "hpx_cl",
            "hpx_sync", "hpx_destroy", "hpx_npix", "hpx_nalm", "hpx_plan_lmax", "hpx_plan_bytes",
            "hpx_last_error", "hpx_strerror", "hpx_set_profiling", "hpx_stage_times",
-           "hpx_analyze_noalloc", "hpx_plan_flags", "hpx_selftest_timeout"]
+           "hpx_analyze_noalloc", "hpx_plan_flags", "hpx_selftest_timeout", "hpx_sh_synthesis"]
 HPX_FLAG_SWEEPS = 1
 HPX_FLAG_GRAPH = 2
 HPX_FLAG_SIMT = 4
 HPX_FLAG_CHECKED = 8
 HPX_FLAG_AUTOTUNE = 16
+HPX_FLAG_SYNTHESIS = 32
 HPX_ERR_NONFINITE = -8
 HPX_NOALLOC_MAX_NSIDE = 128
 HPX_NSTAGES = 6
@@ -93,6 +94,7 @@ def lib():
             "hpx_set_profiling": (i32, [vp, i32]),
             "hpx_analyze_noalloc": (i32, [i32, i32, vp, vp, vp]),
             "hpx_selftest_timeout": (i32, [vp, i32]),
+            "hpx_sh_synthesis": (i32, [vp, vp, vp]),
             "hpx_stage_times": (i32, [vp, ctypes.POINTER(ctypes.c_float), i32, ctypes.POINTER(ctypes.c_int)]),
         }
         for name, (res, args) in sig.items():
@@ -187,7 +189,7 @@ class Plan:
     """Owns one C plan; tensors must live on the plan's CUDA device."""
 
     def __init__(self, nside=None, lmax=-1, batch=1, precision="fp32", sweeps=False, graph=False, nsides=None,
-                 simt=False, lmaxs=None, checked=False, autotune=False):
+                 simt=False, lmaxs=None, checked=False, autotune=False, synthesis=False):
         """Uniform batch (nside, batch), or uneven batch (nsides = nside of every map
         and/or lmaxs = lmax of every map; maps, alm and C_l are then 1-D tensors
         holding the maps concatenated)."""
@@ -207,7 +209,7 @@ class Plan:
         self.device = torch.device("cuda", torch.cuda.current_device())
         flags = ((HPX_FLAG_SWEEPS if sweeps else 0) | (HPX_FLAG_GRAPH if graph else 0) |
                  (HPX_FLAG_SIMT if simt else 0) | (HPX_FLAG_CHECKED if checked else 0) |
-                 (HPX_FLAG_AUTOTUNE if autotune else 0))
+                 (HPX_FLAG_AUTOTUNE if autotune else 0) | (HPX_FLAG_SYNTHESIS if synthesis else 0))
         h = hpx_plan_ex(self.nside, lmax, self.batch, self.precision, flags, self.nsides, self.lmaxs)
         if not h:
             raise HpxError(hpx_last_error(), "hpx_plan_ex")
@@ -269,6 +271,16 @@ class Plan:
             out = self.torch.empty(self._shape(self.npix), dtype=self.rdtype, device=alm.device)
         self._stream()
         self._check(hpx_synthesize(self.handle, alm.data_ptr(), out.data_ptr()), "hpx_synthesize")
+        return out
+
+    def sh_synthesis(self, alm, out=None):
+        """Spherical-harmonic synthesis f = sum a_lm Y_lm at the pixel centres
+        (plan made with synthesis=True): alm (batch, n_alm) -> maps (batch, npix)."""
+        alm = alm.contiguous()
+        if out is None:
+            out = self.torch.empty(self._shape(self.npix), dtype=self.rdtype, device=alm.device)
+        self._stream()
+        self._check(lib().hpx_sh_synthesis(self.handle, alm.data_ptr(), out.data_ptr()), "hpx_sh_synthesis")
         return out
 
     def cl(self, alm, out=None):

@@ -57,7 +57,7 @@ void free_plan(hpx_plan_s* P) {
     auto& t = P->t;
     void* ptrs[] = {t.nphi, t.startN, t.startS, t.pow2, t.logn, t.fftL, t.logL, t.shOff, t.chOff,
                     t.bhOff, t.shift, t.chirp, t.bhat, t.twid, t.poleN, t.poleS, t.polew, t.rowptr,
-                    t.ent, t.entw, t.dec, t.D, t.angOff, t.ang, t.skOff, t.skew, t.skewT, t.nrowptr, t.nent, t.nentw, t.nstart, t.swts, t.hstart, t.hwts, P->Y, P->U, P->bvec,
+                    t.ent, t.entw, t.dec, t.D, t.angOff, t.ang, t.skOff, t.skew, t.skewT, t.nrowptr, t.nent, t.nentw, t.nstart, t.swts, t.hstart, t.hwts, t.Es, t.shifted, P->Y, P->U, P->bvec,
                     P->fusedM, P->fusedOff, P->fusedTiles, P->tcOff, P->tcFirst, P->d_status};
     for (void* q : ptrs)
         if (q) cudaFree(q);
@@ -113,7 +113,7 @@ extern "C" {
 hpx_plan_s* hpx_plan_ex(const hpx_plan_desc* d) {
     if (!d) { set_err(HPX_ERR_ARG); return nullptr; }
     if ((d->flags & ~(unsigned)(HPX_FLAG_SWEEPS | HPX_FLAG_GRAPH | HPX_FLAG_SIMT | HPX_FLAG_CHECKED |
-                                HPX_FLAG_AUTOTUNE)) != 0 ||
+                                HPX_FLAG_AUTOTUNE | HPX_FLAG_SYNTHESIS)) != 0 ||
         d->batch < 1) {
         set_err(HPX_ERR_ARG);
         return nullptr;
@@ -184,6 +184,12 @@ hpx_plan_s* hpx_plan_ex(const hpx_plan_desc* d) {
     t.spreadRows = tb.spreadRows;
     t.spreadD = tb.spreadD;
     t.D = up.real(tb.D, fp64);
+    t.shifted = up.vec(tb.shifted);
+    if (d->flags & HPX_FLAG_SYNTHESIS) {
+        std::vector<double> Es;
+        hpx::build_synthesis_table(tb, Es);
+        t.Es = up.real(Es, fp64);
+    }
     t.angOff = up.vec(tb.angOff); t.ang = up.real(tb.ang, fp64);
     t.skOff = up.vec(tb.skOff); t.skew = up.real(tb.skew, fp64); t.nq = tb.nq;
     t.skewT = up.real(tb.skewT, fp64);
@@ -420,6 +426,21 @@ int hpx_synthesize(hpx_plan_s* P, const void* alm, void* maps) {
     if (P->group) return set_err(hpx::group_synthesize(P, alm, maps));
     if (P->precision == HPX_FP64) hpx::launch_adjoint<double>(P, (const double*)alm, (double*)maps, P->stream);
     else hpx::launch_adjoint<float>(P, (const float*)alm, (float*)maps, P->stream);
+    if (cudaGetLastError() != cudaSuccess) return set_err(HPX_ERR_CUDA);
+    return set_err(HPX_OK);
+}
+
+int hpx_sh_synthesis(hpx_plan_s* P, const void* alm, void* maps) {
+    if (!P || !alm || !maps) return set_err(HPX_ERR_ARG);
+    if (!(P->flags & HPX_FLAG_SYNTHESIS)) return set_err(HPX_ERR_STATE);
+    if (P->flags & HPX_FLAG_CHECKED) {
+        if (!device_pointer(P, maps) || !device_pointer(P, alm)) return set_err(HPX_ERR_ARG);
+        const int64_t n = 2 * (P->group ? P->total_nalm : P->g.nalm * P->g.B);
+        hpx::launch_finite_check(alm, n, P->precision == HPX_FP64, P->d_status, P->stream);
+    }
+    if (P->group) return set_err(hpx::group_sh_synthesis(P, alm, maps));
+    if (P->precision == HPX_FP64) hpx::launch_sh_synthesis<double>(P, (const double*)alm, (double*)maps, P->stream);
+    else hpx::launch_sh_synthesis<float>(P, (const float*)alm, (float*)maps, P->stream);
     if (cudaGetLastError() != cudaSuccess) return set_err(HPX_ERR_CUDA);
     return set_err(HPX_OK);
 }

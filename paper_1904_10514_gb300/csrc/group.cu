@@ -187,23 +187,31 @@ int group_analyze(hpx_plan_s* G, const void* maps, void* alm) {
     return cudaGetLastError() == cudaSuccess ? HPX_OK : HPX_ERR_CUDA;
 }
 
-int group_synthesize(hpx_plan_s* G, const void* alm, void* maps) {
+namespace {
+// alm -> maps through every sub-plan with `fn` (the adjoint or the SH synthesis)
+int group_alm_to_maps(hpx_plan_s* G, const void* alm, void* maps, int (*fn)(hpx_plan_s*, const void*, void*)) {
     for (size_t s = 0; s < G->subs.size(); ++s) {
         hpx_plan_s* S = G->subs[s];
         hpx_set_stream(S, G->stream);
         const size_t es = G->precision == HPX_FP64 ? 8 : 4;
         if (G->sub_inplace[s]) {
-            const int rc = hpx_synthesize(S, (const unsigned char*)alm + G->sub_almoff[s],
-                                          (unsigned char*)maps + G->sub_mapoff[s]);
+            const int rc = fn(S, (const unsigned char*)alm + G->sub_almoff[s], (unsigned char*)maps + G->sub_mapoff[s]);
             if (rc != HPX_OK) return rc;
         } else {
             seg_copy(G, (int)s, alm, G->stage_alm[s], G->d_almoff, S->g.nalm * (int64_t)es * 2, true);
-            const int rc = hpx_synthesize(S, G->stage_alm[s], G->stage_maps[s]);
+            const int rc = fn(S, G->stage_alm[s], G->stage_maps[s]);
             if (rc != HPX_OK) return rc;
             seg_copy(G, (int)s, G->stage_maps[s], maps, G->d_mapoff, S->g.npix * (int64_t)es, false);
         }
     }
     return cudaGetLastError() == cudaSuccess ? HPX_OK : HPX_ERR_CUDA;
+}
+}  // namespace
+
+int group_synthesize(hpx_plan_s* G, const void* alm, void* maps) { return group_alm_to_maps(G, alm, maps, hpx_synthesize); }
+
+int group_sh_synthesis(hpx_plan_s* G, const void* alm, void* maps) {
+    return group_alm_to_maps(G, alm, maps, hpx_sh_synthesis);
 }
 
 int group_cl(hpx_plan_s* G, const void* alm, double* cl) {

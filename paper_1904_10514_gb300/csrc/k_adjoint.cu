@@ -54,7 +54,8 @@ template <class T, int KMAX>
 __global__ void __launch_bounds__(128) rot_adj_kernel(const T* __restrict__ alm, T* __restrict__ beta2,
                                                       const int64_t* __restrict__ skOff,
                                                       const cplx<T>* __restrict__ skewT, int nq, int P2, int L,
-                                                      int p, int B, int64_t nalm, int ngroups, int nitems) {
+                                                      int p, int B, int64_t nalm, int ngroups, int nitems,
+                                                      T wpos, bool dropim) {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (warp >= nitems) return;
@@ -73,8 +74,8 @@ __global__ void __launch_bounds__(128) rot_adj_kernel(const T* __restrict__ alm,
     // order-m chain from the weighted input coefficients
     int n = chain_len(m, c, L);
     const int b = col >> 1, ri = col & 1;
-    const T w = (m == 0) ? T(1) : T(2);
-    const bool drop = ri == 1 && (m == 0 || m == p);
+    const T w = (m == 0) ? T(1) : wpos;
+    const bool drop = dropim && ri == 1 && (m == 0 || m == p);
     const T* in = alm + (int64_t)b * nalm * 2 + ri;
     const int64_t base = (int64_t)m * (2 * L + 1 - m) / 2 + m + c;
     for (int i = 0; i < n; ++i) chain[(int64_t)i * ldc] = drop ? T(0) : w * in[(base + 2 * i) * 2];
@@ -313,7 +314,7 @@ void launch_adjoint(const hpx_plan_s* P, const T* alm, T* maps, cudaStream_t s) 
         const int blocks = (nitems * 32 + 127) / 128;
         constexpr int KMAX = sizeof(T) == 4 ? 32 : 16;
         rot_adj_kernel<T, KMAX><<<blocks, 128, 0, s>>>(alm, (T*)P->beta, t.skOff, (const cplx<T>*)t.skewT, t.nq,
-                                                       g.P2, g.L, g.p, g.B, g.nalm, ngroups, nitems);
+                                                       g.P2, g.L, g.p, g.B, g.nalm, ngroups, nitems, T(2), true);
     }
     {
         const int nmp = g.L / 2 + 1;
@@ -345,6 +346,139 @@ void launch_adjoint(const hpx_plan_s* P, const T* alm, T* maps, cudaStream_t s) 
                                                g.p, g.Q, g.npix);
     }
 }
+
+// ---------------------------------------------------------------- synthesis
+// Spherical-harmonic synthesis f(pixel) = sum_{l,m} a_l^m Y_l^m (real maps: m < 0
+// from a_l^{-m} = (-1)^m conj(a_l^m)), the inverse direction of the analysis:
+//   1. the transposed Givens sweeps (rot_adj_kernel, unweighted) take order m to
+//      order-0/1 Legendre coefficients (the sweeps are orthogonal: R^-1 = R^T);
+//   2. dense_adj_kernel with the table Es maps those to the coefficients X_j of
+//      F_m(t) = (1/sqrt(2 pi)) sum_l a_l^m Pbar_l^m(cos t) = sum_j X_j cos|sin(j t);
+//   3. nufft_adj_kernel evaluates the cosine / sine series at the latitude nodes
+//      (type-2 NUFFT; for even m it returns w_r F_m(t_r) with w_r = 2 on rings);
+//   4. ring_synth_kernel folds the orders into the nphi frequencies of each ring,
+//      F_m e^{i m phi0} summed over m = n mod nphi (m in [-lmax, lmax]), and
+//      transforms back to the ring's pixels (N and S rings packed as one complex
+//      sequence; Bluestein for the polar rings).
+template <class T>
+__global__ void __launch_bounds__(256) ring_synth_kernel(
+    const cplx<T>* __restrict__ Y, T* __restrict__ maps, const int* __restrict__ nphi_t,
+    const int* __restrict__ startN_t, const int* __restrict__ startS_t, const int* __restrict__ shifted_t,
+    const int* __restrict__ pow2_t, const int* __restrict__ logn_t, const int* __restrict__ fftL_t,
+    const int* __restrict__ logL_t, const int64_t* __restrict__ chOff_t, const int64_t* __restrict__ bhOff_t,
+    const cplx<T>* __restrict__ chirp, const cplx<T>* __restrict__ bhat, const cplx<T>* __restrict__ tw, int twlen,
+    int p, int L, int Q, int64_t npix, int npairs) {
+    extern __shared__ unsigned char smem_raw[];
+    cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw);
+    const int i = npairs - 1 - (int)blockIdx.x;
+    const int b = blockIdx.y;
+    const int n = nphi_t[i];
+    const int sN = startN_t[i], sS = startS_t[i];
+    const bool equator = (sN == sS);
+    const int sh = shifted_t[i];
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const cplx<T>* rowN = Y + ((int64_t)b * Q + (i + 1)) * (p + 1);
+    const cplx<T>* rowS = Y + ((int64_t)b * Q + (Q - 2 - i)) * (p + 1);
+    const bool bl = !pow2_t[i];
+    const cplx<T>* ch = chirp + chOff_t[i];
+    // G_m = F_m e^{i m phi0}, phi0 = sh pi / n; F_m = Y / 2 for even m (ring weight 2)
+    auto G = [&](const cplx<T>* row, int m) {
+        cplx<T> v = row[m];
+        if (!(m & 1)) v = scale(v, T(0.5));
+        if (m == 0) return mk<T>(v.r, T(0));
+        if (!sh) return v;
+        const int r = m % (2 * n);
+        T sn, cs;
+        if (sizeof(T) == 4) {
+            float a, c;
+            sincospif((float)r / (float)n, &a, &c);
+            sn = (T)a; cs = (T)c;
+        } else {
+            double a, c;
+            sincospi((double)r / (double)n, &a, &c);
+            sn = (T)a; cs = (T)c;
+        }
+        return mul(v, mk<T>(cs, sn));
+    };
+    for (int k = tid; k < n; k += nt) {
+        cplx<T> cN = mk<T>(T(0), T(0)), cS = cN;
+        for (int m = k; m <= L; m += n) {   // m = k + q n >= 0
+            cN = add(cN, G(rowN, m));
+            if (!equator) cS = add(cS, G(rowS, m));
+        }
+        for (int m = n - k; m <= L; m += n) {   // -m = k - q n < 0: G_{-m} = conj(G_m)
+            if (m == 0) continue;
+            cN = add(cN, conjg(G(rowN, m)));
+            if (!equator) cS = add(cS, conjg(G(rowS, m)));
+        }
+        // z = cN + i cS; the forward transform runs on conj(z) = (cN.r - cS.i) - i (cN.i + cS.r)
+        const cplx<T> zconj = mk<T>(cN.r - cS.i, -(cN.i + cS.r));
+        buf[k] = bl ? mul(zconj, ch[k]) : zconj;
+    }
+    if (bl) {
+        const int Lb = fftL_t[i];
+        for (int k = n + tid; k < Lb; k += nt) buf[k] = mk<T>(T(0), T(0));
+        __syncthreads();
+        const cplx<T>* bh = bhat + bhOff_t[i];
+        block_fft(buf, Lb, logL_t[i], tw, twlen, false);
+        for (int k = tid; k < Lb; k += nt) buf[k] = mul(buf[k], bh[k]);
+        __syncthreads();
+        block_fft(buf, Lb, logL_t[i], tw, twlen, true);
+        for (int k = tid; k < n; k += nt) buf[k] = mul(buf[k], ch[k]);
+        __syncthreads();
+    } else {
+        __syncthreads();
+        block_fft(buf, n, logn_t[i], tw, twlen, false);
+    }
+    // Z = conj(DFT(conj z)): north = Re Z, south = Im Z = -Im DFT(conj z)
+    T* f = maps + (int64_t)b * npix;
+    for (int k = tid; k < n; k += nt) {
+        f[sN + k] = buf[k].r;
+        if (!equator) f[sS + k] = -buf[k].i;
+    }
+}
+
+template <class T>
+void launch_sh_synthesis(const hpx_plan_s* P, const T* alm, T* maps, cudaStream_t s) {
+    const auto& g = P->g;
+    const auto& t = P->t;
+    {
+        const int ngroups = (2 * g.B + 31) / 32;
+        const int nitems = (g.L + 1) * 2 * ngroups;
+        const int blocks = (nitems * 32 + 127) / 128;
+        constexpr int KMAX = sizeof(T) == 4 ? 32 : 16;
+        rot_adj_kernel<T, KMAX><<<blocks, 128, 0, s>>>(alm, (T*)P->beta, t.skOff, (const cplx<T>*)t.skewT, t.nq,
+                                                       g.P2, g.L, g.p, g.B, g.nalm, ngroups, nitems, T(1), false);
+    }
+    {
+        const int nmp = g.L / 2 + 1;
+        dim3 grid((nmp * g.B + AC - 1) / AC, (g.P2 + AK - 1) / AK, 4);
+        dense_adj_kernel<T><<<grid, 256, 0, s>>>((const T*)t.Es, (const cplx<T>*)P->beta, (cplx<T>*)P->bvec, g.P2,
+                                                 g.p, g.L, g.B);
+    }
+    {
+        int logM = 0;
+        while ((1 << logM) < g.M) ++logM;
+        const size_t smem = (size_t)g.M * sizeof(cplx<T>);
+        cudaFuncSetAttribute(nufft_adj_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        dim3 grid(g.L + 1, g.B);
+        nufft_adj_kernel<T><<<grid, 512, smem, s>>>((const cplx<T>*)P->bvec, (cplx<T>*)P->Y, t.nrowptr, t.nent,
+                                                    (const T*)t.nentw, (const T*)t.dec, (const cplx<T>*)t.twid,
+                                                    g.Lmax, g.M, logM, g.p, g.Q, g.P2);
+    }
+    {
+        const size_t smem = (size_t)g.smem_ring * sizeof(cplx<T>);
+        cudaFuncSetAttribute(ring_synth_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        dim3 grid(g.npairs, g.B);
+        ring_synth_kernel<T><<<grid, 256, smem, s>>>(
+            (const cplx<T>*)P->Y, maps, t.nphi, t.startN, t.startS, t.shifted, t.pow2, t.logn, t.fftL, t.logL,
+            t.chOff, t.bhOff, (const cplx<T>*)t.chirp, (const cplx<T>*)t.bhat, (const cplx<T>*)t.twid, g.Lmax, g.p,
+            g.L, g.Q, g.npix, g.npairs);
+    }
+}
+
+template void launch_sh_synthesis<float>(const hpx_plan_s*, const float*, float*, cudaStream_t);
+template void launch_sh_synthesis<double>(const hpx_plan_s*, const double*, double*, cudaStream_t);
 
 template void launch_adjoint<float>(const hpx_plan_s*, const float*, float*, cudaStream_t);
 template void launch_adjoint<double>(const hpx_plan_s*, const double*, double*, cudaStream_t);

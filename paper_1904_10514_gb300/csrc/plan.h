@@ -30,6 +30,8 @@ struct DevTables {
     void* hwts = nullptr;                   // T [spreadH][M/2 + 1][2]
     int spreadH = 0, spreadRows = 0, spreadD = 0;
     void* D = nullptr;                      // T [2][2][P2][P2]
+    void* Es = nullptr;                     // T [2][2][P2][P2]: Legendre-0/1 -> latitude Fourier (synthesis)
+    int* shifted = nullptr;                 // per ring pair: first pixel at pi / nphi (1) or 0 (0)
     int64_t* angOff = nullptr;
     void* ang = nullptr;                    // cplx<T> (cos, sin)
     int64_t* skOff = nullptr;               // skewed angle blocks for the sweep wavefront
@@ -130,6 +132,8 @@ __host__ __device__ inline int64_t tc_elem(int rp, int r, int k) {
     return (int64_t)(k >> 5) * rp * 32 + (r >> 3) * 256 + ((k & 31) >> 2) * 32 + (r & 7) * 4 + (k & 3);
 }
 template <class T> void launch_adjoint(const hpx_plan_s* P, const T* alm, T* maps, cudaStream_t s);
+template <class T> void launch_sh_synthesis(const hpx_plan_s* P, const T* alm, T* maps, cudaStream_t s);
+int group_sh_synthesis(hpx_plan_s* P, const void* alm, void* maps);
 // uneven batches (group.cu)
 hpx_plan_s* group_create(const hpx_plan_desc* d, int* err);
 int group_analyze(hpx_plan_s* P, const void* maps, void* alm);

@@ -172,6 +172,7 @@ std::string build_tables(int nside, int lmax, bool fp64, PlanTables& t) {
         t.startN[i] = (j < ns) ? 2 * j * (j - 1) : 2 * ns * (ns - 1) + (j - ns) * 4 * ns;
         t.startS[i] = (int)(t.npix - t.startN[i] - n);
         phi0[i] = shifted ? kPi / n : 0.0;
+        t.shifted.push_back(shifted ? 1 : 0);
         theta[i] = ring_theta(j, ns);
         t.pow2[i] = is_pow2(n) ? 1 : 0;
         t.logn[i] = ilog2(n);
@@ -604,6 +605,42 @@ std::string build_tables(int nside, int lmax, bool fp64, PlanTables& t) {
                 }
     }
     return "";
+}
+
+void build_synthesis_table(const PlanTables& t, std::vector<double>& Es) {
+    const int p = t.p, L = t.L, P2 = t.P2;
+    Es.assign((size_t)4 * P2 * P2, 0.0);
+    // midpoint rule in t on [0, pi] with N points integrates cos(k t) exactly for
+    // 0 < k < 2N; the products Pbar_l B_j have degree <= L + p < 2N
+    const int N = p + 2;
+    std::vector<double> tn(N);
+    for (int n = 0; n < N; ++n) tn[n] = kPi * (n + 0.5) / N;
+    const double inv = 1.0 / std::sqrt(2.0 * kPi);
+    for (int m0 = 0; m0 < 2; ++m0) {
+        if (L < m0) continue;
+        std::vector<double> PL((size_t)(L + 1) * N, 0.0);   // Pbar_l^{m0}(cos t_n)
+#pragma omp parallel for schedule(static)
+        for (int n = 0; n < N; ++n) {
+            std::vector<double> buf(L + 1);
+            pbar01(m0, L, std::cos(tn[n]), std::sin(tn[n]), buf.data());
+            for (int l = m0; l <= L; ++l) PL[(size_t)l * N + n] = buf[l];
+        }
+#pragma omp parallel for schedule(dynamic, 4)
+        for (int j = m0; j <= p; ++j) {
+            std::vector<double> bj(N);
+            for (int n = 0; n < N; ++n) bj[n] = m0 ? std::sin(j * tn[n]) : std::cos(j * tn[n]);
+            // E_jl = 2 / (pi (1 + [j = 0])) * integral_0^pi Pbar_l(cos t) B_j(t) dt
+            const double scale = (2.0 / kPi) / (j == 0 ? 2.0 : 1.0) * (kPi / N);
+            const int par = j & 1;
+            for (int l = (m0 > par ? m0 + 1 : par); l <= L; l += 2) {
+                if (l < m0) continue;
+                const double* pl = &PL[(size_t)l * N];
+                double s = 0.0;
+                for (int n = 0; n < N; ++n) s += pl[n] * bj[n];
+                Es[(((size_t)m0 * 2 + par) * P2 + (l >> 1)) * P2 + (j >> 1)] = scale * s * inv;
+            }
+        }
+    }
 }
 
 }  // namespace hpx

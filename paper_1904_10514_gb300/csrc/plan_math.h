@@ -17,6 +17,7 @@ struct PlanTables {
 
     // ---- Step 1 (Sec. 3.1): per ring pair i (north ring i, south ring 4Ns-2-i)
     std::vector<int> nphi, startN, startS, pow2, logn, fftL, logL;
+    std::vector<int> shifted;    // 1: first pixel at longitude pi / nphi, 0: at 0
     std::vector<int64_t> shOff, chOff, bhOff;
     std::vector<double> shift;   // complex: (1/nphi) e^{-i m phi0}, Nyquist split folded in
     std::vector<double> chirp;   // complex: e^{-i pi k^2 / nphi} (Bluestein rings)
@@ -78,6 +79,14 @@ struct PlanTables {
 
 // Build all tables; returns an empty string on success or a message.
 std::string build_tables(int nside, int lmax, bool fp64, PlanTables& t);
+
+// Spherical-harmonic synthesis (the inverse direction of Sec. 3.3): the exact
+// expansion of the order-0/1 normalised Legendre functions in the latitude
+// Fourier basis, Pbar_l^{m0}(cos t) = sum_j E_{jl} cos(j t) (m0 = 0) or
+// sin(j t) (m0 = 1), j = l mod 2, scaled by 1/sqrt(2 pi) (Appendix A:
+// Y_l^m = Pbar_l^m e^{i m phi} / sqrt(2 pi)).  Laid out like D:
+// Es[m0][par][q][k] = E_{2k+par, 2q+par} / sqrt(2 pi).
+void build_synthesis_table(const PlanTables& t, std::vector<double>& Es);
 
 // Gauss-Legendre nodes/weights on [-1, 1] (Newton on the Legendre recurrence).
 void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w);

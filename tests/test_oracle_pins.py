@@ -429,3 +429,38 @@ def test_dense_transpose_dot():
     lhs = dense.alm_dot(hp2sph.analyze(f, ns, lmax), a, lmax)
     rhs = float(np.dot(f, dense.transpose_apply(A, a, lmax)[0]))
     assert lhs == pytest.approx(rhs, rel=1e-12)
+
+
+def test_synthesis_matches_scipy_brute_force():
+    """Oracle SH synthesis = brute-force sum of scipy's Y_l^m at every pixel
+    centre (negative orders from a_l^{-m} = (-1)^m conj(a_l^m))."""
+    rng = np.random.default_rng(11)
+    ns, L = 4, 8
+    a = rng.standard_normal(hp2sph.n_alm(L)) + 1j * rng.standard_normal(hp2sph.n_alm(L))
+    for l in range(L + 1):
+        a[hp2sph.alm_index(l, 0, L)] = a[hp2sph.alm_index(l, 0, L)].real
+    f = hp2sph.synthesize(a, ns, L)
+    th, ph = geometry.pixel_angles(ns)
+    g = np.zeros(len(th), dtype=complex)
+    for l in range(L + 1):
+        for m in range(-l, l + 1):
+            am = a[hp2sph.alm_index(l, abs(m), L)]
+            if m < 0:
+                am = (-1) ** m * np.conj(am)
+            g += am * sph_harm_y(l, m, th, ph)
+    assert np.max(np.abs(g.imag)) < 1e-13
+    np.testing.assert_allclose(f, g.real, atol=1e-13)
+
+
+def test_synthesis_then_analysis_exact_subspace():
+    """Analysis inverts synthesis exactly on span{Y_0^0, Y_2^0, Y_l^{+-1}}."""
+    rng = np.random.default_rng(12)
+    ns = 8
+    L = 2 * ns
+    a = np.zeros(hp2sph.n_alm(L), dtype=complex)
+    a[hp2sph.alm_index(0, 0, L)] = 0.7
+    a[hp2sph.alm_index(2, 0, L)] = -1.3
+    for l in range(1, L + 1):
+        a[hp2sph.alm_index(l, 1, L)] = rng.standard_normal() + 1j * rng.standard_normal()
+    back = hp2sph.analyze(hp2sph.synthesize(a, ns, L), ns, L)
+    np.testing.assert_allclose(back, a, atol=1e-12)
