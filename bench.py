@@ -325,7 +325,7 @@ def main():
 
     # spherical-harmonic synthesis of the same batch (the inverse direction): alm -> maps
     t_syn0 = time.perf_counter()
-    plan_syn = hp.Plan(NSIDE, LMAX, nb, "fp32", sweeps=True, synthesis=True)
+    plan_syn = hp.Plan(NSIDE, LMAX, nb, "fp32", synthesis=True)
     torch.cuda.synchronize()
     syn_build_s = time.perf_counter() - t_syn0
     maps_syn = torch.empty_like(maps)
@@ -340,7 +340,8 @@ def main():
     torch.cuda.synchronize()
     t_syn = e0.elapsed_time(e1) / nsyn / 1e3
     synthesis = {"value": npix_step / t_syn / 1e9, "unit": "Gpix/s", "ms_per_step": t_syn * 1e3,
-                 "plan_build_s": syn_build_s}
+                 "plan_build_s": syn_build_s,
+                 "path": "per-order synthesis operators" if plan_syn.flags & hp.HPX_FLAG_SWEEPS == 0 else "sweeps"}
     plan_syn.close()
     del maps_syn
 

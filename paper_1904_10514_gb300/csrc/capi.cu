@@ -58,7 +58,7 @@ void free_plan(hpx_plan_s* P) {
     void* ptrs[] = {t.nphi, t.startN, t.startS, t.pow2, t.logn, t.fftL, t.logL, t.shOff, t.chOff,
                     t.bhOff, t.shift, t.chirp, t.bhat, t.twid, t.poleN, t.poleS, t.polew, t.rowptr,
                     t.ent, t.entw, t.dec, t.D, t.angOff, t.ang, t.skOff, t.skew, t.skewT, t.nrowptr, t.nent, t.nentw, t.nstart, t.swts, t.hstart, t.hwts, t.Es, t.shifted, P->Y, P->U, P->bvec,
-                    P->fusedM, P->fusedOff, P->fusedTiles, P->tcOff, P->tcFirst, P->d_status};
+                    P->fusedM, P->fusedOff, P->fusedTiles, P->tcOff, P->tcFirst, P->d_status, P->synM};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     if (P->ev) {
@@ -185,10 +185,10 @@ hpx_plan_s* hpx_plan_ex(const hpx_plan_desc* d) {
     t.spreadD = tb.spreadD;
     t.D = up.real(tb.D, fp64);
     t.shifted = up.vec(tb.shifted);
+    std::vector<double> EsHost;
     if (d->flags & HPX_FLAG_SYNTHESIS) {
-        std::vector<double> Es;
-        hpx::build_synthesis_table(tb, Es);
-        t.Es = up.real(Es, fp64);
+        hpx::build_synthesis_table(tb, EsHost);
+        t.Es = up.real(EsHost, fp64);
     }
     t.angOff = up.vec(tb.angOff); t.ang = up.real(tb.ang, fp64);
     t.skOff = up.vec(tb.skOff); t.skew = up.real(tb.skew, fp64); t.nq = tb.nq;
@@ -259,9 +259,24 @@ hpx_plan_s* hpx_plan_ex(const hpx_plan_desc* d) {
             double* D64 = (double*)t.D;
             hpx::cplx<double>* sk64 = (hpx::cplx<double>*)t.skew;
             if (!fp64) { D64 = up.vec(tb.D); sk64 = (hpx::cplx<double>*)up.vec(tb.skew); }
-            int rc = up.ok ? (fp64 ? hpx::build_fused<double>(P, D64, sk64, nullptr)
-                                   : hpx::build_fused<float>(P, D64, sk64, nullptr))
+            int rc = up.ok ? (fp64 ? hpx::build_fused<double>(P, D64, sk64, nullptr, P->fusedM, P->use_tc)
+                                   : hpx::build_fused<float>(P, D64, sk64, nullptr, P->fusedM, P->use_tc))
                            : -1;
+            // synthesis operators R_{m,c} Es (row-major), when asked for and room allows
+            const size_t sBytes = (size_t)off.back() * P->fused_ldm * (fp64 ? 8 : 4);
+            cudaMemGetInfo(&freeB, &totalB);
+            if (rc == 0 && (d->flags & HPX_FLAG_SYNTHESIS) && sBytes + ((size_t)1 << 30) < freeB &&
+                cudaMalloc(&P->synM, sBytes) == cudaSuccess) {
+                P->bytes += (int64_t)sBytes;
+                cudaMemset(P->synM, 0, sBytes);
+                double* Es64 = fp64 ? (double*)t.Es : up.vec(EsHost);
+                rc = up.ok ? (fp64 ? hpx::build_fused<double>(P, Es64, sk64, nullptr, P->synM, false)
+                                   : hpx::build_fused<float>(P, Es64, sk64, nullptr, P->synM, false))
+                           : -1;
+                if (!fp64 && Es64) { cudaFree(Es64); P->bytes -= (int64_t)(EsHost.size() * 8); }
+            } else {
+                cudaGetLastError();
+            }
             if (!fp64) {
                 if (D64) { cudaFree(D64); P->bytes -= (int64_t)(tb.D.size() * 8); }
                 if (sk64) { cudaFree(sk64); P->bytes -= (int64_t)(tb.skew.size() * 8); }
@@ -345,11 +360,11 @@ int autotune(hpx_plan_s* P) {
     P->tuned_ms[0] = ms[0] / 3;
     P->tuned_ms[1] = ms[1] / 3;
     if (ms[1] < ms[0]) {   // keep the sweeps: release the operators
-        void* ptrs[] = {P->fusedM, P->fusedOff, P->fusedTiles, P->tcOff, P->tcFirst};
+        void* ptrs[] = {P->fusedM, P->synM ? nullptr : P->fusedOff, P->fusedTiles, P->tcOff, P->tcFirst};
         for (void* q : ptrs)
             if (q) cudaFree(q);
         P->fusedM = nullptr;
-        P->fusedOff = nullptr;
+        if (!P->synM) P->fusedOff = nullptr;
         P->fusedTiles = nullptr;
         P->tcOff = nullptr;
         P->tcFirst = nullptr;

@@ -442,15 +442,15 @@ template <class T>
 void launch_sh_synthesis(const hpx_plan_s* P, const T* alm, T* maps, cudaStream_t s) {
     const auto& g = P->g;
     const auto& t = P->t;
-    {
+    if (P->synM) {
+        launch_synth_apply<T>(P, alm, s);   // the sweeps and Es composed per (m, c)
+    } else {
         const int ngroups = (2 * g.B + 31) / 32;
         const int nitems = (g.L + 1) * 2 * ngroups;
         const int blocks = (nitems * 32 + 127) / 128;
         constexpr int KMAX = sizeof(T) == 4 ? 32 : 16;
         rot_adj_kernel<T, KMAX><<<blocks, 128, 0, s>>>(alm, (T*)P->beta, t.skOff, (const cplx<T>*)t.skewT, t.nq,
                                                        g.P2, g.L, g.p, g.B, g.nalm, ngroups, nitems, T(1), false);
-    }
-    {
         const int nmp = g.L / 2 + 1;
         dim3 grid((nmp * g.B + AC - 1) / AC, (g.P2 + AK - 1) / AK, 4);
         dense_adj_kernel<T><<<grid, 256, 0, s>>>((const T*)t.Es, (const cplx<T>*)P->beta, (cplx<T>*)P->bvec, g.P2,

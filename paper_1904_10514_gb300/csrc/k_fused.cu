@@ -181,6 +181,89 @@ __global__ void __launch_bounds__(TR* TC) fused_apply_kernel(const T* __restrict
     }
 }
 
+// ---------------------------------------------------------------- synthesis apply
+// The synthesis direction of the same composition: with Es the Legendre-0/1 ->
+// latitude-Fourier table in place of D, the build gives S_{m,c} = R_{m,c} Es
+// (rows i = degrees of the chain, columns k = latitude modes), and the
+// cosine/sine coefficients of F_m are the transposed contraction
+//     X[map][m][par][k] = sum_i S_{m,c}[i][k] a_{m+c+2i}^m[map].
+// Block = one (m, c, tile of 128 modes) x 16 maps; 256 threads, each 4 modes x
+// 2 maps; degrees in chunks of 16 staged in shared memory.
+template <class T>
+__global__ void __launch_bounds__(256) synth_apply_kernel(const T* __restrict__ S, const int64_t* __restrict__ moff,
+                                                          const cplx<T>* __restrict__ alm, cplx<T>* __restrict__ bvec,
+                                                          int P2, int ldm, int p, int L, int B, int64_t nalm,
+                                                          int nkt) {
+    constexpr int KT = 128, MB = 16, IC = 16;
+    __shared__ __align__(16) T As[IC][KT];
+    __shared__ cplx<T> Bs[IC][MB];
+    const int item = blockIdx.x;
+    const int kt = item % nkt, mc = item / nkt;
+    const int m = mc >> 1, c = mc & 1;
+    const int par = ((m & 1) + c) & 1;
+    const int nrows = chain_len(m, c, L);
+    const int k0 = kt * KT, b0 = blockIdx.y * MB;
+    const T* A = S + moff[(size_t)m * 2 + c] * ldm;
+    const int64_t base = (int64_t)m * (2 * L + 1 - m) / 2 + m + c;
+    const int tid = threadIdx.x, tk = tid & 31, tb = tid >> 5;
+    T accr[4][2], acci[4][2];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int q = 0; q < 2; ++q) { accr[a][q] = T(0); acci[a][q] = T(0); }
+    for (int i0 = 0; i0 < nrows; i0 += IC) {
+        for (int e = tid; e < IC * KT; e += 256) {
+            const int ii = e / KT, kk = e % KT;
+            const int i = i0 + ii, k = k0 + kk;
+            As[ii][kk] = (i < nrows && k < ldm) ? A[(size_t)i * ldm + k] : T(0);
+        }
+        for (int e = tid; e < IC * MB; e += 256) {
+            const int ii = e / MB, bb = e % MB;
+            const int i = i0 + ii, b = b0 + bb;
+            Bs[ii][bb] = (i < nrows && b < B) ? alm[(int64_t)b * nalm + base + 2 * i] : mk<T>(T(0), T(0));
+        }
+        __syncthreads();
+#pragma unroll
+        for (int ii = 0; ii < IC; ++ii) {
+            T a[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) a[r] = As[ii][tk * 4 + r];
+            const cplx<T> x0 = Bs[ii][tb * 2], x1 = Bs[ii][tb * 2 + 1];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                accr[r][0] += a[r] * x0.r;
+                acci[r][0] += a[r] * x0.i;
+                accr[r][1] += a[r] * x1.r;
+                acci[r][1] += a[r] * x1.i;
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        const int b = b0 + tb * 2 + q;
+        if (b >= B) continue;
+        cplx<T>* out = bvec + (((int64_t)b * (p + 1) + m) * 2 + par) * P2;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int k = k0 + tk * 4 + r;
+            if (k < P2) out[k] = mk<T>(accr[r][q], acci[r][q]);
+        }
+    }
+}
+
+template <class T>
+void launch_synth_apply(const hpx_plan_s* P, const T* alm, cudaStream_t s) {
+    const auto& g = P->g;
+    const int nkt = (g.P2 + 127) / 128;
+    dim3 grid((g.L + 1) * 2 * nkt, (g.B + 15) / 16);
+    synth_apply_kernel<T><<<grid, 256, 0, s>>>((const T*)P->synM, P->fusedOff, (const cplx<T>*)alm,
+                                               (cplx<T>*)P->bvec, g.P2, P->fused_ldm, g.p, g.L, g.B, g.nalm, nkt);
+}
+
+template void launch_synth_apply<float>(const hpx_plan_s*, const float*, cudaStream_t);
+template void launch_synth_apply<double>(const hpx_plan_s*, const double*, cudaStream_t);
+
 // Rows per block of the apply kernel for a batch of B maps (the plan builds its
 // tile list with this).
 int fused_tile_rows(int B) { return B > 8 ? 128 : (B > 2 ? 256 : 512); }
@@ -210,7 +293,8 @@ void launch_fused(const hpx_plan_s* P, T* alm, cudaStream_t s) {
 // Builds the per-order operators of a plan (called once by hpx_plan_ex).
 // D64 / skew64 are FP64 device copies of D and of the skewed sweep angles.
 template <class T>
-int build_fused(hpx_plan_s* P, const double* D64, const cplx<double>* skew64, cudaStream_t s) {
+int build_fused(hpx_plan_s* P, const double* D64, const cplx<double>* skew64, cudaStream_t s, void* out,
+                bool tiled) {
     const auto& g = P->g;
     const int ncplx = (g.P2 + 1) / 2;
     const int ngroups = (ncplx + 31) / 32;
@@ -222,9 +306,9 @@ int build_fused(hpx_plan_s* P, const double* D64, const cplx<double>* skew64, cu
         const int m_cnt = std::min(chunk, g.L + 1 - m_lo);
         const int nitems = m_cnt * 2 * ngroups;
         const int blocks = (nitems * 32 + 63) / 64;
-        build_fused_kernel<T><<<blocks, 64, 0, s>>>(D64, (T*)P->fusedM, P->fusedOff, P->t.skOff, skew64, P->t.nq,
+        build_fused_kernel<T><<<blocks, 64, 0, s>>>(D64, (T*)out, P->fusedOff, P->t.skOff, skew64, P->t.nq,
                                                     g.P2, P->fused_ldm, g.L, m_lo, m_cnt, ngroups, scratch,
-                                                    P->use_tc ? P->tcOff : nullptr, P->tcFirst);
+                                                    tiled ? P->tcOff : nullptr, P->tcFirst);
     }
     const cudaError_t e = cudaStreamSynchronize(s);
     cudaFree(scratch);
@@ -233,7 +317,7 @@ int build_fused(hpx_plan_s* P, const double* D64, const cplx<double>* skew64, cu
 
 template void launch_fused<float>(const hpx_plan_s*, float*, cudaStream_t);
 template void launch_fused<double>(const hpx_plan_s*, double*, cudaStream_t);
-template int build_fused<float>(hpx_plan_s*, const double*, const cplx<double>*, cudaStream_t);
-template int build_fused<double>(hpx_plan_s*, const double*, const cplx<double>*, cudaStream_t);
+template int build_fused<float>(hpx_plan_s*, const double*, const cplx<double>*, cudaStream_t, void*, bool);
+template int build_fused<double>(hpx_plan_s*, const double*, const cplx<double>*, cudaStream_t, void*, bool);
 
 }  // namespace hpx

@@ -84,6 +84,7 @@ struct hpx_plan_s {
     int* tcFirst = nullptr;        // first tile of (m, c)
     int* d_status = nullptr;       // device status word (timed-out waits, non-finite inputs)
     int64_t fused_bytes = 0;       // bytes of M
+    void* synM = nullptr;          // T, n_alm x ldm row-major: synthesis operators R_{m,c} Es (HPX_FLAG_SYNTHESIS)
     float tuned_ms[2] = {0.f, 0.f};   // HPX_FLAG_AUTOTUNE: ms per analysis, operators / sweeps
 
     // uneven batches (group plans): one uniform sub-plan per distinct nside
@@ -125,7 +126,9 @@ void launch_timeout_selftest(const hpx_plan_s* P, int spins, cudaStream_t s);
 // HPX_FLAG_CHECKED: records HPX_ERR_NONFINITE in *status if any of the n reals
 // (float or double) at x is NaN or infinite.
 void launch_finite_check(const void* x, int64_t n, bool fp64, int* status, cudaStream_t s);
-template <class T> int build_fused(hpx_plan_s* P, const double* D64, const cplx<double>* skew64, cudaStream_t s);
+template <class T>
+int build_fused(hpx_plan_s* P, const double* D64, const cplx<double>* skew64, cudaStream_t s, void* out, bool tiled);
+template <class T> void launch_synth_apply(const hpx_plan_s* P, const T* alm, cudaStream_t s);
 // float offset of element (row r of a tile with rp rows, column k) in the
 // tensor-core layout of M, relative to the tile's first chunk
 __host__ __device__ inline int64_t tc_elem(int rp, int r, int k) {
