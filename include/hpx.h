@@ -59,8 +59,9 @@ extern "C" {
  *   plan composes, for every order m and parity chain, D with the sweeps into
  *   one matrix M_{m,c} (built once in FP64 on the GPU from the same rotations,
  *   n_alm x (nside + 1) entries, 8.6 GB in FP32 at nside 1024) and the analysis
- *   applies those as one batched contraction; if that memory is not available
- *   the plan falls back to the sweeps and sets this flag (hpx_plan_flags). */
+ *   applies those as one batched contraction; if that memory is not available,
+ *   or the operators would exceed 24 GB (nside 2048 needs 69 GB and minutes of
+ *   FP64 build), the plan uses the sweeps and sets this flag (hpx_plan_flags). */
 #define HPX_FLAG_SWEEPS 1u
 /* HPX_FLAG_GRAPH: the first hpx_analyze call with a given (maps, alm) pair
  *   captures the plan's whole launch sequence into a CUDA graph (on a stream of

@@ -48,12 +48,18 @@ struct Uploader {
 void free_plan(hpx_plan_s* P) {
     if (!P) return;
     for (auto& e : P->graphs) cudaGraphExecDestroy(e.exec);
-    if (P->cap) cudaStreamDestroy(P->cap);
     if (P->group) {
+        // after a graph capture the sub-plans still name the group's capture
+        // stream: finish it and let them synchronise on the legacy stream
+        if (P->cap) cudaStreamSynchronize(P->cap);
+        for (hpx_plan_s* S : P->subs) S->stream = nullptr;
         hpx::group_free(P);
+        if (P->d_status) cudaFree(P->d_status);
+        if (P->cap) cudaStreamDestroy(P->cap);
         delete P;
         return;
     }
+    if (P->cap) cudaStreamDestroy(P->cap);
     auto& t = P->t;
     void* ptrs[] = {t.nphi, t.startN, t.startS, t.pow2, t.logn, t.fftL, t.logL, t.shOff, t.chOff,
                     t.bhOff, t.shift, t.chirp, t.bhat, t.twid, t.poleN, t.poleS, t.polew, t.rowptr,
@@ -245,7 +251,10 @@ hpx_plan_s* hpx_plan_ex(const hpx_plan_desc* d) {
         }
         size_t freeB = 0, totalB = 0;
         cudaMemGetInfo(&freeB, &totalB);
-        if (mBytes + ((size_t)1 << 30) < freeB && cudaMalloc(&P->fusedM, mBytes) == cudaSuccess) {
+        // operators above 24 GB (nside 2048: 69 GB, ~4 minutes of FP64 build) are
+        // not built by default: the per-call sweeps are used instead
+        const bool fits = mBytes <= ((size_t)24 << 30) && mBytes + ((size_t)1 << 30) < freeB;
+        if (fits && cudaMalloc(&P->fusedM, mBytes) == cudaSuccess) {
             P->bytes += (int64_t)mBytes;
             P->fused_bytes = (int64_t)mBytes;
             cudaMemset(P->fusedM, 0, mBytes);   // zero the row padding
