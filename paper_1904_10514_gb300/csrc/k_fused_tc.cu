@@ -33,6 +33,12 @@
 #include "plan.h"
 #include "plan_math.h"
 
+// 1: the operator tile goes to tensor memory (fused_tc_tmem_kernel, default);
+// 0: both operands through shared memory (fused_tc_kernel)
+#ifndef HPX_TC_TMEM_A
+#define HPX_TC_TMEM_A 1
+#endif
+
 namespace hpx {
 
 namespace {
@@ -73,6 +79,27 @@ __device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t adesc, uint64_
         "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n"
         :
         : "r"(dtmem), "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(acc));
+}
+
+// The same MMA with A read from tensor memory (lane = row, one 32-bit column per k).
+__device__ __forceinline__ void mma_tf32_ta(uint32_t dtmem, uint32_t atmem, uint64_t bdesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}\n"
+        :
+        : "r"(dtmem), "r"(atmem), "l"(bdesc), "r"(kIdesc), "r"(acc));
+}
+
+// 16 consecutive 32-bit columns of this warp's 32 TMEM lanes (one per thread).
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+        "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};"
+        :
+        : "r"(taddr), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]),
+          "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
+        : "memory");
 }
 
 __device__ __forceinline__ void mma_commit(uint32_t mbar) {
@@ -321,6 +348,182 @@ __global__ void __launch_bounds__(NT, 2) fused_tc_kernel(const float* __restrict
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(dtmem), "r"(2 * TN) : "memory");
 }
 
+// Variant with the operator tile in tensor memory: every thread loads the 16
+// consecutive k of one row of the chunk (row = its TMEM lane, k half = warp / 4),
+// splits them in registers and stores the hi and lo parts to TMEM with
+// tcgen05.st; the MMAs read A from TMEM and only b passes through shared memory.
+// TMEM per CTA (256 columns): accumulators of stage s at 64 s, A hi / lo of
+// stage s at 128 + 64 s and 128 + 64 s + 32.
+__global__ void __launch_bounds__(NT, 2) fused_tc_tmem_kernel(
+    const float* __restrict__ Mt, const int64_t* __restrict__ tcOff, const int* __restrict__ tiles,
+    const cplx<float>* __restrict__ bvec, cplx<float>* __restrict__ alm, int P2, int p, int L, int B, int64_t nalm,
+    int* __restrict__ status) {
+    extern __shared__ __align__(1024) unsigned char smem[];   // two stages of (Bhi, Blo)
+    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ uint32_t tmem_base;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m = tiles[3 * blockIdx.x], c = tiles[3 * blockIdx.x + 1], i0 = tiles[3 * blockIdx.x + 2];
+    const int par = ((m & 1) + c) & 1;
+    const int nrows = chain_len(m, c, L);
+    const int rp = (min(TM, nrows - i0) + 7) & ~7;
+    const int b0 = blockIdx.y * (TN / 2);
+    const float* At = Mt + tcOff[blockIdx.x];
+    const int row = 32 * (warp & 3) + lane, khalf = warp >> 2;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                     "r"(256)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        mbar_init(smem_u32(&mbar[0]), 1);
+        mbar_init(smem_u32(&mbar[1]), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t dtmem = tmem_base;
+    const uint32_t lanebits = (uint32_t)(32 * (warp & 3)) << 16;
+
+    const int bl = 8 * (warp & 3) + (lane & 7);
+    const int kq = 4 * (warp >> 2) + (lane >> 3);
+    const int bmap = b0 + bl;
+    const cplx<float>* bsrc = bvec + (((int64_t)min(bmap, B - 1) * (p + 1) + m) * 2 + par) * P2;
+
+    float4 raA[4], raB[4];
+    float2 rbA[4], rbB[4];
+    auto load_chunk = [&](int ch, float4 (&ra)[4], float2 (&rb)[4]) {
+        if (row < rp) {
+            const float* src = At + (int64_t)ch * rp * 32 + (row >> 3) * 256 + (row & 7) * 4;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) ra[q] = __ldg(reinterpret_cast<const float4*>(src + (4 * khalf + q) * 32));
+        }
+        const int k = ch * KC + 4 * kq;
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+            rb[e] = (bmap < B && k + e < P2) ? __ldg(reinterpret_cast<const float2*>(bsrc + k + e))
+                                             : make_float2(0.f, 0.f);
+    };
+    auto store_chunk = [&](int st, const float4 (&ra)[4], const float2 (&rb)[4]) {
+        uint32_t hi[16], lo[16];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float v[4] = {ra[q].x, ra[q].y, ra[q].z, ra[q].w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const Split sp = split(v[e]);
+                hi[4 * q + e] = sp.hi;
+                lo[4 * q + e] = sp.lo;
+            }
+        }
+        const uint32_t acol = 128 + 64 * st + 16 * khalf;
+        tmem_st16(dtmem + lanebits + acol, hi);
+        tmem_st16(dtmem + lanebits + acol + 32, lo);
+        unsigned char* Bhi = smem + st * (2 * TILE_B);
+        unsigned char* Blo = Bhi + TILE_B;
+        const uint32_t offr = (uint32_t)((bl >> 3) * 1024 + kq * 128 + (bl & 7) * 16);
+        const uint32_t offi = offr + 4 * 1024;
+        const Split r0 = split(rb[0].x), r1 = split(rb[1].x), r2 = split(rb[2].x), r3 = split(rb[3].x);
+        const Split q0 = split(rb[0].y), q1 = split(rb[1].y), q2 = split(rb[2].y), q3 = split(rb[3].y);
+        *reinterpret_cast<uint4*>(Bhi + offr) = make_uint4(r0.hi, r1.hi, r2.hi, r3.hi);
+        *reinterpret_cast<uint4*>(Blo + offr) = make_uint4(r0.lo, r1.lo, r2.lo, r3.lo);
+        *reinterpret_cast<uint4*>(Bhi + offi) = make_uint4(q0.hi, q1.hi, q2.hi, q3.hi);
+        *reinterpret_cast<uint4*>(Blo + offi) = make_uint4(q0.lo, q1.lo, q2.lo, q3.lo);
+    };
+
+    float acc[32];
+#pragma unroll
+    for (int q = 0; q < 32; ++q) acc[q] = 0.f;
+    const uint32_t tsub = dtmem + lanebits + (uint32_t)(32 * (warp >> 2));
+    auto drain = [&](int st) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            uint32_t v[16];
+            tmem_ld16(tsub + (uint32_t)(st * TN + 16 * h), v);
+#pragma unroll
+            for (int q = 0; q < 16; ++q) acc[16 * h + q] += __uint_as_float(v[q]);
+        }
+    };
+
+    const int nchunks = (P2 + KC - 1) / KC;
+    bool ok = true;
+    int issued = 0;
+    auto step = [&](int ch, float4 (&ra)[4], float2 (&rb)[4]) {
+        const int st = ch & 1;
+        // stage st (A in TMEM, b in shared memory) was read by the MMAs of chunk
+        // ch - 2, which completed before their accumulator was drained
+        store_chunk(st, ra, rb);
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        if (__syncthreads_or(!ok)) {
+            ok = false;
+            return false;
+        }
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t bH = smem_u32(smem + st * (2 * TILE_B)), bL = bH + TILE_B;
+            const uint32_t aH = dtmem + 128 + 64 * st, aL = aH + 32;
+            const uint32_t d = dtmem + (uint32_t)(st * TN);
+#pragma unroll
+            for (int ks = 0; ks < KC / 8; ++ks) {
+                const uint32_t o = ks * 256;
+                mma_tf32_ta(d, aH + 8 * ks, make_desc(bL + o, 128, 1024), ks > 0 ? 1u : 0u);
+                mma_tf32_ta(d, aL + 8 * ks, make_desc(bH + o, 128, 1024), 1u);
+            }
+#pragma unroll
+            for (int ks = 0; ks < KC / 8; ++ks) {
+                const uint32_t o = ks * 256;
+                mma_tf32_ta(d, aH + 8 * ks, make_desc(bH + o, 128, 1024), 1u);
+            }
+            mma_commit(smem_u32(&mbar[st]));
+        }
+        issued = ch + 1;
+        if (ch + 2 < nchunks) load_chunk(ch + 2, ra, rb);
+        if (ch > 0) {
+            const int sp = st ^ 1;
+            if (!mbar_wait(smem_u32(&mbar[sp]), (uint32_t)(((ch - 1) >> 1) & 1))) ok = false;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            if (ok) drain(sp);
+        }
+        return true;
+    };
+    load_chunk(0, raA, rbA);
+    if (nchunks > 1) load_chunk(1, raB, rbB);
+    for (int ch = 0; ch < nchunks; ch += 2) {
+        if (!step(ch, raA, rbA)) break;
+        if (ch + 1 < nchunks && !step(ch + 1, raB, rbB)) break;
+    }
+    if (ok) {
+        const int cl = nchunks - 1;
+        if (!mbar_wait(smem_u32(&mbar[cl & 1]), (uint32_t)((cl >> 1) & 1))) ok = false;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (ok) drain(cl & 1);
+    }
+    if (__syncthreads_or(!ok)) {
+        if (tid == 0) {
+            atomicExch(status, HPX_ERR_TIMEOUT);
+            if (issued > 0) mbar_wait(smem_u32(&mbar[(issued - 1) & 1]), (uint32_t)(((issued - 1) >> 1) & 1));
+        }
+    } else {
+        const int i = i0 + 32 * (warp & 3) + lane;
+        if (i < nrows) {
+            const int64_t base = (int64_t)m * (2 * L + 1 - m) / 2 + m + c + 2 * (int64_t)i;
+            float* out = reinterpret_cast<float*>(alm) + 2 * base + (warp >> 2);
+#pragma unroll
+            for (int q = 0; q < 32; ++q)
+                if (b0 + q < B) out[2 * (int64_t)(b0 + q) * nalm] = acc[q];
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(dtmem), "r"(256) : "memory");
+}
+
 // Failure-path self-test: a wait on an mbarrier that nothing completes gives up
 // after `spins` polls and reports like the operator kernel does.
 __global__ void timeout_selftest_kernel(int* __restrict__ status, uint32_t spins) {
@@ -337,9 +540,17 @@ void launch_timeout_selftest(const hpx_plan_s* P, int spins, cudaStream_t s) {
 
 void launch_fused_tc(const hpx_plan_s* P, float* alm, cudaStream_t s) {
     const auto& g = P->g;
+    dim3 grid(P->fused_ntiles, (g.B + 31) / 32);
+#if HPX_TC_TMEM_A
+    const size_t smem_t = 4 * TILE_B;
+    cudaFuncSetAttribute(fused_tc_tmem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_t);
+    fused_tc_tmem_kernel<<<grid, NT, smem_t, s>>>((const float*)P->fusedM, P->tcOff, P->fusedTiles,
+                                                  (const cplx<float>*)P->bvec, (cplx<float>*)alm, g.P2, g.p, g.L,
+                                                  g.B, g.nalm, P->d_status);
+    return;
+#endif
     const size_t smem = 2 * STAGE;
     cudaFuncSetAttribute(fused_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    dim3 grid(P->fused_ntiles, (g.B + 31) / 32);
     fused_tc_kernel<<<grid, NT, smem, s>>>((const float*)P->fusedM, P->tcOff, P->fusedTiles,
                                            (const cplx<float>*)P->bvec, (cplx<float>*)alm, g.P2, g.p, g.L, g.B,
                                            g.nalm, P->d_status);
