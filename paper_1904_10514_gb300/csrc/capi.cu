@@ -2,6 +2,7 @@
 // and the launch sequences of Algorithm 1.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstring>
 #include <new>
 #include <string>
@@ -64,7 +65,7 @@ void free_plan(hpx_plan_s* P) {
     void* ptrs[] = {t.nphi, t.startN, t.startS, t.pow2, t.logn, t.fftL, t.logL, t.shOff, t.chOff,
                     t.bhOff, t.shift, t.chirp, t.bhat, t.twid, t.poleN, t.poleS, t.polew, t.rowptr,
                     t.ent, t.entw, t.dec, t.D, t.angOff, t.ang, t.skOff, t.skew, t.skewT, t.nrowptr, t.nent, t.nentw, t.nstart, t.swts, t.hstart, t.hwts, t.Es, t.shifted, P->Y, P->U, P->bvec,
-                    P->fusedM, P->fusedOff, P->fusedTiles, P->tcOff, P->tcFirst, P->d_status, P->synM};
+                    P->fusedM, P->fusedOff, P->fusedTiles, P->tcOff, P->tcFirst, P->d_status, P->synM, P->ringList};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     if (P->ev) {
@@ -183,6 +184,21 @@ hpx_plan_s* hpx_plan_ex(const hpx_plan_desc* d) {
     t.twid = up.real(tb.twid, fp64);
     t.poleN = up.vec(tb.poleN); t.poleS = up.vec(tb.poleS); t.polew = up.vec(tb.polew);
     t.npole = (int)tb.polew.size();
+    {   // ring pairs grouped by transform length, longest first
+        std::vector<std::pair<int, int>> byN;
+        for (int i = 0; i < tb.npairs; ++i) byN.push_back({tb.pow2[i] ? tb.nphi[i] : tb.fftL[i], i});
+        std::stable_sort(byN.begin(), byN.end(), [](const std::pair<int, int>& a, const std::pair<int, int>& b) {
+            return a.first > b.first;
+        });
+        std::vector<int> list;
+        for (size_t k = 0; k < byN.size(); ++k) {
+            if (k == 0 || byN[k].first != byN[k - 1].first)
+                P->ringClasses.push_back({byN[k].first, (int)k, 0});
+            P->ringClasses.back().count++;
+            list.push_back(byN[k].second);
+        }
+        P->ringList = up.vec(list);
+    }
     t.rowptr = up.vec(tb.rowptr); t.ent = up.vec(tb.ent);
     t.entw = up.real(tb.entw, fp64); t.dec = up.real(tb.dec, fp64);
     t.nstart = up.vec(tb.nstart); t.swts = up.real(tb.swts, fp64); t.spreadE = tb.spreadE;

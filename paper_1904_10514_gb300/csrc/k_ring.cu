@@ -16,6 +16,8 @@
 // +-nphi/2 and zero padding for m > nphi/2 (the `shift` table folds 1/nphi,
 // the phase and the Nyquist factor together).  Output row r of Y holds the
 // coefficients m = 0..p of latitude node r (r = ring index + 1).
+#include <algorithm>
+
 #include "plan.h"
 
 namespace hpx {
@@ -31,11 +33,11 @@ __global__ void __launch_bounds__(kRingThreads, (E <= 16 ? 2 : 1)) ring_fft_kern
     const int64_t* __restrict__ chOff_t, const int64_t* __restrict__ bhOff_t,
     const cplx<T>* __restrict__ shift, const cplx<T>* __restrict__ chirp,
     const cplx<T>* __restrict__ bhat, const cplx<T>* __restrict__ tw, int twlen, int p, int Q,
-    int64_t npix, int npairs) {
+    int64_t npix, int npairs, const int* __restrict__ ringlist) {
     extern __shared__ unsigned char smem_raw[];
     cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw);
     // largest rings first: blockIdx.y = 0 is the equator
-    const int i = npairs - 1 - (int)blockIdx.y;
+    const int i = ringlist ? ringlist[blockIdx.y] : npairs - 1 - (int)blockIdx.y;
     const int b = blockIdx.x;
     const int n = nphi_t[i];
     const int sN = startN_t[i], sS = startS_t[i];
@@ -147,14 +149,25 @@ template <class T>
 void launch_ring_fft(const hpx_plan_s* P, const T* maps, cudaStream_t s) {
     const auto& g = P->g;
     const auto& t = P->t;
-    const size_t smem = (size_t)(g.smem_ring + g.smem_ring / 16) * sizeof(cplx<T>);
-    dim3 grid(g.B, g.npairs);
-    auto kern = g.smem_ring > 16 * kRingThreads ? ring_fft_kernel<T, 32> : ring_fft_kernel<T, 16>;
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    kern<<<grid, kRingThreads, smem, s>>>(
-        maps, (cplx<T>*)P->Y, t.nphi, t.startN, t.startS, t.pow2, t.logn, t.fftL, t.logL, t.shOff,
-        t.chOff, t.bhOff, (const cplx<T>*)t.shift, (const cplx<T>*)t.chirp, (const cplx<T>*)t.bhat,
-        (const cplx<T>*)t.twid, g.Lmax, g.p, g.Q, g.npix, g.npairs);
+    auto launch = [&](int N, int nrings, const int* list) {
+        // E elements per thread: blocks of N / E threads (at least one warp)
+        const bool big = N > 16 * kRingThreads;
+        const int threads = std::max(32, N / (big ? 32 : 16));
+        const size_t smem = (size_t)(N + N / 16) * sizeof(cplx<T>);
+        auto kern = big ? ring_fft_kernel<T, 32> : ring_fft_kernel<T, 16>;
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        dim3 grid(g.B, nrings);
+        kern<<<grid, threads, smem, s>>>(
+            maps, (cplx<T>*)P->Y, t.nphi, t.startN, t.startS, t.pow2, t.logn, t.fftL, t.logL, t.shOff,
+            t.chOff, t.bhOff, (const cplx<T>*)t.shift, (const cplx<T>*)t.chirp, (const cplx<T>*)t.bhat,
+            (const cplx<T>*)t.twid, g.Lmax, g.p, g.Q, g.npix, g.npairs, list);
+    };
+    if (!P->ringList) {   // one launch sized for the largest transform
+        launch(g.smem_ring, g.npairs, nullptr);
+        return;
+    }
+    // one launch per transform length, blocks sized to it, longest first
+    for (const auto& c : P->ringClasses) launch(c.N, c.count, P->ringList + c.first);
 }
 
 template <class T>

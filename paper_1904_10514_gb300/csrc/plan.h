@@ -63,6 +63,13 @@ struct hpx_plan_s {
     void* beta = nullptr;   // cplx<T> [B][p+1][2][P2]: order-0/1 Legendre coefficients (aliases Y)
     int64_t bytes = 0;
     int status = 0;
+    // ring FFT launches by transform length (pow2 rings: nphi; others: the
+    // Bluestein length): ring pairs ringList[first .. first + count - 1]
+    struct RingClass {
+        int N, first, count;
+    };
+    std::vector<RingClass> ringClasses;
+    int* ringList = nullptr;
     // profiling: events around the kernels of each recorded hpx_analyze call
     static constexpr int kMaxProf = 256;
     static constexpr int kStages = 6;
