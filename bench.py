@@ -42,6 +42,28 @@ def config_dict():
             "l2": "inputs larger than L2 (1.61 GB of maps per step)"}
 
 
+# ------------------------------------------------------------------ ranks (weak scaling, no collective on the data path)
+def first_map(rank, batch):
+    """Index of the first map of `rank`'s batch: every rank analyses its own maps."""
+    return rank * batch
+
+
+def max_over_ranks(seconds, world, device):
+    """The slowest rank's time (the job's time); one all-reduce outside the timed region."""
+    if world == 1:
+        return seconds
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_gpix(world, pixels_per_rank, seconds):
+    """Whole-job throughput: the pixels of all ranks over the slowest rank's time."""
+    return world * pixels_per_rank / seconds / 1e9
+
+
 # ------------------------------------------------------------------ accounting
 def chain_len(mp, c, L):
     return (L - mp - c) // 2 + 1 if L >= mp + c else 0
@@ -213,7 +235,7 @@ def main():
 
     ns, nb = args.nside, args.batch
     if ns == NSIDE:
-        maps_np = skies.workload_maps(WORKLOAD, nmaps=nb, first=rank * nb, dtype=np.float32)
+        maps_np = skies.workload_maps(WORKLOAD, nmaps=nb, first=first_map(rank, nb), dtype=np.float32)
     else:
         maps_np = skies.small_powerlaw_maps(ns, nb, seed=6000 + rank, alpha=2.0, noise=1e-3)[0].astype(np.float32)
     t_plan0 = time.perf_counter()
@@ -249,12 +271,9 @@ def main():
     stage_ms, ncalls = hp.hpx_stage_times(plan.handle)
     hp.hpx_set_profiling(plan.handle, 0)
     t_step = e0.elapsed_time(e1) / args.steps / 1e3
-    if world > 1:
-        tt = torch.tensor([t_step], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_step = float(tt.item())
+    t_step = max_over_ranks(t_step, world, "cuda")
     npix_step = nb * plan.npix
-    value = world * npix_step / t_step / 1e9
+    value = job_gpix(world, npix_step, t_step)
     if args.kernels_only:
         if rank == 0:
             per_launch = {n: stage_ms[k] / max(ncalls, 1) for k, n in enumerate(plan.stages)}
@@ -312,11 +331,8 @@ def main():
     torch.cuda.synchronize()
     barrier()
     t_e2e = e0.elapsed_time(e1) / args.steps / 1e3
-    if world > 1:
-        tt = torch.tensor([t_e2e], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_e2e = float(tt.item())
-    e2e = {"value": world * npix_step / t_e2e / 1e9, "unit": "Gpix/s",
+    t_e2e = max_over_ranks(t_e2e, world, "cuda")
+    e2e = {"value": job_gpix(world, npix_step, t_e2e), "unit": "Gpix/s",
            "h2d_bytes_per_step": int(host_maps.numel() * 4),
            "d2h_bytes_per_step": int(host_alm[0].numel() * 8 + host_cl[0].numel() * 8),
            "pipelined": "upload of step k+1 and download of step k-1 overlap the analysis of step k",
