@@ -361,6 +361,24 @@ def main():
     plan_syn.close()
     del maps_syn
 
+    # ablation: the paper's form of the latitude solve (CG on the normal equations per
+    # column) with the run-time sweeps, same batch
+    plan_cg = hp.Plan(NSIDE, LMAX, nb, "fp32", cg=True)
+    alm_cg = torch.empty_like(alm)
+    plan_cg.analyze(maps, out=alm_cg)
+    torch.cuda.synchronize()
+    ncg = 2
+    e0.record(stream)
+    for _ in range(ncg):
+        plan_cg.analyze(maps, out=alm_cg)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_cg = e0.elapsed_time(e1) / ncg / 1e3
+    cg = {"value": npix_step / t_cg / 1e9, "unit": "Gpix/s", "ms_per_step": t_cg * 1e3,
+          "max_abs_diff_vs_default": float((alm_cg - alm).abs().max() / alm.abs().max())}
+    plan_cg.close()
+    del alm_cg
+
     # the plain FP64 single-map form on the same GPU
     plan64 = hp.Plan(NSIDE, LMAX, 1, "fp64")
     m64 = maps[:1].double().contiguous()
@@ -428,7 +446,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": config_dict(), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": (len(names) + 1) * args.steps, "clocks": clk, "fp64_single_map": fp64, "sh_synthesis_fp32": synthesis,
+            "gpu_launches": (len(names) + 1) * args.steps, "clocks": clk, "fp64_single_map": fp64, "sh_synthesis_fp32": synthesis, "ablation_cg_latitude_solve": cg,
             "fp32_batched_over_fp64_single": value / world / fp64["value"],
             "stages_ms_per_launch": per_launch, "plan_build_s": plan_build_s, "plan_gb": plan.nbytes / 1e9,
             "plan_path": "sweeps" if plan.flags & hp.HPX_FLAG_SWEEPS else "per-order operators"}

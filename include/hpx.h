@@ -91,6 +91,14 @@ extern "C" {
  *   of the order-0/1 Legendre functions in the latitude Fourier basis, FP64 on
  *   the host at plan time, 4 (nside + 1)^2 entries). */
 #define HPX_FLAG_SYNTHESIS 32u
+/* HPX_FLAG_CG: solve the latitude least squares of every column by conjugate
+ *   gradients on its normal equations (Sec. 3.2.2; matrix-vector products by
+ *   FFT of the Toeplitz-plus-Hankel Gram matrix), then apply the change of basis
+ *   to order-0/1 Legendre functions and the Givens sweeps at run time.  The form
+ *   the paper describes, kept as an ablation of the default premultiplied
+ *   operators; implies HPX_FLAG_SWEEPS.  Stops at a relative residual of 1e-7
+ *   (FP32) or 1e-14 (FP64). */
+#define HPX_FLAG_CG 64u
 
 typedef struct hpx_plan_s hpx_plan_s;
 
@@ -99,7 +107,7 @@ typedef struct hpx_plan_desc {
     int lmax;         /* largest degree returned, 0 <= lmax <= 2 nside; -1 = 2 nside */
     int batch;        /* number of maps processed per call, >= 1                  */
     int precision;    /* HPX_FP32 or HPX_FP64                                     */
-    unsigned flags;   /* HPX_FLAG_* (SWEEPS, GRAPH, SIMT, CHECKED, AUTOTUNE, SYNTHESIS), or 0 */
+    unsigned flags;   /* HPX_FLAG_* (SWEEPS, GRAPH, SIMT, CHECKED, AUTOTUNE, SYNTHESIS, CG), or 0 */
     /* Uneven batches: NULL, or `batch` values giving the nside of every map
      * (then `nside` is ignored).  Maps, coefficients and spectra are then
      * concatenated in the given order: map i occupies 12 nside_i^2 elements of

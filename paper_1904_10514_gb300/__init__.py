@@ -39,6 +39,7 @@ HPX_FLAG_SIMT = 4
 HPX_FLAG_CHECKED = 8
 HPX_FLAG_AUTOTUNE = 16
 HPX_FLAG_SYNTHESIS = 32
+HPX_FLAG_CG = 64
 HPX_ERR_NONFINITE = -8
 HPX_NOALLOC_MAX_NSIDE = 128
 HPX_NSTAGES = 6
@@ -189,7 +190,7 @@ class Plan:
     """Owns one C plan; tensors must live on the plan's CUDA device."""
 
     def __init__(self, nside=None, lmax=-1, batch=1, precision="fp32", sweeps=False, graph=False, nsides=None,
-                 simt=False, lmaxs=None, checked=False, autotune=False, synthesis=False):
+                 simt=False, lmaxs=None, checked=False, autotune=False, synthesis=False, cg=False):
         """Uniform batch (nside, batch), or uneven batch (nsides = nside of every map
         and/or lmaxs = lmax of every map; maps, alm and C_l are then 1-D tensors
         holding the maps concatenated)."""
@@ -209,7 +210,8 @@ class Plan:
         self.device = torch.device("cuda", torch.cuda.current_device())
         flags = ((HPX_FLAG_SWEEPS if sweeps else 0) | (HPX_FLAG_GRAPH if graph else 0) |
                  (HPX_FLAG_SIMT if simt else 0) | (HPX_FLAG_CHECKED if checked else 0) |
-                 (HPX_FLAG_AUTOTUNE if autotune else 0) | (HPX_FLAG_SYNTHESIS if synthesis else 0))
+                 (HPX_FLAG_AUTOTUNE if autotune else 0) | (HPX_FLAG_SYNTHESIS if synthesis else 0) |
+                 (HPX_FLAG_CG if cg else 0))
         h = hpx_plan_ex(self.nside, lmax, self.batch, self.precision, flags, self.nsides, self.lmaxs)
         if not h:
             raise HpxError(hpx_last_error(), "hpx_plan_ex")

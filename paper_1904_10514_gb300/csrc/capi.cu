@@ -64,7 +64,7 @@ void free_plan(hpx_plan_s* P) {
     auto& t = P->t;
     void* ptrs[] = {t.nphi, t.startN, t.startS, t.pow2, t.logn, t.fftL, t.logL, t.shOff, t.chOff,
                     t.bhOff, t.shift, t.chirp, t.bhat, t.twid, t.poleN, t.poleS, t.polew, t.rowptr,
-                    t.ent, t.entw, t.dec, t.D, t.angOff, t.ang, t.skOff, t.skew, t.skewT, t.nrowptr, t.nent, t.nentw, t.nstart, t.swts, t.hstart, t.hwts, t.Es, t.shifted, P->Y, P->U, P->bvec,
+                    t.ent, t.entw, t.dec, t.D, t.angOff, t.ang, t.skOff, t.skew, t.skewT, t.nrowptr, t.nent, t.nentw, t.nstart, t.swts, t.hstart, t.hwts, t.Es, t.shifted, t.C, t.cgH, P->Y, P->U, P->bvec,
                     P->fusedM, P->fusedOff, P->fusedTiles, P->tcOff, P->tcFirst, P->d_status, P->synM, P->ringList};
     for (void* q : ptrs)
         if (q) cudaFree(q);
@@ -98,7 +98,12 @@ int analyze_impl(hpx_plan_s* P, const void* maps, void* alm) {
         }
         if (ev) cudaEventRecord(ev[5], s);
     } else {
-        hpx::launch_dense<T>(P, s);
+        if (P->flags & HPX_FLAG_CG) {
+            hpx::launch_cg<T>(P, s);                  // bvec <- T^{-1} bvec, column by column
+            hpx::launch_dense<T>(P, s, P->t.C);       // change of basis alone
+        } else {
+            hpx::launch_dense<T>(P, s);
+        }
         if (ev) cudaEventRecord(ev[5], s);
         hpx::launch_rot<T>(P, (T*)alm, s);
     }
@@ -120,7 +125,7 @@ extern "C" {
 hpx_plan_s* hpx_plan_ex(const hpx_plan_desc* d) {
     if (!d) { set_err(HPX_ERR_ARG); return nullptr; }
     if ((d->flags & ~(unsigned)(HPX_FLAG_SWEEPS | HPX_FLAG_GRAPH | HPX_FLAG_SIMT | HPX_FLAG_CHECKED |
-                                HPX_FLAG_AUTOTUNE | HPX_FLAG_SYNTHESIS)) != 0 ||
+                                HPX_FLAG_AUTOTUNE | HPX_FLAG_SYNTHESIS | HPX_FLAG_CG)) != 0 ||
         d->batch < 1) {
         set_err(HPX_ERR_ARG);
         return nullptr;
@@ -206,6 +211,12 @@ hpx_plan_s* hpx_plan_ex(const hpx_plan_desc* d) {
     t.spreadRows = tb.spreadRows;
     t.spreadD = tb.spreadD;
     t.D = up.real(tb.D, fp64);
+    if (d->flags & HPX_FLAG_CG) {
+        std::vector<double> H;
+        hpx::build_cg_tables(tb, t.cgN, H, t.cgk0, t.cgn);
+        t.cgH = up.real(H, fp64);
+        t.C = up.real(tb.C, fp64);
+    }
     t.shifted = up.vec(tb.shifted);
     std::vector<double> EsHost;
     if (d->flags & HPX_FLAG_SYNTHESIS) {
@@ -236,7 +247,8 @@ hpx_plan_s* hpx_plan_ex(const hpx_plan_desc* d) {
         set_err(HPX_ERR_CUDA);
         return nullptr;
     }
-    if (!(d->flags & HPX_FLAG_SWEEPS)) {
+    if (d->flags & HPX_FLAG_CG) P->flags |= HPX_FLAG_SWEEPS;   // CG runs with the per-call sweeps
+    if (!(P->flags & HPX_FLAG_SWEEPS)) {
         // per-order operators; without room for them the plan keeps the sweeps
         std::vector<int64_t> off((size_t)(L + 1) * 2 + 1, 0);
         std::vector<int> tiles;

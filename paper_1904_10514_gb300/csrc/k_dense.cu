@@ -93,15 +93,15 @@ __global__ void __launch_bounds__(256) dense_kernel(const T* __restrict__ D,
 }
 
 template <class T>
-void launch_dense(const hpx_plan_s* P, cudaStream_t s) {
+void launch_dense(const hpx_plan_s* P, cudaStream_t s, const void* Dmat) {
     const auto& g = P->g;
     const int nmp = g.L / 2 + 1;
     dim3 grid((nmp * g.B + TC - 1) / TC, (g.P2 + TQ - 1) / TQ, 4);
-    dense_kernel<T><<<grid, 256, 0, s>>>((const T*)P->t.D, (const cplx<T>*)P->bvec, (cplx<T>*)P->beta,
+    dense_kernel<T><<<grid, 256, 0, s>>>((const T*)(Dmat ? Dmat : P->t.D), (const cplx<T>*)P->bvec, (cplx<T>*)P->beta,
                                          g.P2, g.p, g.L, g.B);
 }
 
-template void launch_dense<float>(const hpx_plan_s*, cudaStream_t);
-template void launch_dense<double>(const hpx_plan_s*, cudaStream_t);
+template void launch_dense<float>(const hpx_plan_s*, cudaStream_t, const void*);
+template void launch_dense<double>(const hpx_plan_s*, cudaStream_t, const void*);
 
 }  // namespace hpx

@@ -30,6 +30,9 @@ struct DevTables {
     void* hwts = nullptr;                   // T [spreadH][M/2 + 1][2]
     int spreadH = 0, spreadRows = 0, spreadD = 0;
     void* D = nullptr;                      // T [2][2][P2][P2]
+    void* C = nullptr;                      // T [2][2][P2][P2]: change of basis alone (HPX_FLAG_CG)
+    void* cgH = nullptr;                    // cplx<T> [4][2][cgN]: CG matrix-vector tables
+    int cgN = 0, cgk0[4] = {0, 0, 0, 0}, cgn[4] = {0, 0, 0, 0};
     void* Es = nullptr;                     // T [2][2][P2][P2]: Legendre-0/1 -> latitude Fourier (synthesis)
     int* shifted = nullptr;                 // per ring pair: first pixel at pi / nphi (1) or 0 (0)
     int64_t* angOff = nullptr;
@@ -124,7 +127,8 @@ template <class T> void launch_poles(const hpx_plan_s* P, const T* maps, cudaStr
 template <class T> void launch_nufft(const hpx_plan_s* P, cudaStream_t s);
 template <class T> void launch_spread(const hpx_plan_s* P, cudaStream_t s);
 template <class T> void launch_lat_fft(const hpx_plan_s* P, cudaStream_t s);
-template <class T> void launch_dense(const hpx_plan_s* P, cudaStream_t s);
+template <class T> void launch_dense(const hpx_plan_s* P, cudaStream_t s, const void* Dmat = nullptr);
+template <class T> void launch_cg(const hpx_plan_s* P, cudaStream_t s);
 template <class T> void launch_rot(const hpx_plan_s* P, T* alm, cudaStream_t s);
 int fused_tile_rows(int B);
 template <class T> void launch_fused(const hpx_plan_s* P, T* alm, cudaStream_t s);

@@ -424,6 +424,7 @@ std::string build_tables(int nside, int lmax, bool fp64, PlanTables& t) {
         const int P2 = p / 2 + 1;
         t.P2 = P2;
         t.D.assign((size_t)4 * P2 * P2, 0.0);
+        t.C.assign((size_t)4 * P2 * P2, 0.0);
         std::vector<double> tc(2 * p + 1), ts(2 * p + 1);
         for (int k = 0; k <= 2 * p; ++k) {
             double sc = 0.0, ss = 0.0;
@@ -436,6 +437,8 @@ std::string build_tables(int nside, int lmax, bool fp64, PlanTables& t) {
             tc[k] = sc;
             ts[k] = ss;
         }
+        t.tc = tc;
+        t.ts = ts;
         const int G = p + 2;   // exact for the polynomial integrands of degree <= 2p
         std::vector<double> xg, wg;
         gauss_legendre(G, xg, wg);
@@ -490,8 +493,10 @@ std::string build_tables(int nside, int lmax, bool fp64, PlanTables& t) {
                         for (int g = 0; g < Gh; ++g) s += wg[g] * pl[g] * bj[g];
                         row[b] = 2.0 * s;   // the integrand is even in x
                     }
-                    chol_solve(T, nj, row.data());   // row <- T^{-1} row (T symmetric)
                     const int q = l >> 1;
+                    for (int b = 0; b < nj; ++b)
+                        t.C[(((size_t)mpar * 2 + par) * P2 + q) * P2 + (js[b] >> 1)] = s2pi * row[b];
+                    chol_solve(T, nj, row.data());   // row <- T^{-1} row (T symmetric)
                     for (int b = 0; b < nj; ++b) {
                         const int k = js[b] >> 1;
                         t.D[(((size_t)mpar * 2 + par) * P2 + q) * P2 + k] = s2pi * row[b];
@@ -639,6 +644,48 @@ void build_synthesis_table(const PlanTables& t, std::vector<double>& Es) {
                 for (int n = 0; n < N; ++n) s += pl[n] * bj[n];
                 Es[(((size_t)m0 * 2 + par) * P2 + (l >> 1)) * P2 + (j >> 1)] = scale * s * inv;
             }
+        }
+    }
+}
+
+void build_cg_tables(const PlanTables& t, int& N, std::vector<double>& H, int k0[4], int n[4]) {
+    const int P2 = t.P2;
+    int nmax = 0;
+    for (int blk = 0; blk < 4; ++blk) {
+        const int mpar = blk >> 1, par = blk & 1;
+        k0[blk] = (mpar == 1 && par == 0) ? 1 : 0;
+        const int k1 = par == 0 ? P2 - 1 : P2 - 2;
+        n[blk] = std::max(0, k1 - k0[blk] + 1);
+        nmax = std::max(nmax, n[blk]);
+    }
+    N = 1;
+    while (N < 3 * nmax - 2) N <<= 1;
+    H.assign((size_t)4 * 2 * N * 2, 0.0);
+    for (int blk = 0; blk < 4; ++blk) {
+        const int mpar = blk >> 1, par = blk & 1, nn = n[blk];
+        if (nn == 0) continue;
+        const std::vector<double>& tt = mpar ? t.ts : t.tc;
+        const double sg = mpar ? -1.0 : 1.0;
+        std::vector<double> cvec(N, 0.0), gvec(N, 0.0);
+        for (int d = 0; d < nn; ++d) {
+            cvec[d] = 0.5 * tt[2 * d];
+            if (d > 0) cvec[N - d] = 0.5 * tt[2 * d];
+        }
+        for (int e = 0; e <= 2 * nn - 2; ++e) gvec[e] = sg * 0.5 * tt[2 * e + 4 * k0[blk] + 2 * par];
+        double* Hc = &H[((size_t)blk * 2 + 0) * N * 2];
+        double* Hg = &H[((size_t)blk * 2 + 1) * N * 2];
+#pragma omp parallel for schedule(static)
+        for (int k = 0; k < N; ++k) {
+            double cr = 0, ci = 0, gr = 0, gi = 0;
+            for (int i = 0; i < N; ++i) {
+                if (cvec[i] == 0.0 && gvec[i] == 0.0) continue;
+                const double a = -2.0 * kPi * (double)(((int64_t)k * i) % N) / N;
+                const double cs = std::cos(a), sn = std::sin(a);
+                cr += cvec[i] * cs; ci += cvec[i] * sn;
+                gr += gvec[i] * cs; gi += gvec[i] * sn;
+            }
+            Hc[2 * k] = cr / N; Hc[2 * k + 1] = ci / N;
+            Hg[2 * k] = gr / N; Hg[2 * k + 1] = gi / N;
         }
     }
 }

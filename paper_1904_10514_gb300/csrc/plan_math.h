@@ -53,6 +53,11 @@ struct PlanTables {
     // ---- latitude least squares + Chebyshev -> order-0/1 Legendre (Sec. 3.2.2, 3.3)
     int P2 = 0;                  // p/2 + 1
     std::vector<double> D;       // [mpar][par][P2][P2], rows q -> l = 2q+par, cols k -> j = 2k+par
+    // The two factors of D = C T^{-1}: C = sqrt(2 pi) <Pbar_l, B_j> (the change of
+    // basis, same layout as D) and the normal-equation matrix T of each (mpar, par)
+    // block, T_ab = (tt[|j_a - j_b|] +- tt[j_a + j_b]) / 2 with tt = tc (cosine,
+    // +) or ts (sine, -), j = 0..2p (the conjugate-gradient form)
+    std::vector<double> C, tc, ts;
 
     // ---- Givens rotations of the order m' -> m'+2 connection (Sec. 3.3)
     std::vector<int64_t> angOff; // [(L+1) * 2]: offset of (m', chain c)
@@ -87,6 +92,15 @@ std::string build_tables(int nside, int lmax, bool fp64, PlanTables& t);
 // Y_l^m = Pbar_l^m e^{i m phi} / sqrt(2 pi)).  Laid out like D:
 // Es[m0][par][q][k] = E_{2k+par, 2q+par} / sqrt(2 pi).
 void build_synthesis_table(const PlanTables& t, std::vector<double>& Es);
+
+// Conjugate-gradient form of the latitude least squares (Sec. 3.2.2: CG on the
+// normal equations, matrix-vector products by FFT).  For block (mpar, par) the
+// unknowns are the modes k = k0 .. k0 + n - 1 (j = 2k + par); T x is
+// IFFT_N(Hc . X + Hg . X(-k)) restricted to the first n entries, X = FFT_N(x):
+// Hc holds the circulant embedding of the Toeplitz part, Hg the Hankel part,
+// both divided by N (N = the power of two >= 3n - 2).  Layout H[blk][2][N]
+// complex (blk = 2 mpar + par); k0[blk], n[blk].
+void build_cg_tables(const PlanTables& t, int& N, std::vector<double>& H, int k0[4], int n[4]);
 
 // Gauss-Legendre nodes/weights on [-1, 1] (Newton on the Legendre recurrence).
 void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w);
