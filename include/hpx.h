@@ -186,6 +186,8 @@ int hpx_plan_lmax(const hpx_plan_s* plan);
 int64_t hpx_plan_bytes(const hpx_plan_s* plan);
 /* Flags in effect (HPX_FLAG_SWEEPS set when the sweeps run at call time). */
 int hpx_plan_flags(const hpx_plan_s* plan);
+/* Kernel launches of one hpx_analyze call (ring FFTs: one per transform length). */
+int hpx_plan_launches(const hpx_plan_s* plan);
 
 /* Stage timing for profiling.  With profiling enabled (enable = 1) every
  * hpx_analyze records CUDA events on the plan's stream around each of its

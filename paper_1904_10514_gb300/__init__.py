@@ -32,7 +32,7 @@ HPX_FP64 = 1
 EXPORTS = ["hpx_plan", "hpx_plan_ex", "hpx_set_stream", "hpx_analyze", "hpx_synthesize", "hpx_cl",
            "hpx_sync", "hpx_destroy", "hpx_npix", "hpx_nalm", "hpx_plan_lmax", "hpx_plan_bytes",
            "hpx_last_error", "hpx_strerror", "hpx_set_profiling", "hpx_stage_times",
-           "hpx_analyze_noalloc", "hpx_plan_flags", "hpx_selftest_timeout", "hpx_sh_synthesis"]
+           "hpx_analyze_noalloc", "hpx_plan_flags", "hpx_selftest_timeout", "hpx_sh_synthesis", "hpx_plan_launches"]
 HPX_FLAG_SWEEPS = 1
 HPX_FLAG_GRAPH = 2
 HPX_FLAG_SIMT = 4
@@ -96,6 +96,7 @@ def lib():
             "hpx_analyze_noalloc": (i32, [i32, i32, vp, vp, vp]),
             "hpx_selftest_timeout": (i32, [vp, i32]),
             "hpx_sh_synthesis": (i32, [vp, vp, vp]),
+            "hpx_plan_launches": (i32, [vp]),
             "hpx_stage_times": (i32, [vp, ctypes.POINTER(ctypes.c_float), i32, ctypes.POINTER(ctypes.c_int)]),
         }
         for name, (res, args) in sig.items():

@@ -572,6 +572,22 @@ int hpx_plan_lmax(const hpx_plan_s* P) { return P ? P->g.L : -1; }
 int64_t hpx_plan_bytes(const hpx_plan_s* P) { return P ? P->bytes : 0; }
 int hpx_plan_flags(const hpx_plan_s* P) { return P ? (int)P->flags : -1; }
 
+int hpx_plan_launches(const hpx_plan_s* P) {
+    if (!P) return -1;
+    if (P->group) {
+        int n = 0;
+        for (const hpx_plan_s* S : P->subs) n += hpx_plan_launches(S);
+        for (size_t s = 0; s < P->subs.size(); ++s) n += P->sub_inplace[s] ? 0 : 2;   // gather + scatter
+        return n;
+    }
+    int n = P->ringList ? (int)P->ringClasses.size() : 1;   // ring FFTs
+    n += 3;                                                 // poles, spreading, grid FFTs
+    if (P->flags & HPX_FLAG_CG) n += 1;                     // CG solves
+    n += P->fusedM ? 1 : 2;                                 // operators, or D (or C) and the sweeps
+    if (P->flags & HPX_FLAG_CHECKED) n += 1;
+    return n;
+}
+
 int hpx_selftest_timeout(hpx_plan_s* P, int spins) {
     if (!P || spins < 1 || spins > (1 << 20)) return set_err(HPX_ERR_ARG);
     hpx_plan_s* Q = P->group ? P->subs[0] : P;   // a group reports through its sub-plans
