@@ -31,6 +31,8 @@ METRIC = "HEALPix analysis Gpix/s at Nside=1024 (batched FP32 vs plain FP64, err
 NSIDE, LMAX, BATCH = 1024, 2048, 32
 WORKLOAD = "bench_nside1024x32"
 MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# measured DRAM traffic / algorithmic bytes of a kernel (ncu capture, Nside 512, 32 maps)
+TRAFFIC_OVER_ALGORITHMIC = {"fused_fsht": 1.5613 / 1.4829}
 # FP32 SIMT peak: 152 SMs x 128 FP32 lanes x 2 flop/FMA x 2.070 GHz (maximum SM clock)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 
@@ -421,7 +423,13 @@ def main():
         roof = {"bound": "alu", "achieved": amount / t_dom / 1e12, "peak": peak, "unit": "TFLOP/s",
                 "peak_source": "FP32 FMA pipes: 152 SMs x 128 lanes x 2 flop x 2.070 GHz"}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = None
+    # DRAM bytes per launch: ncu (dram__bytes_read + write) over the algorithmic bytes of the
+    # same kernel at Nside 512 x 32 maps, scaled to this launch (traffic grows with the
+    # operator size like the algorithmic bytes: tile rows padded to 8, K to a multiple of 32)
+    ratio = TRAFFIC_OVER_ALGORITHMIC.get(dom)
+    roof["traffic"] = amount * ratio if (ratio and kind == "hbm") else None
+    roof["traffic_source"] = ("ncu at Nside 512, 32 maps: %.4f x the algorithmic bytes, scaled" % ratio
+                              if roof["traffic"] else None)
     roof["kernel"] = dom
     roof["per_launch_ms"] = per_launch[dom]
 
