@@ -274,12 +274,74 @@ void launch_spread(const hpx_plan_s* P, cudaStream_t s) {
                                              t.spreadH, H, g.p, g.Q, g.L, P->ldu);
 }
 
+// lat_fft_pair_kernel: the same outputs for two orders per block, one M-point
+// FFT for both.  The grid of an even order m is symmetric (u[M-t] = u[t]), that
+// of the odd order m+1 antisymmetric, so the transform Z of their sum splits as
+//     B_m(j) = (Z_j + Z_{M-j}) / 2,   B_{m+1}(j) = (Z_j - Z_{M-j}) / 2,
+// and only the modes j <= p and j >= M - p of Z are kept (in shared memory).
+template <class T, int E>
+__global__ void __launch_bounds__(512, (E <= 16 ? 2 : 1)) lat_fft_pair_kernel(
+    const cplx<T>* __restrict__ U, cplx<T>* __restrict__ bvec, const T* __restrict__ dec,
+    const cplx<T>* __restrict__ tw, int twlen, int M, int logM, int p, int L, int P2, int ldu) {
+    extern __shared__ unsigned char smem_raw[];
+    cplx<T>* u = reinterpret_cast<cplx<T>*>(smem_raw);   // M (padded)
+    cplx<T>* zlo = u + M + M / 16;                         // Z_j, j = 0..p
+    cplx<T>* zhi = zlo + (p + 1);                          // Z_{M-j}, j = 0..p
+    const int m0 = 2 * blockIdx.x, m1 = m0 + 1;
+    const int b = blockIdx.y;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int H = M >> 1;
+    const bool has1 = m1 <= L;
+    const cplx<T>* s0 = U + ((int64_t)b * (L + 1) + m0) * ldu;
+    const cplx<T>* s1 = U + ((int64_t)b * (L + 1) + (has1 ? m1 : m0)) * ldu;
+    auto ld = [&](int t) {
+        const bool lo = t <= H;
+        const int tt = lo ? t : M - t;
+        cplx<T> v = s0[tt];
+        if (has1) {
+            const cplx<T> w = s1[tt];
+            v = lo ? add(v, w) : sub(v, w);
+        }
+        return v;
+    };
+    auto st = [&](int j, cplx<T> v) {
+        if (j <= p) zlo[j] = v;
+        else if (j >= M - p) zhi[M - j] = v;
+    };
+    block_fft_io<T, E>(u, logM, tw, twlen, ld, st);
+    __syncthreads();
+    cplx<T>* out0 = bvec + ((int64_t)b * (p + 1) + m0) * 2 * P2;
+    cplx<T>* out1 = out0 + 2 * P2;
+    for (int j = tid; j <= p; j += nt) {
+        const cplx<T> a = zlo[j], c = (j == 0) ? zlo[0] : zhi[j];
+        const T dj = dec[j];
+        out0[(j & 1) * P2 + (j >> 1)] = scale(add(a, c), T(0.5) * dj);
+        if (has1) {
+            const cplx<T> v = scale(sub(a, c), T(0.5) * dj);   // B_{m+1}(j), times i/2 below
+            out1[(j & 1) * P2 + (j >> 1)] = mk<T>(T(-0.5) * v.i, T(0.5) * v.r);
+        }
+    }
+    if (tid == 0) {
+        out0[P2 + (P2 - 1)] = mk<T>(T(0), T(0));
+        if (has1) out1[P2 + (P2 - 1)] = mk<T>(T(0), T(0));
+    }
+}
+
 template <class T>
 void launch_lat_fft(const hpx_plan_s* P, cudaStream_t s) {
     const auto& g = P->g;
     int logM = 0;
     while ((1 << logM) < g.M) ++logM;
     const size_t smem = (size_t)(g.M + g.M / 16) * sizeof(cplx<T>);
+    if (logM >= 5) {   // two orders per block
+        const size_t smem2 = (size_t)(g.M + g.M / 16 + 2 * (g.p + 1)) * sizeof(cplx<T>);
+        auto kern2 = g.M > 16 * 512 ? lat_fft_pair_kernel<T, 32> : lat_fft_pair_kernel<T, 16>;
+        cudaFuncSetAttribute(kern2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
+        dim3 grid2((g.L + 2) / 2, g.B);
+        kern2<<<grid2, 512, smem2, s>>>((const cplx<T>*)P->U, (cplx<T>*)P->bvec, (const T*)P->t.dec,
+                                        (const cplx<T>*)P->t.twid, g.Lmax, g.M, logM, g.p, g.L, g.P2, P->ldu);
+        return;
+    }
     auto kern = g.M > 16 * 512 ? lat_fft_kernel<T, 32> : lat_fft_kernel<T, 16>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     dim3 grid(g.L + 1, g.B);
