@@ -324,6 +324,24 @@ def main():
                 ev_out[i].record(s_out)
         stream.wait_stream(s_out)
 
+    # the copies alone, to show what bounds the pipelined steps
+    c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(s_in):
+        dmaps[1].copy_(host_maps, non_blocking=True)
+        c0.record(s_in)
+        for _ in range(3):
+            dmaps[1].copy_(host_maps, non_blocking=True)
+        c1.record(s_in)
+    torch.cuda.synchronize()
+    h2d_gbs = 3 * host_maps.numel() * 4 / (c0.elapsed_time(c1) / 1e3) / 1e9
+    with torch.cuda.stream(s_out):
+        c0.record(s_out)
+        for _ in range(3):
+            host_alm[1].copy_(dalm[0], non_blocking=True)
+        c1.record(s_out)
+    torch.cuda.synchronize()
+    d2h_gbs = 3 * host_alm[1].numel() * 8 / (c0.elapsed_time(c1) / 1e3) / 1e9
+
     e2e_run(2)
     torch.cuda.synchronize()
     barrier()
@@ -338,6 +356,7 @@ def main():
            "h2d_bytes_per_step": int(host_maps.numel() * 4),
            "d2h_bytes_per_step": int(host_alm[0].numel() * 8 + host_cl[0].numel() * 8),
            "pipelined": "upload of step k+1 and download of step k-1 overlap the analysis of step k",
+           "h2d_gbs_alone": h2d_gbs, "d2h_gbs_alone": d2h_gbs,
            "host_result_matches_device": bool(torch.equal(host_alm[(args.steps - 1) % 2],
                                                           dalm[(args.steps - 1) % 2].cpu()))}
 
