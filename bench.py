@@ -32,7 +32,7 @@ NSIDE, LMAX, BATCH = 1024, 2048, 32
 WORKLOAD = "bench_nside1024x32"
 MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # measured DRAM traffic / algorithmic bytes of a kernel (ncu capture, Nside 512, 32 maps)
-TRAFFIC_OVER_ALGORITHMIC = {"fused_fsht": 1.5613 / 1.4829}
+TRAFFIC_OVER_ALGORITHMIC = {}
 # FP32 SIMT peak: 152 SMs x 128 FP32 lanes x 2 flop/FMA x 2.070 GHz (maximum SM clock)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 
@@ -104,8 +104,9 @@ def stage_work(ns, L, B, es=8):
         "lat_fft": ("hbm", B * (L + 1) * ((4 * ns + 1) * es + 2 * P2 * es)),
         "lat_solve": ("alu", B * dense),
         "rot_sweep": ("alu", B * rotation_count(L) * 12),
-        # per-order operators on the tensor cores: read M (n_alm x P2 FP32 entries, once per
-        # launch for up to 32 maps) and the right-hand sides, write the coefficients
+        # per-order operators on the tensor cores: read M (n_alm x P2 entries of 4 bytes, an FP16
+        # pair each, once per launch for up to 32 maps) and the right-hand sides, write the
+        # coefficients
         "fused_fsht": ("hbm", ((B + 31) // 32) * nalm * P2 * 4 + B * (L + 1) * 2 * P2 * es + B * nalm * es),
         "unused": ("alu", 0),
     }

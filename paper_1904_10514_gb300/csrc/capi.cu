@@ -16,6 +16,10 @@ namespace {
 
 thread_local int g_last_error = HPX_OK;
 
+// ring transforms of at most this many points run in one launch (blocks of
+// kRingMergeN / 16 threads)
+constexpr int kRingMergeN = 2048;
+
 int set_err(int code) {
     g_last_error = code;
     return code;
@@ -65,7 +69,7 @@ void free_plan(hpx_plan_s* P) {
     void* ptrs[] = {t.nphi, t.startN, t.startS, t.pow2, t.logn, t.fftL, t.logL, t.shOff, t.chOff,
                     t.bhOff, t.shift, t.chirp, t.bhat, t.twid, t.poleN, t.poleS, t.polew, t.rowptr,
                     t.ent, t.entw, t.dec, t.D, t.angOff, t.ang, t.skOff, t.skew, t.skewT, t.nrowptr, t.nent, t.nentw, t.nstart, t.swts, t.hstart, t.hwts, t.Es, t.shifted, t.C, t.cgH, P->Y, P->U, P->bvec,
-                    P->fusedM, P->fusedOff, P->fusedTiles, P->tcOff, P->tcFirst, P->d_status, P->synM, P->ringList};
+                    P->fusedM, P->fusedOff, P->fusedTiles, P->tcOff, P->tcFirst, P->tcRinv, P->bscale, P->d_status, P->synM, P->ringList};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     if (P->ev) {
@@ -197,7 +201,11 @@ hpx_plan_s* hpx_plan_ex(const hpx_plan_desc* d) {
         });
         std::vector<int> list;
         for (size_t k = 0; k < byN.size(); ++k) {
-            if (k == 0 || byN[k].first != byN[k - 1].first)
+            // transforms of kRingMergeN points or fewer share one launch, with
+            // blocks sized for the longest of them: alone, each of these short
+            // launches is bound by its latency, not by its work
+            const bool merged = byN[k].first <= kRingMergeN && k > 0 && byN[k - 1].first <= kRingMergeN;
+            if (k == 0 || (byN[k].first != byN[k - 1].first && !merged))
                 P->ringClasses.push_back({byN[k].first, (int)k, 0});
             P->ringClasses.back().count++;
             list.push_back(byN[k].second);
@@ -299,6 +307,7 @@ hpx_plan_s* hpx_plan_ex(const hpx_plan_desc* d) {
             int rc = up.ok ? (fp64 ? hpx::build_fused<double>(P, D64, sk64, nullptr, P->fusedM, P->use_tc)
                                    : hpx::build_fused<float>(P, D64, sk64, nullptr, P->fusedM, P->use_tc))
                            : -1;
+            if (rc == 0 && P->use_tc) rc = hpx::prepare_fused_tc(P);
             // synthesis operators R_{m,c} Es (row-major), when asked for and room allows
             const size_t sBytes = (size_t)off.back() * P->fused_ldm * (fp64 ? 8 : 4);
             cudaMemGetInfo(&freeB, &totalB);
@@ -397,7 +406,8 @@ int autotune(hpx_plan_s* P) {
     P->tuned_ms[0] = ms[0] / 3;
     P->tuned_ms[1] = ms[1] / 3;
     if (ms[1] < ms[0]) {   // keep the sweeps: release the operators
-        void* ptrs[] = {P->fusedM, P->synM ? nullptr : P->fusedOff, P->fusedTiles, P->tcOff, P->tcFirst};
+        void* ptrs[] = {P->fusedM, P->synM ? nullptr : P->fusedOff, P->fusedTiles, P->tcOff, P->tcFirst,
+                        P->tcRinv, P->bscale};
         for (void* q : ptrs)
             if (q) cudaFree(q);
         P->fusedM = nullptr;
@@ -405,6 +415,8 @@ int autotune(hpx_plan_s* P) {
         P->fusedTiles = nullptr;
         P->tcOff = nullptr;
         P->tcFirst = nullptr;
+        P->tcRinv = nullptr;
+        P->bscale = nullptr;
         P->bytes -= P->fused_bytes;
         P->fused_bytes = 0;
         P->use_tc = false;

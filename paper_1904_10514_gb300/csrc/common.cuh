@@ -20,6 +20,21 @@ template <class T> __device__ __forceinline__ cplx<T> mul(cplx<T> a, cplx<T> b) 
 template <class T> __device__ __forceinline__ cplx<T> conjg(cplx<T> a) { return mk<T>(a.r, -a.i); }
 template <class T> __device__ __forceinline__ cplx<T> scale(cplx<T> a, T s) { return mk<T>(a.r * s, a.i * s); }
 
+// 8-byte asynchronous global -> shared copy; src_bytes = 0 writes zeros.
+__device__ __forceinline__ void cp_async8(void* dst, const void* src, int src_bytes) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
+}
+
+// The power of two 2^(target - floor(log2 mx)) (clamped to normal floats), which
+// brings a largest magnitude mx into [2^target, 2^(target+1)); 1 when mx is zero
+// or not finite.
+__device__ __forceinline__ float pow2_scale(float mx, int target) {
+    if (!(mx > 0.f) || !(mx <= 3.4e38f)) return 1.f;
+    const int k = max(-126, min(127, target - ilogbf(mx)));
+    return __int_as_float((k + 127) << 23);
+}
+
 // Forward (sign -1) or inverse (sign +1, unnormalised) DFT of length n = 2^logn,
 // in place in shared memory, by all threads of the block.  `tw` holds
 // e^{-2 pi i k / twlen} for k < twlen/2 (twlen a power of two >= n).

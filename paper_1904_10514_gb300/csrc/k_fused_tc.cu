@@ -28,6 +28,8 @@
 // Every wait is bounded: on timeout the CTA records HPX_ERR_TIMEOUT in the
 // plan's status word, waits (bounded) for its last committed MMAs and returns
 // after releasing its tensor memory.
+#include <cuda_fp16.h>
+
 #include <cstdint>
 
 #include "plan.h"
@@ -37,6 +39,17 @@
 // 0: both operands through shared memory (fused_tc_kernel)
 #ifndef HPX_TC_TMEM_A
 #define HPX_TC_TMEM_A 1
+#endif
+// 1: FP16 form (fused_tc_ws_kernel, default): M and b split into pairs of
+// scaled FP16 numbers, 3 kind::f16 MMAs per K-step; 0: the 3xTF32 forms below
+#ifndef HPX_TC_F16
+#define HPX_TC_F16 1
+#endif
+// With the operator in tensor memory: 1 = its chunks arrive in shared memory by
+// bulk asynchronous copies, NSA chunks ahead (default); 0 = loaded into
+// registers two chunks ahead
+#ifndef HPX_TC_A_BULK
+#define HPX_TC_A_BULK 1
 #endif
 
 namespace hpx {
@@ -52,6 +65,7 @@ constexpr int STAGE = 2 * TILE_A + 2 * TILE_B;   // hi / lo copies of both opera
 constexpr int NT = 256;          // threads per CTA
 constexpr int AU = TM * KC / 4 / NT;   // 16-byte units of an A chunk per thread
 constexpr uint32_t kSpinLimit = 1u << 26;
+constexpr int NSA = 4;           // operator chunks in flight in the bulk-copy form
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -109,6 +123,25 @@ __device__ __forceinline__ void mma_commit(uint32_t mbar) {
 
 __device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(count) : "memory");
+}
+
+// One-dimensional bulk copy global -> shared memory of `bytes` (a multiple of
+// 16, both addresses 16-byte aligned) that completes as transaction bytes on
+// the mbarrier; the source lines are marked evict-first in L2 (the operators
+// are streamed once per call, the right-hand sides are reused).
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar) {
+    asm volatile(
+        "{\n\t.reg .b64 pol;\n\t"
+        "createpolicy.fractional.L2::evict_first.b64 pol, 1.0;\n\t"
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], pol;\n\t}\n"
+        :
+        : "r"(dst), "l"(src), "r"(bytes), "r"(mbar)
+        : "memory");
+}
+
+// Arrive on the mbarrier (count 1) announcing `bytes` of transactions.
+__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
 }
 
 // Bounded wait for the given phase parity; returns false on timeout.
@@ -354,12 +387,22 @@ __global__ void __launch_bounds__(NT, 2) fused_tc_kernel(const float* __restrict
 // tcgen05.st; the MMAs read A from TMEM and only b passes through shared memory.
 // TMEM per CTA (256 columns): accumulators of stage s at 64 s, A hi / lo of
 // stage s at 128 + 64 s and 128 + 64 s + 32.
+// BULK: the chunks of the operator tile (each one contiguous block of rp x 128
+// bytes) are copied by one thread into a ring of NSA shared-memory stages with
+// cp.async.bulk, NSA chunks ahead of their use, and every thread reads its 16
+// values from there (8 lanes cover 128 contiguous bytes: no bank conflicts);
+// otherwise they are loaded from global memory into registers two chunks ahead.
+// Shared memory: [NSA operator stages (BULK)] [two stages of (Bhi, Blo)].
+template <bool BULK>
 __global__ void __launch_bounds__(NT, 2) fused_tc_tmem_kernel(
     const float* __restrict__ Mt, const int64_t* __restrict__ tcOff, const int* __restrict__ tiles,
     const cplx<float>* __restrict__ bvec, cplx<float>* __restrict__ alm, int P2, int p, int L, int B, int64_t nalm,
     int* __restrict__ status) {
-    extern __shared__ __align__(1024) unsigned char smem[];   // two stages of (Bhi, Blo)
+    extern __shared__ __align__(1024) unsigned char smem_all[];
+    unsigned char* const sA = smem_all;                                // BULK: NSA x TILE_A
+    unsigned char* const smem = smem_all + (BULK ? NSA * TILE_A : 0);  // two stages of (Bhi, Blo)
     __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ __align__(8) uint64_t fullA[NSA];
     __shared__ uint32_t tmem_base;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -377,10 +420,23 @@ __global__ void __launch_bounds__(NT, 2) fused_tc_tmem_kernel(
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
+    const int nchunks = (P2 + KC - 1) / KC;
+    const uint32_t chunkBytes = (uint32_t)rp * 128u;
+    int issuedA = 0, doneA = 0;   // bulk copies issued / seen complete (thread 0)
+    auto issueA = [&](int ch) {   // thread 0: chunk ch into stage ch % NSA
+        const uint32_t fb = smem_u32(&fullA[ch % NSA]);
+        mbar_expect_tx(fb, chunkBytes);
+        bulk_g2s(smem_u32(sA + (ch % NSA) * TILE_A), At + (int64_t)ch * rp * 32, chunkBytes, fb);
+        issuedA = ch + 1;
+    };
     if (tid == 0) {
         mbar_init(smem_u32(&mbar[0]), 1);
         mbar_init(smem_u32(&mbar[1]), 1);
+        if (BULK)
+            for (int q = 0; q < NSA; ++q) mbar_init(smem_u32(&fullA[q]), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        if (BULK)
+            for (int q = 0; q < NSA && q < nchunks; ++q) issueA(q);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -396,7 +452,7 @@ __global__ void __launch_bounds__(NT, 2) fused_tc_tmem_kernel(
     float4 raA[4], raB[4];
     float2 rbA[4], rbB[4];
     auto load_chunk = [&](int ch, float4 (&ra)[4], float2 (&rb)[4]) {
-        if (row < rp) {
+        if (!BULK && row < rp) {
             const float* src = At + (int64_t)ch * rp * 32 + (row >> 3) * 256 + (row & 7) * 4;
 #pragma unroll
             for (int q = 0; q < 4; ++q) ra[q] = __ldg(reinterpret_cast<const float4*>(src + (4 * khalf + q) * 32));
@@ -407,7 +463,15 @@ __global__ void __launch_bounds__(NT, 2) fused_tc_tmem_kernel(
             rb[e] = (bmap < B && k + e < P2) ? __ldg(reinterpret_cast<const float2*>(bsrc + k + e))
                                              : make_float2(0.f, 0.f);
     };
-    auto store_chunk = [&](int st, const float4 (&ra)[4], const float2 (&rb)[4]) {
+    auto store_chunk = [&](int ch, float4 (&ra)[4], const float2 (&rb)[4]) {
+        const int st = ch & 1;
+        if (BULK) {   // this row's 16 values of the chunk from its shared-memory stage
+            const unsigned char* a = sA + (ch % NSA) * TILE_A + (row >> 3) * 1024 + (row & 7) * 16;
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                ra[q] = row < rp ? *reinterpret_cast<const float4*>(a + (4 * khalf + q) * 128)
+                                 : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
         uint32_t hi[16], lo[16];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -448,14 +512,17 @@ __global__ void __launch_bounds__(NT, 2) fused_tc_tmem_kernel(
         }
     };
 
-    const int nchunks = (P2 + KC - 1) / KC;
     bool ok = true;
     int issued = 0;
     auto step = [&](int ch, float4 (&ra)[4], float2 (&rb)[4]) {
         const int st = ch & 1;
+        if (BULK) {   // the chunk's bulk copy has landed
+            if (!mbar_wait(smem_u32(&fullA[ch % NSA]), (uint32_t)((ch / NSA) & 1))) ok = false;
+            else if (tid == 0) doneA = ch + 1;
+        }
         // stage st (A in TMEM, b in shared memory) was read by the MMAs of chunk
         // ch - 2, which completed before their accumulator was drained
-        store_chunk(st, ra, rb);
+        store_chunk(ch, ra, rb);
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -480,6 +547,8 @@ __global__ void __launch_bounds__(NT, 2) fused_tc_tmem_kernel(
                 mma_tf32_ta(d, aH + 8 * ks, make_desc(bH + o, 128, 1024), 1u);
             }
             mma_commit(smem_u32(&mbar[st]));
+            // every thread has read operator stage ch % NSA (before the barrier)
+            if (BULK && ch + NSA < nchunks) issueA(ch + NSA);
         }
         issued = ch + 1;
         if (ch + 2 < nchunks) load_chunk(ch + 2, ra, rb);
@@ -507,6 +576,8 @@ __global__ void __launch_bounds__(NT, 2) fused_tc_tmem_kernel(
         if (tid == 0) {
             atomicExch(status, HPX_ERR_TIMEOUT);
             if (issued > 0) mbar_wait(smem_u32(&mbar[(issued - 1) & 1]), (uint32_t)(((issued - 1) >> 1) & 1));
+            // bulk copies still in flight into this CTA's shared memory
+            for (int q = doneA; q < issuedA; ++q) mbar_wait(smem_u32(&fullA[q % NSA]), (uint32_t)((q / NSA) & 1));
         }
     } else {
         const int i = i0 + 32 * (warp & 3) + lane;
@@ -524,6 +595,375 @@ __global__ void __launch_bounds__(NT, 2) fused_tc_tmem_kernel(
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(dtmem), "r"(256) : "memory");
 }
 
+// ---------------------------------------------------------------- FP16 form
+//
+// The same contraction with every FP32 number x represented as a pair of FP16
+// numbers after a power-of-two scaling: x' = s x, hi = fp16(x'), lo = fp16(x' - hi)
+// (x' - hi is exact in FP32, and |x' - hi - lo| <= 2^-22 |x'| while lo is an FP16
+// normal number).  Each row of M is scaled so that its largest entry lies in
+// [2^14, 2^15) (plan time, tc_to_f16_kernel); each column of b (one map, one
+// order: both parities, real and imaginary parts) so that its largest entry lies
+// in [2^13, 2^14) (the grid-FFT kernels record its largest magnitude, bscale).  The products of
+// FP16 numbers are exact in the FP32 accumulator, and
+//     A_hi B_lo + A_lo B_hi + A_hi B_hi
+// carries the same 2^-22 relative error per product as 3xTF32, in 3 kind::f16
+// MMAs (K = 16) at twice the TF32 rate.  Entries below 2^-18 of their row (or
+// column) maximum lose relative precision, with an absolute error below 2^-39
+// of that maximum.  The scales are undone in the epilogue.
+//
+// The kernel is warp-specialised; its roles meet only at mbarriers, so each
+// stream runs ahead by its own ring of stages:
+//   * warp 4 copies: one lane the operator chunks (hi block, then lo block,
+//     rp x 64 bytes each, K-major core matrices of 8 rows x 8 halves: 8-row
+//     groups 512 bytes apart, core matrices adjacent in K 128 bytes apart) by
+//     bulk copy into NSH shared-memory stages (fullA / emptyA), and all lanes
+//     the chunk's FP32 b values (32 maps x 32 k, 8-byte cp.async, rows padded
+//     to 272 bytes) into NBR raw stages (brawFull / brawEmpty);
+//   * warp 5 (one lane) issues, per chunk, 2 K-steps x 3 kind::f16 MMAs
+//     (M = 128, N = 64, K = 16) into a fresh accumulator of NACC TMEM stages
+//     (64 columns each) and commits them to emptyA, emptyB and accFull;
+//   * warps 0-3 (128 workers) split the raw b of a chunk into the FP16 pair of
+//     B stages (NB stages; fullB / emptyB), and drain the
+//     accumulator of chunk c - LAG into FP32 registers (thread = TMEM lane =
+//     row; 32 real and 32 imaginary columns), then release it (accEmpty).
+// The operator tile needs no conversion in the kernel.  Every wait is bounded
+// and watches an abort flag: a role that gives up sets it, the others stop at
+// their next wait, and one thread then waits (bounded) for the bulk copies and
+// MMAs still in flight before the CTA releases its tensor memory.
+
+constexpr int TILE_H = TN * KC * 2;   // bytes of one FP16 copy of a b chunk (4 KB)
+constexpr int NSH = 4;                // operator stages of the FP16 form
+constexpr int NB = 2;                 // b stages (hi, lo)
+constexpr int NBR = 3;                // raw FP32 b stages
+constexpr int BRS = 272;              // bytes per map in a raw b stage (32 complex + padding)
+constexpr int TILE_R = 32 * BRS;      // one raw b stage
+constexpr int NACC = 4;               // accumulator stages (TMEM, 64 columns each)
+constexpr int LAG = 2;                // workers drain chunk c - LAG after preparing chunk c
+constexpr int NW = 128;               // worker threads (warps 0-3)
+constexpr int NTW = NW + 64;          // + the copy warp and the MMA warp
+static_assert(LAG < NACC, "the MMA of chunk c must not wait for the drain of chunk c - NACC");
+
+// Instruction descriptor: kind::f16, D = F32, A = B = F16, both K-major,
+// M = 128, N = 64.
+constexpr uint32_t kIdescH = (1u << 4) | ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+
+__device__ __forceinline__ void mma_f16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
+        :
+        : "r"(dtmem), "l"(adesc), "l"(bdesc), "r"(kIdescH), "r"(acc));
+}
+
+// The FP16 pair of x (already scaled), packed two values per 32-bit word
+// (the first one in the low half, i.e. at the lower address).
+struct HalfPair {
+    __half hi, lo;
+};
+__device__ __forceinline__ HalfPair split_h(float x) {
+    const __half h = __float2half_rn(x);
+    return HalfPair{h, __float2half_rn(x - __half2float(h))};
+}
+__device__ __forceinline__ uint32_t pack_h(__half a, __half b) {
+    return (uint32_t)__half_as_ushort(a) | ((uint32_t)__half_as_ushort(b) << 16);
+}
+
+
+// Bounded wait that also gives up when another role has set *abort.
+__device__ __forceinline__ bool ws_wait(uint32_t mbar, uint32_t parity, volatile int* abort) {
+    for (uint32_t it = 0; it < kSpinLimit; ++it) {
+        uint32_t done = 0;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.b32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(done)
+            : "r"(mbar), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if ((it & 63) == 63 && *abort) return false;
+    }
+    *abort = 1;
+    return false;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
+}
+
+__global__ void __launch_bounds__(NTW, 2) fused_tc_ws_kernel(
+    const unsigned char* __restrict__ Mh, const int64_t* __restrict__ tcOff, const float* __restrict__ tcRinv,
+    const int* __restrict__ tiles, const cplx<float>* __restrict__ bvec, const float* __restrict__ bscale,
+    cplx<float>* __restrict__ alm, int P2, int p, int L, int B, int64_t nalm, int* __restrict__ status) {
+    extern __shared__ __align__(1024) unsigned char smem_w[];
+    unsigned char* const sA = smem_w;                  // NSH x TILE_A: operator chunks (hi, lo)
+    unsigned char* const sB = smem_w + NSH * TILE_A;   // NB x (Bhi, Blo), TILE_H each
+    unsigned char* const sR = sB + NB * 2 * TILE_H;     // NBR x TILE_R: raw b
+    __shared__ __align__(8) uint64_t fullA[NSH], emptyA[NSH], fullB[NB], emptyB[NB], accFull[NACC],
+        accEmpty[NACC], brawFull[NBR], brawEmpty[NBR];
+    __shared__ uint32_t tmem_base;
+    __shared__ int abort_, issuedA, seenA, committed;
+    __shared__ float tinv[TN / 2];   // 1 / column scale of each map of the tile
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m = tiles[3 * blockIdx.x], c = tiles[3 * blockIdx.x + 1], i0 = tiles[3 * blockIdx.x + 2];
+    const int par = ((m & 1) + c) & 1;
+    const int nrows = chain_len(m, c, L);
+    const int rp = (min(TM, nrows - i0) + 7) & ~7;
+    const int b0 = blockIdx.y * (TN / 2);
+    const int nchunks = (P2 + KC - 1) / KC;
+    const uint32_t chunkBytes = (uint32_t)rp * 128u;
+    volatile int* abort = &abort_;
+
+    if (warp == 0) {   // NACC x 64 accumulator columns
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                     "r"(NACC * TN)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        for (int q = 0; q < NSH; ++q) {
+            mbar_init(smem_u32(&fullA[q]), 1);
+            mbar_init(smem_u32(&emptyA[q]), 1);
+        }
+        for (int q = 0; q < NB; ++q) {
+            mbar_init(smem_u32(&fullB[q]), NW);
+            mbar_init(smem_u32(&emptyB[q]), 1);
+        }
+        for (int q = 0; q < NACC; ++q) {
+            mbar_init(smem_u32(&accFull[q]), 1);
+            mbar_init(smem_u32(&accEmpty[q]), NW);
+        }
+        for (int q = 0; q < NBR; ++q) {
+            mbar_init(smem_u32(&brawFull[q]), 32);   // one asynchronous arrival per copying lane
+            mbar_init(smem_u32(&brawEmpty[q]), NW);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        abort_ = 0;
+        issuedA = 0;
+        seenA = 0;
+        committed = 0;
+    }
+    if (tid < TN / 2) {
+        const int bm = b0 + tid;
+        tinv[tid] = bm < B ? 1.f / pow2_scale(bscale[(int64_t)bm * (L + 1) + m], 13) : 0.f;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t dtmem = tmem_base;
+
+    if (warp == 4) {
+        // ---------------------------------------------------------- copies
+        const unsigned char* At = Mh + tcOff[blockIdx.x] * 4;
+        for (int ch = 0; ch < nchunks; ++ch) {
+            const int s = ch % NSH, r = ch % NBR;
+            if (ch >= NSH && !ws_wait(smem_u32(&emptyA[s]), (uint32_t)((ch / NSH + 1) & 1), abort)) break;
+            if (lane == 0) {
+                const uint32_t fb = smem_u32(&fullA[s]);
+                mbar_expect_tx(fb, chunkBytes);
+                bulk_g2s(smem_u32(sA + s * TILE_A), At + (int64_t)ch * chunkBytes, chunkBytes, fb);
+                issuedA = ch + 1;
+            }
+            if (ch >= NBR && !ws_wait(smem_u32(&brawEmpty[r]), (uint32_t)((ch / NBR + 1) & 1), abort)) break;
+            // lane = k within the chunk; zero fill past P2 and past the last map
+            const int k = ch * KC + lane;
+            unsigned char* dst = sR + r * TILE_R + lane * 8;
+#pragma unroll 8
+            for (int q = 0; q < TN / 2; ++q) {
+                const int bm = b0 + q;
+                const bool okb = bm < B && k < P2;
+                const cplx<float>* src = bvec + (((int64_t)min(bm, B - 1) * (p + 1) + m) * 2 + par) * P2 + min(k, P2 - 1);
+                cp_async8(dst + q * BRS, src, okb ? 8 : 0);
+            }
+            asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(&brawFull[r]))
+                         : "memory");
+        }
+        asm volatile("cp.async.wait_all;" ::: "memory");
+    } else if (warp == 5) {
+        // ---------------------------------------------------------- MMAs
+        if (lane == 0) {
+            for (int ch = 0; ch < nchunks; ++ch) {
+                const int s = ch % NSH, t = ch % NB, a = ch % NACC;
+                if (!ws_wait(smem_u32(&fullA[s]), (uint32_t)((ch / NSH) & 1), abort)) break;
+                seenA = ch + 1;
+                if (!ws_wait(smem_u32(&fullB[t]), (uint32_t)((ch / NB) & 1), abort)) break;
+                if (ch >= NACC && !ws_wait(smem_u32(&accEmpty[a]), (uint32_t)((ch / NACC + 1) & 1), abort)) break;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t aH = smem_u32(sA + s * TILE_A), aL = aH + (uint32_t)rp * 64;
+                const uint32_t bH = smem_u32(sB + t * (2 * TILE_H)), bL = bH + TILE_H;
+                const uint32_t d = dtmem + (uint32_t)(a * TN);
+#pragma unroll
+                for (int ks = 0; ks < KC / 16; ++ks) {
+                    const uint32_t o = ks * 256;
+                    mma_f16(d, make_desc(aH + o, 128, 512), make_desc(bL + o, 128, 512), ks > 0 ? 1u : 0u);
+                    mma_f16(d, make_desc(aL + o, 128, 512), make_desc(bH + o, 128, 512), 1u);
+                }
+#pragma unroll
+                for (int ks = 0; ks < KC / 16; ++ks) {
+                    const uint32_t o = ks * 256;
+                    mma_f16(d, make_desc(aH + o, 128, 512), make_desc(bH + o, 128, 512), 1u);
+                }
+                mma_commit(smem_u32(&emptyA[s]));
+                mma_commit(smem_u32(&emptyB[t]));
+                mma_commit(smem_u32(&accFull[a]));
+                committed = ch + 1;
+            }
+        }
+    } else {
+        // ---------------------------------------------------------- workers
+        // b: thread -> map (tid & 31) and the 8 consecutive k = 8 (tid >> 5) ..;
+        // real parts to B row (tid & 31), imaginary parts to row 32 + (tid & 31):
+        // one 16-byte core-matrix row each
+        const int bm = tid & 31, kg = tid >> 5;
+        const int bmap = b0 + bm;
+        const float tb = bmap < B ? pow2_scale(bscale[(int64_t)bmap * (L + 1) + m], 13) : 1.f;
+        const uint32_t offr = (uint32_t)((bm >> 3) * 512 + kg * 128 + (bm & 7) * 16);
+        const uint32_t offi = offr + 4 * 512;
+        float acc[64];
+#pragma unroll
+        for (int q = 0; q < 64; ++q) acc[q] = 0.f;
+        const uint32_t trow = dtmem + ((uint32_t)(32 * warp) << 16);
+        bool ok = true;
+        auto drain = [&](int dch) {
+            const int a = dch % NACC;
+            if (!ws_wait(smem_u32(&accFull[a]), (uint32_t)((dch / NACC) & 1), abort)) return false;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                uint32_t v[16];
+                tmem_ld16(trow + (uint32_t)(a * TN + 16 * h), v);
+#pragma unroll
+                for (int q = 0; q < 16; ++q) acc[16 * h + q] += __uint_as_float(v[q]);
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            mbar_arrive(smem_u32(&accEmpty[a]));
+            return true;
+        };
+        auto work = [&](int ch) {
+            const int t = ch % NB, r = ch % NBR;
+            // this thread's 8 complex b values of the chunk from the raw stage
+            if (!ws_wait(smem_u32(&brawFull[r]), (uint32_t)((ch / NBR) & 1), abort)) return false;
+            float2 rb[8];
+            const float4* raw = reinterpret_cast<const float4*>(sR + r * TILE_R + bm * BRS + kg * 64);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const float4 v = raw[e];
+                rb[2 * e] = make_float2(v.x, v.y);
+                rb[2 * e + 1] = make_float2(v.z, v.w);
+            }
+            mbar_arrive(smem_u32(&brawEmpty[r]));
+            if (ch >= NB && !ws_wait(smem_u32(&emptyB[t]), (uint32_t)((ch / NB + 1) & 1), abort)) return false;
+            unsigned char* Bhi = sB + t * (2 * TILE_H);
+            uint32_t rh[4], rl[4], qh[4], ql[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const HalfPair x0 = split_h(tb * rb[2 * e].x), x1 = split_h(tb * rb[2 * e + 1].x);
+                const HalfPair y0 = split_h(tb * rb[2 * e].y), y1 = split_h(tb * rb[2 * e + 1].y);
+                rh[e] = pack_h(x0.hi, x1.hi);
+                rl[e] = pack_h(x0.lo, x1.lo);
+                qh[e] = pack_h(y0.hi, y1.hi);
+                ql[e] = pack_h(y0.lo, y1.lo);
+            }
+            *reinterpret_cast<uint4*>(Bhi + offr) = make_uint4(rh[0], rh[1], rh[2], rh[3]);
+            *reinterpret_cast<uint4*>(Bhi + TILE_H + offr) = make_uint4(rl[0], rl[1], rl[2], rl[3]);
+            *reinterpret_cast<uint4*>(Bhi + offi) = make_uint4(qh[0], qh[1], qh[2], qh[3]);
+            *reinterpret_cast<uint4*>(Bhi + TILE_H + offi) = make_uint4(ql[0], ql[1], ql[2], ql[3]);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_arrive(smem_u32(&fullB[t]));
+            return ch < LAG || drain(ch - LAG);
+        };
+        for (int ch = 0; ch < nchunks && ok; ++ch) ok = work(ch);
+        for (int dch = max(0, nchunks - LAG); ok && dch < nchunks; ++dch) ok = drain(dch);
+        if (ok) {
+            const int row = 32 * warp + lane;
+            const int i = i0 + row;
+            if (i < nrows) {
+                const float ri = tcRinv[tcOff[blockIdx.x] / (32 * nchunks) + row];
+                const int64_t base = (int64_t)m * (2 * L + 1 - m) / 2 + m + c + 2 * (int64_t)i;
+#pragma unroll
+                for (int q = 0; q < 32; ++q)
+                    if (b0 + q < B) {
+                        const float sc = ri * tinv[q];
+                        alm[(int64_t)(b0 + q) * nalm + base] = mk<float>(acc[q] * sc, acc[32 + q] * sc);
+                    }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (abort_) {
+        if (tid == 0) {
+            atomicExch(status, HPX_ERR_TIMEOUT);
+            // operator copies issued but not seen by the MMA warp, and the last MMAs
+            for (int q = seenA; q < issuedA; ++q)
+                mbar_wait(smem_u32(&fullA[q % NSH]), (uint32_t)((q / NSH) & 1));
+            if (committed > 0)
+                mbar_wait(smem_u32(&accFull[(committed - 1) % NACC]), (uint32_t)(((committed - 1) / NACC) & 1));
+        }
+        __syncthreads();
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(dtmem), "r"(NACC * TN) : "memory");
+}
+
+// Plan time, FP32 tiles -> FP16 form in place (one block of 128 threads per
+// tile, thread r = row r): the row's largest magnitude gives its scale s_r,
+// 1 / s_r goes to rinv, and every chunk (all of it read before any of it is
+// rewritten) becomes the hi block followed by the lo block of s_r M.
+__global__ void __launch_bounds__(TM) tc_to_f16_kernel(float* __restrict__ Mt, const int64_t* __restrict__ tcOff,
+                                                       const int* __restrict__ tiles, int P2, int L,
+                                                       float* __restrict__ rinv) {
+    const int m = tiles[3 * blockIdx.x], c = tiles[3 * blockIdx.x + 1], i0 = tiles[3 * blockIdx.x + 2];
+    const int rp = (min(TM, chain_len(m, c, L) - i0) + 7) & ~7;
+    const int nchunks = (P2 + KC - 1) / KC;
+    float* At = Mt + tcOff[blockIdx.x];
+    const int r = threadIdx.x;
+    const bool mine = r < rp;
+    float mx = 0.f;
+    if (mine)
+        for (int ch = 0; ch < nchunks; ++ch) {
+            const float* src = At + (int64_t)ch * rp * 32 + (r >> 3) * 256 + (r & 7) * 4;
+            for (int kk = 0; kk < 8; ++kk) {
+                const float4 v = *reinterpret_cast<const float4*>(src + kk * 32);
+                mx = fmaxf(mx, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+            }
+        }
+    const float sr = pow2_scale(mx, 14);
+    if (mine) rinv[tcOff[blockIdx.x] / (32 * nchunks) + r] = 1.f / sr;
+    for (int ch = 0; ch < nchunks; ++ch) {
+        float* base = At + (int64_t)ch * rp * 32;
+        float v[32];
+        if (mine) {
+            const float* src = base + (r >> 3) * 256 + (r & 7) * 4;
+#pragma unroll
+            for (int kk = 0; kk < 8; ++kk) {
+                const float4 q = *reinterpret_cast<const float4*>(src + kk * 32);
+                v[4 * kk] = q.x; v[4 * kk + 1] = q.y; v[4 * kk + 2] = q.z; v[4 * kk + 3] = q.w;
+            }
+        }
+        __syncthreads();
+        if (mine) {
+            unsigned char* hb = reinterpret_cast<unsigned char*>(base) + (r >> 3) * 512 + (r & 7) * 16;
+#pragma unroll
+            for (int kc = 0; kc < 4; ++kc) {
+                uint32_t h[4], l[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const HalfPair a = split_h(sr * v[8 * kc + 2 * e]), b = split_h(sr * v[8 * kc + 2 * e + 1]);
+                    h[e] = pack_h(a.hi, b.hi);
+                    l[e] = pack_h(a.lo, b.lo);
+                }
+                *reinterpret_cast<uint4*>(hb + kc * 128) = make_uint4(h[0], h[1], h[2], h[3]);
+                *reinterpret_cast<uint4*>(hb + rp * 64 + kc * 128) = make_uint4(l[0], l[1], l[2], l[3]);
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // Failure-path self-test: a wait on an mbarrier that nothing completes gives up
 // after `spins` polls and reports like the operator kernel does.
 __global__ void timeout_selftest_kernel(int* __restrict__ status, uint32_t spins) {
@@ -538,15 +978,41 @@ void launch_timeout_selftest(const hpx_plan_s* P, int spins, cudaStream_t s) {
     timeout_selftest_kernel<<<1, 32, 0, s>>>(P->d_status, (uint32_t)spins);
 }
 
+int prepare_fused_tc(hpx_plan_s* P) {
+#if HPX_TC_F16
+    const auto& g = P->g;
+    const int64_t nch = (g.P2 + KC - 1) / KC;
+    const int64_t rows = P->fused_bytes / 4 / (32 * nch);   // stored rows of all tiles
+    const size_t rb = (size_t)rows * sizeof(float), bb = (size_t)g.B * (g.L + 1) * sizeof(float);
+    if (cudaMalloc(&P->tcRinv, rb) != cudaSuccess || cudaMalloc(&P->bscale, bb) != cudaSuccess) return -1;
+    P->bytes += (int64_t)(rb + bb);
+    P->fused_bytes += (int64_t)(rb + bb);
+    tc_to_f16_kernel<<<P->fused_ntiles, TM>>>((float*)P->fusedM, P->tcOff, P->fusedTiles, g.P2, g.L, P->tcRinv);
+    return cudaDeviceSynchronize() == cudaSuccess ? 0 : -1;
+#else
+    (void)P;
+    return 0;
+#endif
+}
+
 void launch_fused_tc(const hpx_plan_s* P, float* alm, cudaStream_t s) {
     const auto& g = P->g;
     dim3 grid(P->fused_ntiles, (g.B + 31) / 32);
+#if HPX_TC_F16
+    const size_t smem_h = NSH * TILE_A + NB * 2 * TILE_H + NBR * TILE_R;
+    cudaFuncSetAttribute(fused_tc_ws_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_h);
+    fused_tc_ws_kernel<<<grid, NTW, smem_h, s>>>((const unsigned char*)P->fusedM, P->tcOff, P->tcRinv, P->fusedTiles,
+                                                 (const cplx<float>*)P->bvec, P->bscale, (cplx<float>*)alm, g.P2,
+                                                 g.p, g.L, g.B, g.nalm, P->d_status);
+    return;
+#endif
 #if HPX_TC_TMEM_A
-    const size_t smem_t = 4 * TILE_B;
-    cudaFuncSetAttribute(fused_tc_tmem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_t);
-    fused_tc_tmem_kernel<<<grid, NT, smem_t, s>>>((const float*)P->fusedM, P->tcOff, P->fusedTiles,
-                                                  (const cplx<float>*)P->bvec, (cplx<float>*)alm, g.P2, g.p, g.L,
-                                                  g.B, g.nalm, P->d_status);
+    constexpr bool bulk = HPX_TC_A_BULK != 0;
+    const size_t smem_t = 4 * TILE_B + (bulk ? NSA * TILE_A : 0);
+    cudaFuncSetAttribute(fused_tc_tmem_kernel<bulk>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_t);
+    fused_tc_tmem_kernel<bulk><<<grid, NT, smem_t, s>>>((const float*)P->fusedM, P->tcOff, P->fusedTiles,
+                                                        (const cplx<float>*)P->bvec, (cplx<float>*)alm, g.P2, g.p,
+                                                        g.L, g.B, g.nalm, P->d_status);
     return;
 #endif
     const size_t smem = 2 * STAGE;

@@ -121,11 +121,6 @@ __global__ void __launch_bounds__(256) spread_kernel(const cplx<T>* __restrict__
     }
 }
 
-// 8-byte asynchronous global -> shared copy; src_bytes = 0 writes zeros.
-__device__ __forceinline__ void cp_async8(void* dst, const void* src, int src_bytes) {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
-}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
@@ -136,10 +131,10 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // t0 + 4w .. t0 + 4w + 3 and lane l order m0 + l; the thread keeps its 4 x EW
 // weights (for the parity of its order) in registers, aligned to a common
 // window of EW + DM latitude nodes, so every node value read from shared
-// memory feeds four grid points.  The node values of the next 32 orders are
-// copied into the other half of a double buffer (cp.async) while the current
+// memory feeds four grid points.  The node values of the orders 32 .. 32 (NS-1)
+// ahead are in flight (cp.async into a ring of NS buffers) while the current
 // ones are used.
-template <int EW, int DM>
+template <int EW, int DM, int NS>
 __global__ void __launch_bounds__(256, 2) spread_rb_kernel(const cplx<float>* __restrict__ Y,
                                                            cplx<float>* __restrict__ U,
                                                            const int* __restrict__ hstart,
@@ -148,7 +143,7 @@ __global__ void __launch_bounds__(256, 2) spread_rb_kernel(const cplx<float>* __
     constexpr int W = EW + DM;
     extern __shared__ unsigned char smem_raw[];
     cplx<float>* out = reinterpret_cast<cplx<float>*>(smem_raw);   // [32 orders][33]
-    cplx<float>* ys0 = out + 32 * 33;                              // 2 x [nrw rows][32 orders]
+    cplx<float>* ys0 = out + 32 * 33;                              // NS x [nrw rows][32 orders]
     const int t0 = blockIdx.x * 32, b = blockIdx.y;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int R0 = hstart[t0];
@@ -176,16 +171,21 @@ __global__ void __launch_bounds__(256, 2) spread_rb_kernel(const cplx<float>* __
         cp_async_commit();
     };
     const int ntiles = (L + 32) / 32;
-    fetch(0, ys0);
+    // one commit group per tile (empty past the last), so that waiting until at
+    // most NS - 1 groups are pending means tile it has landed
+#pragma unroll
+    for (int q = 0; q < NS - 1; ++q) {
+        if (q < ntiles) fetch(32 * q, ys0 + q * nrw * 32);
+        else cp_async_commit();
+    }
     for (int it = 0; it < ntiles; ++it) {
         const int m0 = 32 * it;
-        cplx<float>* ys = ys0 + (it & 1) * nrw * 32;
-        if (it + 1 < ntiles) {
-            fetch(m0 + 32, ys0 + ((it + 1) & 1) * nrw * 32);
-            cp_async_wait<1>();
-        } else {
-            cp_async_wait<0>();
-        }
+        cplx<float>* ys = ys0 + (it % NS) * nrw * 32;
+        // buffer (it + NS - 1) % NS was last read in iteration it - 1, which
+        // ended with a barrier
+        if (it + NS - 1 < ntiles) fetch(m0 + 32 * (NS - 1), ys0 + ((it + NS - 1) % NS) * nrw * 32);
+        else cp_async_commit();
+        cp_async_wait<NS - 1>();
         __syncthreads();
         float ar[4] = {0.f, 0.f, 0.f, 0.f}, ai[4] = {0.f, 0.f, 0.f, 0.f};
         const cplx<float>* yr = ys + base * 32 + lane;
@@ -216,7 +216,8 @@ __global__ void __launch_bounds__(256, 2) spread_rb_kernel(const cplx<float>* __
 template <class T, int E>
 __global__ void __launch_bounds__(512, (E <= 16 ? 2 : 1)) lat_fft_kernel(
     const cplx<T>* __restrict__ U, cplx<T>* __restrict__ bvec, const T* __restrict__ dec,
-    const cplx<T>* __restrict__ tw, int twlen, int M, int logM, int p, int L, int P2, int ldu) {
+    const cplx<T>* __restrict__ tw, int twlen, int M, int logM, int p, int L, int P2, int ldu,
+    float* __restrict__ bscale) {
     extern __shared__ unsigned char smem_raw[];
     cplx<T>* u = reinterpret_cast<cplx<T>*>(smem_raw);   // M (padded)
     const int m = blockIdx.x;
@@ -233,11 +234,13 @@ __global__ void __launch_bounds__(512, (E <= 16 ? 2 : 1)) lat_fft_kernel(
         return odd ? mk<T>(-v.r, -v.i) : v;
     };
     // mode j <= p: deconvolve and store as a right-hand side
+    float mx = 0.f;   // largest magnitude stored (for bscale)
     auto st = [&](int j, cplx<T> v) {
         if (j > p) return;
         v = scale(v, dec[j]);
         if (odd) v = mk<T>(T(-0.5) * v.i, T(0.5) * v.r);
         out[(j & 1) * P2 + (j >> 1)] = v;
+        mx = fmaxf(mx, fmaxf(fabsf((float)v.r), fabsf((float)v.i)));
     };
     if (logM >= 5) {
         block_fft_io<T, E>(u, logM, tw, twlen, ld, st);
@@ -248,6 +251,10 @@ __global__ void __launch_bounds__(512, (E <= 16 ? 2 : 1)) lat_fft_kernel(
         for (int j = tid; j < M; j += nt) st(j, u[pad(j)]);
     }
     if (tid == 0) out[P2 + (P2 - 1)] = mk<T>(T(0), T(0));
+    if (bscale) {   // the column's largest magnitude, for the FP16 operator kernel
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if ((tid & 31) == 0) atomicMax(reinterpret_cast<int*>(bscale) + (int64_t)b * (L + 1) + m, __float_as_int(mx));
+    }
 }
 
 template <class T>
@@ -255,16 +262,16 @@ void launch_spread(const hpx_plan_s* P, cudaStream_t s) {
     const auto& g = P->g;
     const auto& t = P->t;
     const int H = g.M / 2;
-    constexpr int EW = 12, DM = 4;
+    constexpr int EW = 12, DM = 4, NS = 4;
     if (sizeof(T) == 4 && t.spreadH <= EW && t.spreadD <= DM) {
         // rows a block needs: its first window start .. the last window end
         const int nrw = t.spreadRows - t.spreadH + EW + DM;
-        const size_t smem = (size_t)(32 * 33 + 2 * 32 * nrw) * sizeof(cplx<float>);
-        cudaFuncSetAttribute(spread_rb_kernel<EW, DM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        const size_t smem = (size_t)(32 * 33 + NS * 32 * nrw) * sizeof(cplx<float>);
+        auto kern = spread_rb_kernel<EW, DM, NS>;
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         dim3 grid((H + 32) / 32, g.B);
-        spread_rb_kernel<EW, DM><<<grid, 256, smem, s>>>((const cplx<float>*)P->Y, (cplx<float>*)P->U, t.hstart,
-                                                         (const float*)t.hwts, t.spreadH, H, g.p, g.Q, g.L,
-                                                         P->ldu, nrw);
+        kern<<<grid, 256, smem, s>>>((const cplx<float>*)P->Y, (cplx<float>*)P->U, t.hstart, (const float*)t.hwts,
+                                     t.spreadH, H, g.p, g.Q, g.L, P->ldu, nrw);
         return;
     }
     const size_t smem = (size_t)(32 * 33 + 32 * t.spreadRows) * sizeof(cplx<T>);
@@ -282,7 +289,8 @@ void launch_spread(const hpx_plan_s* P, cudaStream_t s) {
 template <class T, int E>
 __global__ void __launch_bounds__(512, (E <= 16 ? 2 : 1)) lat_fft_pair_kernel(
     const cplx<T>* __restrict__ U, cplx<T>* __restrict__ bvec, const T* __restrict__ dec,
-    const cplx<T>* __restrict__ tw, int twlen, int M, int logM, int p, int L, int P2, int ldu) {
+    const cplx<T>* __restrict__ tw, int twlen, int M, int logM, int p, int L, int P2, int ldu,
+    float* __restrict__ bscale) {
     extern __shared__ unsigned char smem_raw[];
     cplx<T>* u = reinterpret_cast<cplx<T>*>(smem_raw);   // M (padded)
     cplx<T>* zlo = u + M + M / 16;                         // Z_j, j = 0..p
@@ -312,24 +320,41 @@ __global__ void __launch_bounds__(512, (E <= 16 ? 2 : 1)) lat_fft_pair_kernel(
     __syncthreads();
     cplx<T>* out0 = bvec + ((int64_t)b * (p + 1) + m0) * 2 * P2;
     cplx<T>* out1 = out0 + 2 * P2;
+    float mx0 = 0.f, mx1 = 0.f;   // largest magnitudes stored (for bscale)
     for (int j = tid; j <= p; j += nt) {
         const cplx<T> a = zlo[j], c = (j == 0) ? zlo[0] : zhi[j];
         const T dj = dec[j];
-        out0[(j & 1) * P2 + (j >> 1)] = scale(add(a, c), T(0.5) * dj);
+        const cplx<T> v0 = scale(add(a, c), T(0.5) * dj);
+        out0[(j & 1) * P2 + (j >> 1)] = v0;
+        mx0 = fmaxf(mx0, fmaxf(fabsf((float)v0.r), fabsf((float)v0.i)));
         if (has1) {
             const cplx<T> v = scale(sub(a, c), T(0.5) * dj);   // B_{m+1}(j), times i/2 below
             out1[(j & 1) * P2 + (j >> 1)] = mk<T>(T(-0.5) * v.i, T(0.5) * v.r);
+            mx1 = fmaxf(mx1, 0.5f * fmaxf(fabsf((float)v.r), fabsf((float)v.i)));
         }
     }
     if (tid == 0) {
         out0[P2 + (P2 - 1)] = mk<T>(T(0), T(0));
         if (has1) out1[P2 + (P2 - 1)] = mk<T>(T(0), T(0));
     }
+    if (bscale) {   // the columns' largest magnitudes, for the FP16 operator kernel
+        for (int o = 16; o > 0; o >>= 1) {
+            mx0 = fmaxf(mx0, __shfl_xor_sync(0xffffffffu, mx0, o));
+            mx1 = fmaxf(mx1, __shfl_xor_sync(0xffffffffu, mx1, o));
+        }
+        if ((tid & 31) == 0) {   // non-negative floats order like their bits
+            atomicMax(reinterpret_cast<int*>(bscale) + (int64_t)b * (L + 1) + m0, __float_as_int(mx0));
+            if (has1) atomicMax(reinterpret_cast<int*>(bscale) + (int64_t)b * (L + 1) + m1, __float_as_int(mx1));
+        }
+    }
 }
 
 template <class T>
 void launch_lat_fft(const hpx_plan_s* P, cudaStream_t s) {
     const auto& g = P->g;
+    // bscale (FP16 operator form): per column the largest magnitude of b, as
+    // the atomic maximum of the float bits over the warps that write it
+    if (P->bscale) cudaMemsetAsync(P->bscale, 0, (size_t)g.B * (g.L + 1) * sizeof(float), s);
     int logM = 0;
     while ((1 << logM) < g.M) ++logM;
     const size_t smem = (size_t)(g.M + g.M / 16) * sizeof(cplx<T>);
@@ -339,14 +364,15 @@ void launch_lat_fft(const hpx_plan_s* P, cudaStream_t s) {
         cudaFuncSetAttribute(kern2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
         dim3 grid2((g.L + 2) / 2, g.B);
         kern2<<<grid2, 512, smem2, s>>>((const cplx<T>*)P->U, (cplx<T>*)P->bvec, (const T*)P->t.dec,
-                                        (const cplx<T>*)P->t.twid, g.Lmax, g.M, logM, g.p, g.L, g.P2, P->ldu);
+                                        (const cplx<T>*)P->t.twid, g.Lmax, g.M, logM, g.p, g.L, g.P2, P->ldu,
+                                        P->bscale);
         return;
     }
     auto kern = g.M > 16 * 512 ? lat_fft_kernel<T, 32> : lat_fft_kernel<T, 16>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     dim3 grid(g.L + 1, g.B);
     kern<<<grid, 512, smem, s>>>((const cplx<T>*)P->U, (cplx<T>*)P->bvec, (const T*)P->t.dec,
-                                 (const cplx<T>*)P->t.twid, g.Lmax, g.M, logM, g.p, g.L, g.P2, P->ldu);
+                                 (const cplx<T>*)P->t.twid, g.Lmax, g.M, logM, g.p, g.L, g.P2, P->ldu, P->bscale);
 }
 
 template void launch_spread<float>(const hpx_plan_s*, cudaStream_t);

@@ -86,12 +86,15 @@ struct hpx_plan_s {
     int* fusedTiles = nullptr;     // (m, c, first row) per block of the apply kernel
     int fused_ntiles = 0;
     int fused_ldm = 0;             // row stride of M (P2 rounded up to a multiple of 4)
-    bool use_tc = false;           // FP32: apply M with tcgen05 3xTF32 MMAs
+    bool use_tc = false;           // FP32: apply M with tcgen05 MMAs (k_fused_tc.cu)
     // tensor-core layout of M (use_tc): tile t (128 rows of one chain, rows
     // padded to a multiple of 8 = rp) is stored as consecutive K-chunks of
-    // rp x 32 floats in the MMA's core-matrix order, from float offset tcOff[t]
+    // rp x 128 bytes in the MMA's core-matrix order, from 4-byte offset tcOff[t]
+    // (rp x 32 floats, or after prepare_fused_tc the FP16 pairs of the scaled rows)
     int64_t* tcOff = nullptr;
     int* tcFirst = nullptr;        // first tile of (m, c)
+    float* tcRinv = nullptr;       // FP16 form: 1 / row scale, per stored row of the tiles
+    float* bscale = nullptr;       // FP16 form: [B][L+1] largest magnitude of each b column
     int* d_status = nullptr;       // device status word (timed-out waits, non-finite inputs)
     int64_t fused_bytes = 0;       // bytes of M
     void* synM = nullptr;          // T, n_alm x ldm row-major: synthesis operators R_{m,c} Es (HPX_FLAG_SYNTHESIS)
@@ -133,6 +136,9 @@ template <class T> void launch_rot(const hpx_plan_s* P, T* alm, cudaStream_t s);
 int fused_tile_rows(int B);
 template <class T> void launch_fused(const hpx_plan_s* P, T* alm, cudaStream_t s);
 void launch_fused_tc(const hpx_plan_s* P, float* alm, cudaStream_t s);
+// after build_fused<float> of the tensor-core layout: converts M to the form
+// launch_fused_tc reads (and allocates its scale arrays); 0 on success
+int prepare_fused_tc(hpx_plan_s* P);
 void launch_timeout_selftest(const hpx_plan_s* P, int spins, cudaStream_t s);
 // HPX_FLAG_CHECKED: records HPX_ERR_NONFINITE in *status if any of the n reals
 // (float or double) at x is NaN or infinite.
