@@ -71,8 +71,9 @@ extern "C" {
 #define HPX_FLAG_GRAPH 2u
 /* HPX_FLAG_SIMT: apply the per-order operators of an FP32 plan on the FP32
  *   pipes.  By default FP32 plans of 9 or more maps use the tensor cores
- *   (tcgen05, 3xTF32: each operand split into two TF32 parts, three MMAs
- *   accumulated in FP32). */
+ *   (tcgen05: each operand, scaled by a power of two, split into a pair of
+ *   FP16 numbers, three kind::f16 MMAs accumulated in FP32; the relative error
+ *   of each product is below 2^-22, as with FP32 rounding). */
 #define HPX_FLAG_SIMT 4u
 /* HPX_FLAG_CHECKED: every hpx_analyze / hpx_synthesize first checks on the host
  *   that its two pointers are device (or managed) memory of the plan's device

@@ -1,33 +1,31 @@
 // Per-order operators on the 5th-generation tensor cores (tcgen05, TMEM).
 //
 // The contraction a_{m+c+2i}^m[map] = sum_k M_{m,c}[i][k] b[map][m][par][k] of
-// k_fused.cu, for FP32 plans, as 3xTF32 MMAs: every operand x is split into
-// two TF32 numbers, x_hi = x rounded to TF32 and x_lo = (x - x_hi) rounded to
-// TF32 (|x - x_hi - x_lo| <= 2^-22 |x|), and the product is accumulated as
-//     A_hi B_hi + A_hi B_lo + A_lo B_hi
-// in FP32 in tensor memory (the dropped A_lo B_lo term is below 2^-22 of the
-// product).  One CTA (8 warps) computes a tile of 128 rows (degrees of one
-// chain) x 64 real columns (real parts of 32 maps, then their imaginary parts)
-// over K = P2 in chunks of 32, with two shared-memory stages and two TMEM
-// accumulators:
-//   * the plan stores M for this kernel tile by tile as consecutive K-chunks
-//     in the MMA's K-major, no-swizzle core-matrix order (8 rows x 16 bytes per
-//     core matrix; core matrices adjacent in K 128 bytes apart, 8-row groups
-//     1 KB apart), so a chunk is one contiguous block of rp x 128 bytes;
-//   * all threads split the chunk of M and of b, held in registers, into hi /
-//     lo copies in shared memory (bank-conflict-free 16-byte stores);
-//   * one thread issues 4 K-steps x 3 tcgen05.mma (M=128, N=64, K=8) into a
-//     fresh accumulator and commits them to the stage's mbarrier;
-//   * meanwhile the threads load the chunk after next into registers (two
-//     register sets), then wait for the previous chunk's MMAs and add its
-//     accumulator (tcgen05.ld; warp w owns TMEM lanes 32 (w mod 4) .. +31) to
-//     FP32 registers.
-// Summing chunk partials in registers keeps every tensor-core accumulation
-// step at the size of one chunk's partial sum; the registers add 1 + K/32
-// terms with round-to-nearest.
+// k_fused.cu, for FP32 plans, with FP32-level accuracy from lower-precision
+// tensor-core MMAs: every operand x is split into a pair hi + lo of numbers of
+// 11 significant bits (|x - hi - lo| <= 2^-22 |x|) and the product is
+// accumulated as
+//     A_hi B_lo + A_lo B_hi + A_hi B_hi
+// (the dropped A_lo B_lo term is below 2^-22 of the product).  One CTA
+// computes a tile of 128 rows (degrees of one chain) x 64 real columns (real
+// parts of 32 maps, then their imaginary parts) over K = P2 in chunks of 32.
+// The plan stores M tile by tile as consecutive K-chunks in the MMA's K-major,
+// no-swizzle core-matrix order, so a chunk is one contiguous block of rp x 128
+// bytes that one bulk copy brings into shared memory.  Each chunk goes into a
+// fresh TMEM accumulator whose value is added to FP32 registers: every
+// tensor-core accumulation then stays at the size of one chunk's partial sum,
+// and the registers add 1 + K/32 terms with round-to-nearest.
+//
+// Two forms (HPX_TC_F16):
+//   1 (default) fused_tc_ws_kernel: hi / lo are FP16 numbers of the operands
+//     after power-of-two scaling (M converted at plan time), kind::f16 MMAs,
+//     warp-specialised (description below);
+//   0 fused_tc_tmem_kernel: hi / lo are TF32 numbers, kind::tf32 MMAs; the
+//     threads split each chunk of M into tensor memory and of b into shared
+//     memory, with one block barrier per chunk.
 // Every wait is bounded: on timeout the CTA records HPX_ERR_TIMEOUT in the
-// plan's status word, waits (bounded) for its last committed MMAs and returns
-// after releasing its tensor memory.
+// plan's status word, waits (bounded) for its copies and MMAs still in flight
+// and returns after releasing its tensor memory.
 #include <cuda_fp16.h>
 
 #include <cstdint>
@@ -35,21 +33,8 @@
 #include "plan.h"
 #include "plan_math.h"
 
-// 1: the operator tile goes to tensor memory (fused_tc_tmem_kernel, default);
-// 0: both operands through shared memory (fused_tc_kernel)
-#ifndef HPX_TC_TMEM_A
-#define HPX_TC_TMEM_A 1
-#endif
-// 1: FP16 form (fused_tc_ws_kernel, default): M and b split into pairs of
-// scaled FP16 numbers, 3 kind::f16 MMAs per K-step; 0: the 3xTF32 forms below
 #ifndef HPX_TC_F16
 #define HPX_TC_F16 1
-#endif
-// With the operator in tensor memory: 1 = its chunks arrive in shared memory by
-// bulk asynchronous copies, NSA chunks ahead (default); 0 = loaded into
-// registers two chunks ahead
-#ifndef HPX_TC_A_BULK
-#define HPX_TC_A_BULK 1
 #endif
 
 namespace hpx {
@@ -59,13 +44,11 @@ namespace {
 constexpr int TM = 128;          // rows per tile (MMA M)
 constexpr int TN = 64;           // real columns per tile (MMA N): 32 maps x (re, im)
 constexpr int KC = 32;           // K per chunk
-constexpr int TILE_A = TM * KC * 4;   // bytes of one A copy (16 KB)
-constexpr int TILE_B = TN * KC * 4;   // bytes of one B copy (8 KB)
-constexpr int STAGE = 2 * TILE_A + 2 * TILE_B;   // hi / lo copies of both operands (48 KB)
-constexpr int NT = 256;          // threads per CTA
-constexpr int AU = TM * KC / 4 / NT;   // 16-byte units of an A chunk per thread
+constexpr int TILE_A = TM * KC * 4;   // bytes of one operator chunk (16 KB)
+constexpr int TILE_B = TN * KC * 4;   // bytes of one TF32 copy of a b chunk (8 KB)
+constexpr int NT = 256;          // threads per CTA of the TF32 form
 constexpr uint32_t kSpinLimit = 1u << 26;
-constexpr int NSA = 4;           // operator chunks in flight in the bulk-copy form
+constexpr int NSA = 4;           // operator stages of the TF32 form
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -86,16 +69,7 @@ __device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint
 constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TN >> 3) << 17) |
                             ((uint32_t)(TM >> 4) << 24);
 
-__device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t acc) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n"
-        :
-        : "r"(dtmem), "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(acc));
-}
-
-// The same MMA with A read from tensor memory (lane = row, one 32-bit column per k).
+// kind::tf32 MMA with A read from tensor memory (lane = row, one 32-bit column per k).
 __device__ __forceinline__ void mma_tf32_ta(uint32_t dtmem, uint32_t atmem, uint64_t bdesc, uint32_t acc) {
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
@@ -171,20 +145,6 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// 32 consecutive FP32 columns of this warp's 32 TMEM lanes (one per thread).
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
-          "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
-          "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-
 // x rounded to the nearest TF32 number (10 stored mantissa bits; ties away from
 // zero): add half a TF32 ulp to the magnitude bits and clear the low 13 bits.
 __device__ __forceinline__ uint32_t tf32_rn(float x) { return (__float_as_uint(x) + 0x1000u) & 0xFFFFE000u; }
@@ -201,206 +161,26 @@ __device__ __forceinline__ Split split(float x) {
 
 }  // namespace
 
-__global__ void __launch_bounds__(NT, 2) fused_tc_kernel(const float* __restrict__ Mt, const int64_t* __restrict__ tcOff,
-                                                         const int* __restrict__ tiles,
-                                                         const cplx<float>* __restrict__ bvec,
-                                                         cplx<float>* __restrict__ alm, int P2, int p, int L, int B,
-                                                         int64_t nalm, int* __restrict__ status) {
-    extern __shared__ __align__(1024) unsigned char smem[];   // two stages of (Ahi, Alo, Bhi, Blo)
-    __shared__ __align__(8) uint64_t mbar[2];
-    __shared__ uint32_t tmem_base;
-
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int m = tiles[3 * blockIdx.x], c = tiles[3 * blockIdx.x + 1], i0 = tiles[3 * blockIdx.x + 2];
-    const int par = ((m & 1) + c) & 1;
-    const int nrows = chain_len(m, c, L);
-    const int rp = (min(TM, nrows - i0) + 7) & ~7;   // stored rows of this tile
-    const int units = rp * 8;                         // 16-byte units of one A chunk
-    const int b0 = blockIdx.y * (TN / 2);
-    const float* At = Mt + tcOff[blockIdx.x];
-
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
-                     "r"(2 * TN)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    }
-    if (tid == 0) {
-        mbar_init(smem_u32(&mbar[0]), 1);
-        mbar_init(smem_u32(&mbar[1]), 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint32_t dtmem = tmem_base;
-
-    // b: thread -> map bl (8 maps per warp quarter) and 4 consecutive k; its real
-    // parts go to B row bl, its imaginary parts to row 32 + bl
-    const int bl = 8 * (warp & 3) + (lane & 7);
-    const int kq = 4 * (warp >> 2) + (lane >> 3);   // k = 4 kq .. 4 kq + 3 of the chunk
-    const int bmap = b0 + bl;
-    const cplx<float>* bsrc = bvec + (((int64_t)min(bmap, B - 1) * (p + 1) + m) * 2 + par) * P2;
-
-    // two register sets: the chunk after next is in flight while a chunk is split
-    float4 raA[AU], raB[AU];
-    float2 rbA[4], rbB[4];
-    auto load_chunk = [&](int ch, float4 (&ra)[AU], float2 (&rb)[4]) {
-        const float4* src = reinterpret_cast<const float4*>(At + (int64_t)ch * rp * 32);
-#pragma unroll
-        for (int j = 0; j < AU; ++j) {
-            const int u = tid + NT * j;
-            if (u < units) ra[j] = __ldg(src + u);
-        }
-        const int k = ch * KC + 4 * kq;
-#pragma unroll
-        for (int e = 0; e < 4; ++e)
-            rb[e] = (bmap < B && k + e < P2) ? __ldg(reinterpret_cast<const float2*>(bsrc + k + e))
-                                             : make_float2(0.f, 0.f);
-    };
-    // split the registers into the hi / lo tiles of stage st (rows of A past rp
-    // keep stale values: they only feed accumulator rows that are not stored)
-    auto store_chunk = [&](int st, const float4 (&ra)[AU], const float2 (&rb)[4]) {
-        unsigned char* Ahi = smem + st * STAGE;
-        unsigned char* Alo = Ahi + TILE_A;
-        unsigned char* Bhi = Ahi + 2 * TILE_A;
-        unsigned char* Blo = Bhi + TILE_B;
-#pragma unroll
-        for (int j = 0; j < AU; ++j) {
-            const int u = tid + NT * j;
-            if (u < units) {
-                const float4 v = ra[j];
-                const Split sx = split(v.x), sy = split(v.y), sz = split(v.z), sw = split(v.w);
-                *reinterpret_cast<uint4*>(Ahi + 16 * u) = make_uint4(sx.hi, sy.hi, sz.hi, sw.hi);
-                *reinterpret_cast<uint4*>(Alo + 16 * u) = make_uint4(sx.lo, sy.lo, sz.lo, sw.lo);
-            }
-        }
-        const uint32_t offr = (uint32_t)((bl >> 3) * 1024 + kq * 128 + (bl & 7) * 16);
-        const uint32_t offi = offr + 4 * 1024;   // row 32 + bl
-        const Split r0 = split(rb[0].x), r1 = split(rb[1].x), r2 = split(rb[2].x), r3 = split(rb[3].x);
-        const Split q0 = split(rb[0].y), q1 = split(rb[1].y), q2 = split(rb[2].y), q3 = split(rb[3].y);
-        *reinterpret_cast<uint4*>(Bhi + offr) = make_uint4(r0.hi, r1.hi, r2.hi, r3.hi);
-        *reinterpret_cast<uint4*>(Blo + offr) = make_uint4(r0.lo, r1.lo, r2.lo, r3.lo);
-        *reinterpret_cast<uint4*>(Bhi + offi) = make_uint4(q0.hi, q1.hi, q2.hi, q3.hi);
-        *reinterpret_cast<uint4*>(Blo + offi) = make_uint4(q0.lo, q1.lo, q2.lo, q3.lo);
-    };
-
-    // warp w drains TMEM lanes 32 (w & 3) .. +31 (its accumulator rows) and
-    // columns 32 (w >> 2) .. +31: the real parts (w < 4) or imaginary parts of 32 maps
-    float acc[32];
-#pragma unroll
-    for (int q = 0; q < 32; ++q) acc[q] = 0.f;
-    const uint32_t tsub = dtmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(32 * (warp >> 2));
-    auto drain = [&](int st) {
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            uint32_t v[16];
-            tmem_ld16(tsub + (uint32_t)(st * TN + 16 * h), v);
-#pragma unroll
-            for (int q = 0; q < 16; ++q) acc[16 * h + q] += __uint_as_float(v[q]);
-        }
-    };
-
-    const int nchunks = (P2 + KC - 1) / KC;
-    bool ok = true;
-    int issued = 0;   // chunks whose MMAs were committed
-    // one chunk: split it into stage ch & 1, issue its MMAs, start loading chunk
-    // ch + 2 into the same registers, then drain the accumulator of chunk ch - 1
-    auto step = [&](int ch, float4 (&ra)[AU], float2 (&rb)[4]) {
-        const int st = ch & 1;
-        // stage st was read by the MMAs of chunk ch - 2, which completed before
-        // their accumulator was drained in the previous step
-        store_chunk(st, ra, rb);
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic smem writes -> tensor core
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        if (__syncthreads_or(!ok)) {
-            ok = false;
-            return false;
-        }
-        if (tid == 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t aH = smem_u32(smem + st * STAGE), aL = aH + TILE_A, bH = aH + 2 * TILE_A, bL = bH + TILE_B;
-            const uint32_t d = dtmem + (uint32_t)(st * TN);
-            // cross terms first, while the accumulator is small, then A_hi B_hi:
-            // the tensor core's FP32 accumulation then rounds at most 4 times per
-            // chunk at the size of the chunk's partial sum
-#pragma unroll
-            for (int ks = 0; ks < KC / 8; ++ks) {
-                const uint32_t o = ks * 256;   // 8 k = two core matrices along K
-                mma_tf32(d, make_desc(aH + o, 128, 1024), make_desc(bL + o, 128, 1024), ks > 0 ? 1u : 0u);
-                mma_tf32(d, make_desc(aL + o, 128, 1024), make_desc(bH + o, 128, 1024), 1u);
-            }
-#pragma unroll
-            for (int ks = 0; ks < KC / 8; ++ks) {
-                const uint32_t o = ks * 256;
-                mma_tf32(d, make_desc(aH + o, 128, 1024), make_desc(bH + o, 128, 1024), 1u);
-            }
-            mma_commit(smem_u32(&mbar[st]));
-        }
-        issued = ch + 1;
-        if (ch + 2 < nchunks) load_chunk(ch + 2, ra, rb);   // in flight during the next two steps
-        if (ch > 0) {
-            // chunk ch - 1: wait for its MMAs, add its accumulator to the registers
-            const int sp = st ^ 1;
-            if (!mbar_wait(smem_u32(&mbar[sp]), (uint32_t)(((ch - 1) >> 1) & 1))) ok = false;
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            if (ok) drain(sp);
-        }
-        return true;
-    };
-    load_chunk(0, raA, rbA);
-    if (nchunks > 1) load_chunk(1, raB, rbB);
-    for (int ch = 0; ch < nchunks; ch += 2) {
-        if (!step(ch, raA, rbA)) break;
-        if (ch + 1 < nchunks && !step(ch + 1, raB, rbB)) break;
-    }
-    if (ok) {
-        const int cl = nchunks - 1;
-        if (!mbar_wait(smem_u32(&mbar[cl & 1]), (uint32_t)((cl >> 1) & 1))) ok = false;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (ok) drain(cl & 1);
-    }
-    if (__syncthreads_or(!ok)) {
-        if (tid == 0) {
-            atomicExch(status, HPX_ERR_TIMEOUT);
-            if (issued > 0) mbar_wait(smem_u32(&mbar[(issued - 1) & 1]), (uint32_t)(((issued - 1) >> 1) & 1));
-        }
-    } else {
-        const int i = i0 + 32 * (warp & 3) + lane;
-        if (i < nrows) {
-            const int64_t base = (int64_t)m * (2 * L + 1 - m) / 2 + m + c + 2 * (int64_t)i;
-            float* out = reinterpret_cast<float*>(alm) + 2 * base + (warp >> 2);
-#pragma unroll
-            for (int q = 0; q < 32; ++q)
-                if (b0 + q < B) out[2 * (int64_t)(b0 + q) * nalm] = acc[q];
-        }
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(dtmem), "r"(2 * TN) : "memory");
-}
-
-// Variant with the operator tile in tensor memory: every thread loads the 16
-// consecutive k of one row of the chunk (row = its TMEM lane, k half = warp / 4),
-// splits them in registers and stores the hi and lo parts to TMEM with
-// tcgen05.st; the MMAs read A from TMEM and only b passes through shared memory.
+// TF32 form: the chunks of the operator tile are copied by one thread into a
+// ring of NSA shared-memory stages with cp.async.bulk, NSA chunks ahead of their
+// use; every thread reads the 16 consecutive k of one row of the chunk (row =
+// its TMEM lane, k half = warp / 4; 8 lanes cover 128 contiguous bytes: no bank
+// conflicts), splits them in registers and stores the hi and lo parts to TMEM
+// with tcgen05.st; b is loaded into registers two chunks ahead and split into
+// shared memory.  One thread issues 4 K-steps x 3 kind::tf32 MMAs (M = 128,
+// N = 64, K = 8, A from TMEM) into a fresh accumulator and commits them to the
+// stage's mbarrier; the threads then wait for the previous chunk's MMAs and add
+// its accumulator (tcgen05.ld; warp w owns TMEM lanes 32 (w mod 4) .. +31).
 // TMEM per CTA (256 columns): accumulators of stage s at 64 s, A hi / lo of
-// stage s at 128 + 64 s and 128 + 64 s + 32.
-// BULK: the chunks of the operator tile (each one contiguous block of rp x 128
-// bytes) are copied by one thread into a ring of NSA shared-memory stages with
-// cp.async.bulk, NSA chunks ahead of their use, and every thread reads its 16
-// values from there (8 lanes cover 128 contiguous bytes: no bank conflicts);
-// otherwise they are loaded from global memory into registers two chunks ahead.
-// Shared memory: [NSA operator stages (BULK)] [two stages of (Bhi, Blo)].
-template <bool BULK>
+// stage s at 128 + 64 s and 128 + 64 s + 32.  Shared memory: [NSA operator
+// stages] [two stages of (Bhi, Blo)].
 __global__ void __launch_bounds__(NT, 2) fused_tc_tmem_kernel(
     const float* __restrict__ Mt, const int64_t* __restrict__ tcOff, const int* __restrict__ tiles,
     const cplx<float>* __restrict__ bvec, cplx<float>* __restrict__ alm, int P2, int p, int L, int B, int64_t nalm,
     int* __restrict__ status) {
     extern __shared__ __align__(1024) unsigned char smem_all[];
-    unsigned char* const sA = smem_all;                                // BULK: NSA x TILE_A
-    unsigned char* const smem = smem_all + (BULK ? NSA * TILE_A : 0);  // two stages of (Bhi, Blo)
+    unsigned char* const sA = smem_all;                  // NSA x TILE_A
+    unsigned char* const smem = smem_all + NSA * TILE_A;   // two stages of (Bhi, Blo)
     __shared__ __align__(8) uint64_t mbar[2];
     __shared__ __align__(8) uint64_t fullA[NSA];
     __shared__ uint32_t tmem_base;
@@ -432,11 +212,9 @@ __global__ void __launch_bounds__(NT, 2) fused_tc_tmem_kernel(
     if (tid == 0) {
         mbar_init(smem_u32(&mbar[0]), 1);
         mbar_init(smem_u32(&mbar[1]), 1);
-        if (BULK)
-            for (int q = 0; q < NSA; ++q) mbar_init(smem_u32(&fullA[q]), 1);
+        for (int q = 0; q < NSA; ++q) mbar_init(smem_u32(&fullA[q]), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        if (BULK)
-            for (int q = 0; q < NSA && q < nchunks; ++q) issueA(q);
+        for (int q = 0; q < NSA && q < nchunks; ++q) issueA(q);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -449,23 +227,18 @@ __global__ void __launch_bounds__(NT, 2) fused_tc_tmem_kernel(
     const int bmap = b0 + bl;
     const cplx<float>* bsrc = bvec + (((int64_t)min(bmap, B - 1) * (p + 1) + m) * 2 + par) * P2;
 
-    float4 raA[4], raB[4];
     float2 rbA[4], rbB[4];
-    auto load_chunk = [&](int ch, float4 (&ra)[4], float2 (&rb)[4]) {
-        if (!BULK && row < rp) {
-            const float* src = At + (int64_t)ch * rp * 32 + (row >> 3) * 256 + (row & 7) * 4;
-#pragma unroll
-            for (int q = 0; q < 4; ++q) ra[q] = __ldg(reinterpret_cast<const float4*>(src + (4 * khalf + q) * 32));
-        }
+    auto load_chunk = [&](int ch, float2 (&rb)[4]) {
         const int k = ch * KC + 4 * kq;
 #pragma unroll
         for (int e = 0; e < 4; ++e)
             rb[e] = (bmap < B && k + e < P2) ? __ldg(reinterpret_cast<const float2*>(bsrc + k + e))
                                              : make_float2(0.f, 0.f);
     };
-    auto store_chunk = [&](int ch, float4 (&ra)[4], const float2 (&rb)[4]) {
+    auto store_chunk = [&](int ch, const float2 (&rb)[4]) {
         const int st = ch & 1;
-        if (BULK) {   // this row's 16 values of the chunk from its shared-memory stage
+        float4 ra[4];   // this row's 16 values of the chunk from its shared-memory stage
+        {
             const unsigned char* a = sA + (ch % NSA) * TILE_A + (row >> 3) * 1024 + (row & 7) * 16;
 #pragma unroll
             for (int q = 0; q < 4; ++q)
@@ -514,15 +287,14 @@ __global__ void __launch_bounds__(NT, 2) fused_tc_tmem_kernel(
 
     bool ok = true;
     int issued = 0;
-    auto step = [&](int ch, float4 (&ra)[4], float2 (&rb)[4]) {
+    auto step = [&](int ch, float2 (&rb)[4]) {
         const int st = ch & 1;
-        if (BULK) {   // the chunk's bulk copy has landed
-            if (!mbar_wait(smem_u32(&fullA[ch % NSA]), (uint32_t)((ch / NSA) & 1))) ok = false;
-            else if (tid == 0) doneA = ch + 1;
-        }
+        // the chunk's bulk copy has landed
+        if (!mbar_wait(smem_u32(&fullA[ch % NSA]), (uint32_t)((ch / NSA) & 1))) ok = false;
+        else if (tid == 0) doneA = ch + 1;
         // stage st (A in TMEM, b in shared memory) was read by the MMAs of chunk
         // ch - 2, which completed before their accumulator was drained
-        store_chunk(ch, ra, rb);
+        store_chunk(ch, rb);
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -548,10 +320,10 @@ __global__ void __launch_bounds__(NT, 2) fused_tc_tmem_kernel(
             }
             mma_commit(smem_u32(&mbar[st]));
             // every thread has read operator stage ch % NSA (before the barrier)
-            if (BULK && ch + NSA < nchunks) issueA(ch + NSA);
+            if (ch + NSA < nchunks) issueA(ch + NSA);
         }
         issued = ch + 1;
-        if (ch + 2 < nchunks) load_chunk(ch + 2, ra, rb);
+        if (ch + 2 < nchunks) load_chunk(ch + 2, rb);
         if (ch > 0) {
             const int sp = st ^ 1;
             if (!mbar_wait(smem_u32(&mbar[sp]), (uint32_t)(((ch - 1) >> 1) & 1))) ok = false;
@@ -560,11 +332,11 @@ __global__ void __launch_bounds__(NT, 2) fused_tc_tmem_kernel(
         }
         return true;
     };
-    load_chunk(0, raA, rbA);
-    if (nchunks > 1) load_chunk(1, raB, rbB);
+    load_chunk(0, rbA);
+    if (nchunks > 1) load_chunk(1, rbB);
     for (int ch = 0; ch < nchunks; ch += 2) {
-        if (!step(ch, raA, rbA)) break;
-        if (ch + 1 < nchunks && !step(ch + 1, raB, rbB)) break;
+        if (!step(ch, rbA)) break;
+        if (ch + 1 < nchunks && !step(ch + 1, rbB)) break;
     }
     if (ok) {
         const int cl = nchunks - 1;
@@ -1004,22 +776,13 @@ void launch_fused_tc(const hpx_plan_s* P, float* alm, cudaStream_t s) {
     fused_tc_ws_kernel<<<grid, NTW, smem_h, s>>>((const unsigned char*)P->fusedM, P->tcOff, P->tcRinv, P->fusedTiles,
                                                  (const cplx<float>*)P->bvec, P->bscale, (cplx<float>*)alm, g.P2,
                                                  g.p, g.L, g.B, g.nalm, P->d_status);
-    return;
+#else
+    const size_t smem_t = NSA * TILE_A + 4 * TILE_B;
+    cudaFuncSetAttribute(fused_tc_tmem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_t);
+    fused_tc_tmem_kernel<<<grid, NT, smem_t, s>>>((const float*)P->fusedM, P->tcOff, P->fusedTiles,
+                                                  (const cplx<float>*)P->bvec, (cplx<float>*)alm, g.P2, g.p, g.L,
+                                                  g.B, g.nalm, P->d_status);
 #endif
-#if HPX_TC_TMEM_A
-    constexpr bool bulk = HPX_TC_A_BULK != 0;
-    const size_t smem_t = 4 * TILE_B + (bulk ? NSA * TILE_A : 0);
-    cudaFuncSetAttribute(fused_tc_tmem_kernel<bulk>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_t);
-    fused_tc_tmem_kernel<bulk><<<grid, NT, smem_t, s>>>((const float*)P->fusedM, P->tcOff, P->fusedTiles,
-                                                        (const cplx<float>*)P->bvec, (cplx<float>*)alm, g.P2, g.p,
-                                                        g.L, g.B, g.nalm, P->d_status);
-    return;
-#endif
-    const size_t smem = 2 * STAGE;
-    cudaFuncSetAttribute(fused_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    fused_tc_kernel<<<grid, NT, smem, s>>>((const float*)P->fusedM, P->tcOff, P->fusedTiles,
-                                           (const cplx<float>*)P->bvec, (cplx<float>*)alm, g.P2, g.p, g.L, g.B,
-                                           g.nalm, P->d_status);
 }
 
 }  // namespace hpx
