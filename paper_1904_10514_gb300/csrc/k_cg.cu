@@ -1,4 +1,4 @@
-// Conjugate-gradient form of the latitude least squares (Sec. 3.2.2; SURVEY f2):
+// Conjugate-gradient form of the latitude least squares (Sec. 3.2.2):
 // instead of applying the premultiplied inverse, each column's normal equations
 //     T g = b     (T = the Toeplitz-plus-Hankel Gram matrix of the cosine or
 //                  sine basis at the latitude nodes, one per parity of m and j)

@@ -56,7 +56,7 @@ struct PlanTables {
     // The two factors of D = C T^{-1}: C = sqrt(2 pi) <Pbar_l, B_j> (the change of
     // basis, same layout as D) and the normal-equation matrix T of each (mpar, par)
     // block, T_ab = (tt[|j_a - j_b|] +- tt[j_a + j_b]) / 2 with tt = tc (cosine,
-    // +) or ts (sine, -), j = 0..2p (the conjugate-gradient form)
+    // +) or ts (sine, -), j = 0..2p (the conjugate-gradient form, HPX_FLAG_CG)
     std::vector<double> C, tc, ts;
 
     // ---- Givens rotations of the order m' -> m'+2 connection (Sec. 3.3)
