@@ -112,6 +112,46 @@ def stage_work(ns, L, B, es=8):
     }
 
 
+def stage_roofline(kind, amount, ms, peaks):
+    """Roofline entry of one stage: algorithmic bytes (or flops) of one launch over its time."""
+    t = ms / 1e3
+    if kind == "hbm":
+        peak = peaks.get("hbm_gbs", 6800.0)
+        roof = {"bound": "hbm", "achieved": amount / t / 1e9, "peak": peak, "unit": "GB/s",
+                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
+    else:
+        roof = {"bound": "alu", "achieved": amount / t / 1e12, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "peak_source": "FP32 FMA pipes: 152 SMs x 128 lanes x 2 flop x 2.070 GHz"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    return roof
+
+
+def roofline_report(work, per_launch, peaks):
+    """The roofline object of the dominant stage (longest time per call) and a short entry per stage.
+
+    work: stage -> (bound, algorithmic bytes or flops per launch); per_launch: stage -> ms per launch.
+    DRAM bytes per launch come from an ncu capture (dram__bytes_read + write) over the algorithmic bytes of
+    the same kernel at Nside 512 x 32 maps, scaled to this launch (traffic grows with the operator size like
+    the algorithmic bytes: tile rows padded to 8, K to a multiple of 32); null for stages without a capture.
+    """
+    names = [n for n in per_launch if n in work and work[n][1] > 0]
+    dom = max(names, key=lambda n: per_launch[n])
+    kind, amount = work[dom]
+    roof = stage_roofline(kind, amount, per_launch[dom], peaks)
+    ratio = TRAFFIC_OVER_ALGORITHMIC.get(dom)
+    roof["traffic"] = amount * ratio if (ratio and kind == "hbm") else None
+    roof["traffic_source"] = ("ncu at Nside 512, 32 maps: %.4f x the algorithmic bytes, scaled" % ratio
+                              if roof["traffic"] else None)
+    roof["kernel"] = dom
+    roof["per_launch_ms"] = per_launch[dom]
+    per_stage = {}
+    for n in names:
+        r = stage_roofline(work[n][0], work[n][1], per_launch[n], peaks)
+        per_stage[n] = {"bound": r["bound"], "ms": per_launch[n], "achieved": r["achieved"], "unit": r["unit"],
+                        "frac": r["frac"]}
+    return roof, per_stage
+
+
 # ------------------------------------------------------------------ clocks
 class Clocks:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -426,32 +466,12 @@ def main():
             dist.destroy_process_group()
         return
 
-    # roofline of the dominant kernel
+    # roofline of the dominant kernel (and of every stage)
     work = stage_work(NSIDE, LMAX, BATCH)
     names = [n for n in plan.stages if n != "unused"]
     per_launch = {n: stage_ms[k] / max(ncalls, 1) for k, n in enumerate(names)}
-    dom = max(names, key=lambda n: per_launch[n])
-    kind, amount = work[dom]
     peaks = json.load(open(MEASURED)) if os.path.exists(MEASURED) else {}
-    t_dom = per_launch[dom] / 1e3
-    if kind == "hbm":
-        peak = peaks.get("hbm_gbs", 6800.0)
-        roof = {"bound": "hbm", "achieved": amount / t_dom / 1e9, "peak": peak, "unit": "GB/s",
-                "peak_source": "measured" if peaks else "fallback"}
-    else:
-        peak = FP32_PEAK_TFLOPS
-        roof = {"bound": "alu", "achieved": amount / t_dom / 1e12, "peak": peak, "unit": "TFLOP/s",
-                "peak_source": "FP32 FMA pipes: 152 SMs x 128 lanes x 2 flop x 2.070 GHz"}
-    roof["frac"] = roof["achieved"] / roof["peak"]
-    # DRAM bytes per launch: ncu (dram__bytes_read + write) over the algorithmic bytes of the
-    # same kernel at Nside 512 x 32 maps, scaled to this launch (traffic grows with the
-    # operator size like the algorithmic bytes: tile rows padded to 8, K to a multiple of 32)
-    ratio = TRAFFIC_OVER_ALGORITHMIC.get(dom)
-    roof["traffic"] = amount * ratio if (ratio and kind == "hbm") else None
-    roof["traffic_source"] = ("ncu at Nside 512, 32 maps: %.4f x the algorithmic bytes, scaled" % ratio
-                              if roof["traffic"] else None)
-    roof["kernel"] = dom
-    roof["per_launch_ms"] = per_launch[dom]
+    roof, per_stage = roofline_report(work, per_launch, peaks)
 
     cpu = None
     if not args.no_cpu:
@@ -473,7 +493,7 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": "Gpix/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": config_dict(), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+            "config": config_dict(), "roofline": roof, "roofline_stages": per_stage, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": (hp.lib().hpx_plan_launches(plan.handle) + 1) * args.steps, "clocks": clk, "fp64_single_map": fp64, "sh_synthesis_fp32": synthesis, "ablation_cg_latitude_solve": cg,
             "fp32_batched_over_fp64_single": value / world / fp64["value"],
             "stages_ms_per_launch": per_launch, "plan_build_s": plan_build_s, "plan_gb": plan.nbytes / 1e9,
