@@ -211,9 +211,25 @@ def oracle_sample(maps0, ms):
     return time.perf_counter() - t0, cols
 
 
-def cpu_gpix(seconds, ncols):
-    full = seconds * (LMAX + 1) / ncols          # scaled to all 2049 orders of one map
-    return 12 * NSIDE * NSIDE / full / 1e9
+def fit_cost_model(n_small, t_small, n_large, t_large):
+    """The oracle's time for n orders of one map is fixed + n * per_order: the fixed part
+    (the least-squares factorisation in latitude, the per-ring Python loop, the Fourier
+    basis at the quadrature nodes) does not grow with the number of orders.  Two sample
+    sizes give both terms."""
+    per = max((t_large - t_small) / (n_large - n_small), 1e-9)
+    fixed = max(t_small - n_small * per, 0.0)
+    return fixed, per
+
+
+def full_map_seconds(fixed, per):
+    return fixed + (LMAX + 1) * per
+
+
+def cpu_gpix(seconds_full_map):
+    return 12 * NSIDE * NSIDE / seconds_full_map / 1e9
+
+
+SMALL_ORDERS, LARGE_ORDERS = [0, 1], list(range(8))
 
 
 def run_reference(args, rank):
@@ -221,20 +237,31 @@ def run_reference(args, rank):
         return
     import skies
     maps0 = skies.workload_maps(WORKLOAD, nmaps=1, dtype=np.float32)[0]
-    ms = [0, 1]
-    for _ in range(args.warmup):
-        oracle_sample(maps0, ms)
-    ts = [oracle_sample(maps0, ms)[0] for _ in range(args.steps)]
+    # warm-up steps alternate two sample sizes to fit the fixed and per-order costs
+    ts_s, ts_l = [], []
+    for k in range(args.warmup):
+        if k % 2 == 0:
+            ts_l.append(oracle_sample(maps0, LARGE_ORDERS)[0])
+        else:
+            ts_s.append(oracle_sample(maps0, SMALL_ORDERS)[0])
+    if not ts_s:
+        ts_s.append(oracle_sample(maps0, SMALL_ORDERS)[0])
+    fixed, _ = fit_cost_model(len(SMALL_ORDERS), float(np.median(ts_s)), len(LARGE_ORDERS), float(np.median(ts_l)))
+    # every timed step: orders 0..7 of map 0; its full-map time = fixed + 2049 x its per-order time
+    ts = [oracle_sample(maps0, LARGE_ORDERS)[0] for _ in range(args.steps)]
+    fulls = [full_map_seconds(fixed, max(t - fixed, 1e-9) / len(LARGE_ORDERS)) for t in ts]
     t = float(np.mean(ts))
-    v = cpu_gpix(t, len(ms))
-    sample = ("orders m=0,1 of map 0 (2 of 2049 columns) per step, time scaled x2049/2 to a full "
-              "map; FP64 oracle (direct ring DFTs, dense QR least squares, Gauss-Legendre projection)")
+    v = cpu_gpix(float(np.mean(fulls)))
+    sample = ("orders m=0..7 of map 0 (8 of 2049 columns) per step; full-map time = fixed + 2049 x per-order "
+              "(fixed part %.2f s fitted from the warm-up steps' 2- and 8-order samples); FP64 oracle (direct "
+              "ring DFTs, dense least squares, Gauss-Legendre projection)" % fixed)
     line = {"metric": METRIC, "value": v, "unit": "Gpix/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_dict(),
             "impl": "reference",
             "cpu_baseline": {"value": v, "unit": "Gpix/s", "cores": os.cpu_count(), "kind": "oracle",
-                             "sample": sample},
+                             "sample": sample, "model": {"fixed_s": fixed,
+                                                         "full_map_s": float(np.mean(fulls))}},
             "e2e": {"value": v, "unit": "Gpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -441,6 +468,37 @@ def main():
     plan_cg.close()
     del alm_cg
 
+    # the run-time Givens sweeps (HPX_FLAG_SWEEPS): D applied alone and the rotation kernel,
+    # stage by stage, same batch
+    plan_sw = hp.Plan(NSIDE, LMAX, nb, "fp32", sweeps=True)
+    alm_sw = torch.empty_like(alm)
+    for _ in range(2):
+        plan_sw.analyze(maps, out=alm_sw)
+    torch.cuda.synchronize()
+    nsw = 3
+    hp.hpx_set_profiling(plan_sw.handle, 1)
+    e0.record(stream)
+    for _ in range(nsw):
+        plan_sw.analyze(maps, out=alm_sw)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_sw = e0.elapsed_time(e1) / nsw / 1e3
+    sw_ms, sw_calls = hp.hpx_stage_times(plan_sw.handle)
+    hp.hpx_set_profiling(plan_sw.handle, 0)
+    sw_stage = {n: sw_ms[k] / max(sw_calls, 1) for k, n in enumerate(plan_sw.stages)}
+    sw_work = stage_work(NSIDE, LMAX, nb)
+    rot_flops = sw_work["rot_sweep"][1]
+    sweeps = {"value": npix_step / t_sw / 1e9, "unit": "Gpix/s", "ms_per_step": t_sw * 1e3,
+              "stages_ms_per_launch": sw_stage,
+              "rot_sweep": {"flops": rot_flops, "tflops": rot_flops / (sw_stage["rot_sweep"] / 1e3) / 1e12,
+                            "fp32_pipe_frac": rot_flops / (sw_stage["rot_sweep"] / 1e3) / 1e12 / FP32_PEAK_TFLOPS,
+                            "peak": "FP32 FMA pipes: 152 SMs x 128 lanes x 2 flop x 2.070 GHz"},
+              "lat_solve": {"flops": sw_work["lat_solve"][1],
+                            "tflops": sw_work["lat_solve"][1] / (sw_stage["lat_solve"] / 1e3) / 1e12},
+              "max_abs_diff_vs_default": float((alm_sw - alm).abs().max() / alm.abs().max())}
+    plan_sw.close()
+    del alm_sw
+
     # the plain FP64 single-map form on the same GPU
     plan64 = hp.Plan(NSIDE, LMAX, 1, "fp64")
     m64 = maps[:1].double().contiguous()
@@ -475,8 +533,10 @@ def main():
 
     cpu = None
     if not args.no_cpu:
+        t_small, _ = oracle_sample(maps_np[0], SMALL_ORDERS)
         ms = list(range(16))
         secs, cols = oracle_sample(maps_np[0], ms)
+        fixed, per = fit_cost_model(len(SMALL_ORDERS), t_small, len(ms), secs)
         got = alm[0].cpu().numpy()
         worst = 0.0
         for m in ms:
@@ -484,17 +544,29 @@ def main():
             g = got[i0:i0 + LMAX - m + 1]
             r = cols[m][0]
             worst = max(worst, float(np.max(np.abs(g - r)) / np.max(np.abs(r))))
-        cpu = {"value": cpu_gpix(secs, len(ms)), "unit": "Gpix/s", "cores": os.cpu_count(),
+        # a directly measured point: one whole Nside-256 map (lmax 512), no extrapolation
+        from oracle import hp2sph
+        m256 = skies.small_powerlaw_maps(256, 1, seed=6256, alpha=2.0, noise=1e-3)[0][0]
+        t0 = time.perf_counter()
+        hp2sph.analyze(m256, 256, 512)
+        t256 = time.perf_counter() - t0
+        cpu = {"value": cpu_gpix(full_map_seconds(fixed, per)), "unit": "Gpix/s", "cores": os.cpu_count(),
                "kind": "oracle",
-               "sample": "orders m=0..15 of map 0 (16 of 2049 columns), FP64 oracle, %.1f s, scaled "
-                         "x2049/16 to one full map" % secs,
+               "sample": "orders m=0..1 (%.1f s) and m=0..15 (%.1f s) of map 0, FP64 oracle; full-map time = "
+                         "fixed + 2049 x per-order = %.1f + 2049 x %.3f s" % (t_small, secs, fixed, per),
+               "model": {"fixed_s": fixed, "per_order_s": per, "full_map_s": full_map_seconds(fixed, per)},
+               "direct_nside256": {"value": 12 * 256 * 256 / t256 / 1e9, "unit": "Gpix/s", "seconds": t256,
+                                   "what": "one whole Nside-256 map, lmax 512, measured end to end"},
                "sample_max_rel_err_vs_gpu": worst}
 
     line = {"metric": METRIC, "value": value, "unit": "Gpix/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 (operator contraction: f16 hi/lo pairs on tcgen05, f32 accumulation)",
+            "data": "synthetic",
             "config": config_dict(), "roofline": roof, "roofline_stages": per_stage, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": (hp.lib().hpx_plan_launches(plan.handle) + 1) * args.steps, "clocks": clk, "fp64_single_map": fp64, "sh_synthesis_fp32": synthesis, "ablation_cg_latitude_solve": cg,
+            "sweeps_path": sweeps,
             "fp32_batched_over_fp64_single": value / world / fp64["value"],
             "stages_ms_per_launch": per_launch, "plan_build_s": plan_build_s, "plan_gb": plan.nbytes / 1e9,
             "plan_path": "sweeps" if plan.flags & hp.HPX_FLAG_SWEEPS else "per-order operators"}

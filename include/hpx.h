@@ -164,6 +164,27 @@ int hpx_synthesize(hpx_plan_s* plan, const void* alm, void* maps);
  * plan made with HPX_FLAG_SYNTHESIS (else HPX_ERR_STATE).  Asynchronous. */
 int hpx_sh_synthesis(hpx_plan_s* plan, const void* alm, void* maps);
 
+/* Vector-Jacobian product of hpx_analyze, for gradients of a loss L(alm) with
+ * respect to the maps.  galm = dL/dRe(a) + i dL/dIm(a) for every stored
+ * coefficient (the packed m >= 0 array read as independent real and imaginary
+ * parts, the convention torch uses for complex tensors); gmaps = dL/df, i.e.
+ * gmaps_i = sum over stored (l, m) of Re(conj(galm_lm) d a_lm / d f_i).  It is
+ * the transpose of the analysis (Algorithm 1 step by step, in reverse) under
+ * the plain Euclidean inner product on the packed array: hpx_synthesize with
+ * unit instead of doubled weight on m > 0.  The imaginary parts of galm at
+ * m = 0 and m = 2 nside are ignored (the analysis returns those coefficients
+ * real).  Layouts as hpx_synthesize (uneven batches concatenated); gmaps is
+ * overwritten.  Asynchronous. */
+int hpx_analyze_vjp(hpx_plan_s* plan, const void* galm, void* gmaps);
+
+/* Vector-Jacobian product of hpx_cl (Eq. APS): given gcl = dL/dC_l
+ * ([batch][lmax + 1] double, device) and the coefficients alm the spectrum was
+ * computed from, writes galm = dL/dRe(a) + i dL/dIm(a) in alm's layout and
+ * precision:  galm_lm = gcl_l * 2 w_m a_lm / (2l + 1), w_0 = 1, w_m = 2 (m > 0).
+ * Uneven batches: alm, gcl and galm concatenated as for hpx_cl.  galm may not
+ * alias alm.  Asynchronous. */
+int hpx_cl_vjp(hpx_plan_s* plan, const void* alm, const double* gcl, void* galm);
+
 /* Angular power spectrum of Eq. (APS) for real maps,
  * C_l = (|a_l0|^2 + 2 sum_{m=1}^{l} |a_lm|^2) / (2l + 1),
  * squares summed in groups of 4 in the plan precision, the group sums in
@@ -220,7 +241,9 @@ int hpx_stage_times(hpx_plan_s* plan, float* ms, int n, int* ncalls);
  * (cudaGetSymbolAddress, with that device current); make that first call before
  * any stream capture.  A call whose nside/lmax differ from the previous call's on
  * the same device rebuilds the tables on the host and copies them into the array
- * (synchronising `cuda_stream`).  All calls share the array and it keeps the
+ * (synchronising `cuda_stream`); such a call made while `cuda_stream` is being
+ * captured returns HPX_ERR_STATE and touches neither the stream nor the array
+ * (make one call of that size before the capture starts).  All calls share the array and it keeps the
  * last call's contents, so calls that overlap on the GPU (different streams or
  * threads) race; serialise them.  Asynchronous on `cuda_stream` otherwise. */
 #define HPX_NOALLOC_MAX_NSIDE 128

@@ -32,7 +32,8 @@ HPX_FP64 = 1
 EXPORTS = ["hpx_plan", "hpx_plan_ex", "hpx_set_stream", "hpx_analyze", "hpx_synthesize", "hpx_cl",
            "hpx_sync", "hpx_destroy", "hpx_npix", "hpx_nalm", "hpx_plan_lmax", "hpx_plan_bytes",
            "hpx_last_error", "hpx_strerror", "hpx_set_profiling", "hpx_stage_times",
-           "hpx_analyze_noalloc", "hpx_plan_flags", "hpx_selftest_timeout", "hpx_sh_synthesis", "hpx_plan_launches"]
+           "hpx_analyze_noalloc", "hpx_plan_flags", "hpx_selftest_timeout", "hpx_sh_synthesis", "hpx_plan_launches",
+           "hpx_analyze_vjp", "hpx_cl_vjp"]
 HPX_FLAG_SWEEPS = 1
 HPX_FLAG_GRAPH = 2
 HPX_FLAG_SIMT = 4
@@ -97,6 +98,8 @@ def lib():
             "hpx_selftest_timeout": (i32, [vp, i32]),
             "hpx_sh_synthesis": (i32, [vp, vp, vp]),
             "hpx_plan_launches": (i32, [vp]),
+            "hpx_analyze_vjp": (i32, [vp, vp, vp]),
+            "hpx_cl_vjp": (i32, [vp, vp, vp, vp]),
             "hpx_stage_times": (i32, [vp, ctypes.POINTER(ctypes.c_float), i32, ctypes.POINTER(ctypes.c_int)]),
         }
         for name, (res, args) in sig.items():
@@ -153,6 +156,14 @@ def hpx_cl(plan, alm_ptr, cl_ptr):
 
 def hpx_sync(plan):
     return lib().hpx_sync(plan)
+
+
+def hpx_analyze_vjp(plan, galm_ptr, gmaps_ptr):
+    return lib().hpx_analyze_vjp(plan, galm_ptr, gmaps_ptr)
+
+
+def hpx_cl_vjp(plan, alm_ptr, gcl_ptr, galm_ptr):
+    return lib().hpx_cl_vjp(plan, alm_ptr, gcl_ptr, galm_ptr)
 
 
 def hpx_destroy(plan):
@@ -276,6 +287,25 @@ class Plan:
         self._check(hpx_synthesize(self.handle, alm.data_ptr(), out.data_ptr()), "hpx_synthesize")
         return out
 
+    def analyze_vjp(self, galm, out=None):
+        """dL/dmaps from galm = dL/dRe(alm) + i dL/dIm(alm) (hpx_analyze_vjp)."""
+        galm = galm.contiguous()
+        if out is None:
+            out = self.torch.empty(self._shape(self.npix), dtype=self.rdtype, device=galm.device)
+        self._stream()
+        self._check(hpx_analyze_vjp(self.handle, galm.data_ptr(), out.data_ptr()), "hpx_analyze_vjp")
+        return out
+
+    def cl_vjp(self, alm, gcl, out=None):
+        """dL/dalm from gcl = dL/dC_l and the coefficients (hpx_cl_vjp)."""
+        alm = alm.contiguous()
+        gcl = gcl.to(self.torch.float64).contiguous()
+        if out is None:
+            out = self.torch.empty_like(alm)
+        self._stream()
+        self._check(hpx_cl_vjp(self.handle, alm.data_ptr(), gcl.data_ptr(), out.data_ptr()), "hpx_cl_vjp")
+        return out
+
     def sh_synthesis(self, alm, out=None):
         """Spherical-harmonic synthesis f = sum a_lm Y_lm at the pixel centres
         (plan made with synthesis=True): alm (batch, n_alm) -> maps (batch, npix)."""
@@ -316,11 +346,8 @@ def _torch_functions():
     import torch
 
     class AnalyzeFn(torch.autograd.Function):
-        """alm = A maps; the backward pass is the library's adjoint (hpx_synthesize).
-
-        torch hands the backward pass g = dL/dRe(a) + i dL/dIm(a).  The map gradient
-        is sum_lm Re(A[lm, i] conj(g_lm)), i.e. the transpose with unit weights;
-        hpx_synthesize weights m > 0 by 2, so those entries are halved first."""
+        """alm = A maps; the backward pass is the library's vector-Jacobian
+        product of the analysis (hpx_analyze_vjp)."""
 
         @staticmethod
         def forward(ctx, maps, plan):
@@ -329,13 +356,10 @@ def _torch_functions():
 
         @staticmethod
         def backward(ctx, g):
-            plan = ctx.plan
-            g = g.contiguous().clone()
-            g[:, plan.lmax + 1:] *= 0.5
-            return plan.synthesize(g), None
+            return ctx.plan.analyze_vjp(g), None
 
     class ClFn(torch.autograd.Function):
-        """C_l of Eq. (APS) (hpx_cl); backward dL/da_lm = dL/dC_l * 2 w_m a_lm / (2l+1)."""
+        """C_l of Eq. (APS) (hpx_cl); the backward pass is hpx_cl_vjp."""
 
         @staticmethod
         def forward(ctx, alm, plan):
@@ -346,34 +370,26 @@ def _torch_functions():
         @staticmethod
         def backward(ctx, gcl):
             (alm,) = ctx.saved_tensors
-            plan = ctx.plan
-            l_idx, w_idx = plan.index_tables()
-            scale = gcl[:, l_idx] * (2.0 * w_idx / (2.0 * l_idx.to(gcl.dtype) + 1.0))
-            return alm * scale.to(alm.real.dtype), None
+            return ctx.plan.cl_vjp(alm, gcl), None
 
     return AnalyzeFn, ClFn
 
 
+_FNS = None
+
+
+def _fns():
+    global _FNS
+    if _FNS is None:
+        _FNS = _torch_functions()
+    return _FNS
+
+
 def analyze(maps, plan):
     """Differentiable analysis (torch.autograd) through the C ABI."""
-    return _torch_functions()[0].apply(maps, plan)
+    return _fns()[0].apply(maps, plan)
 
 
 def cl(alm, plan):
     """Differentiable C_l (torch.autograd) through the C ABI."""
-    return _torch_functions()[1].apply(alm, plan)
-
-
-def _index_tables(self):
-    """(l, weight) of every packed coefficient, on the plan's device (cached)."""
-    if getattr(self, "_idx", None) is None:
-        t = self.torch
-        L = self.lmax
-        m = t.cat([t.full((L + 1 - k,), k, dtype=t.int64) for k in range(L + 1)])
-        l = t.cat([t.arange(k, L + 1, dtype=t.int64) for k in range(L + 1)])
-        w = t.where(m == 0, 1.0, 2.0).to(t.float64)
-        self._idx = (l.to(self.device), w.to(self.device))
-    return self._idx
-
-
-Plan.index_tables = _index_tables
+    return _fns()[1].apply(alm, plan)

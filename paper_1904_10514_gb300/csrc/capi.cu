@@ -494,6 +494,38 @@ int hpx_synthesize(hpx_plan_s* P, const void* alm, void* maps) {
     return set_err(HPX_OK);
 }
 
+int hpx_analyze_vjp(hpx_plan_s* P, const void* galm, void* gmaps) {
+    if (!P || !galm || !gmaps) return set_err(HPX_ERR_ARG);
+    if (P->flags & HPX_FLAG_CHECKED) {
+        if (!device_pointer(P, gmaps) || !device_pointer(P, galm)) return set_err(HPX_ERR_ARG);
+        const int64_t n = 2 * (P->group ? P->total_nalm : P->g.nalm * P->g.B);
+        hpx::launch_finite_check(galm, n, P->precision == HPX_FP64, P->d_status, P->stream);
+    }
+    if (P->group) return set_err(hpx::group_analyze_vjp(P, galm, gmaps));
+    if (P->precision == HPX_FP64) hpx::launch_adjoint<double>(P, (const double*)galm, (double*)gmaps, P->stream, 1.0);
+    else hpx::launch_adjoint<float>(P, (const float*)galm, (float*)gmaps, P->stream, 1.0f);
+    if (cudaGetLastError() != cudaSuccess) return set_err(HPX_ERR_CUDA);
+    return set_err(HPX_OK);
+}
+
+int hpx_cl_vjp(hpx_plan_s* P, const void* alm, const double* gcl, void* galm) {
+    if (!P || !alm || !gcl || !galm) return set_err(HPX_ERR_ARG);
+    if ((P->flags & HPX_FLAG_CHECKED) &&
+        (!device_pointer(P, alm) || !device_pointer(P, gcl) || !device_pointer(P, galm)))
+        return set_err(HPX_ERR_ARG);
+    const int64_t* ao = P->group ? P->d_almel : nullptr;
+    const int64_t* co = P->group ? P->d_clel : nullptr;
+    const int* lm = P->group ? P->d_lmax : nullptr;
+    if (P->precision == HPX_FP64)
+        hpx::launch_cl_vjp<double>((const double*)alm, gcl, (double*)galm, ao, co, lm, P->g.L, P->g.B, P->g.L,
+                                   P->g.nalm, P->stream);
+    else
+        hpx::launch_cl_vjp<float>((const float*)alm, gcl, (float*)galm, ao, co, lm, P->g.L, P->g.B, P->g.L,
+                                  P->g.nalm, P->stream);
+    if (cudaGetLastError() != cudaSuccess) return set_err(HPX_ERR_CUDA);
+    return set_err(HPX_OK);
+}
+
 int hpx_sh_synthesis(hpx_plan_s* P, const void* alm, void* maps) {
     if (!P || !alm || !maps) return set_err(HPX_ERR_ARG);
     if (!(P->flags & HPX_FLAG_SYNTHESIS)) return set_err(HPX_ERR_STATE);

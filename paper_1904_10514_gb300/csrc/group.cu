@@ -69,7 +69,8 @@ hpx_plan_s* group_create(const hpx_plan_desc* d, int* err) {
     cudaGetDevice(&G->device);
     const size_t es = fp64 ? 8 : 4;
     // per-map offsets (bytes) in the caller's concatenated arrays
-    std::vector<int64_t> mapoff(B), almoff(B), cloff(B);
+    std::vector<int64_t> mapoff(B), almoff(B), cloff(B), almel(B), clel(B);
+    std::vector<int> lmaxv(B);
     std::map<std::pair<int, int>, std::vector<int>> byNside;   // (nside, lmax) -> maps
     int64_t om = 0, oa = 0, oc = 0;
     int Lmax_all = 0;
@@ -80,6 +81,9 @@ hpx_plan_s* group_create(const hpx_plan_desc* d, int* err) {
         mapoff[i] = om * (int64_t)es;
         almoff[i] = oa * (int64_t)es * 2;
         cloff[i] = oc * 8;
+        almel[i] = oa;
+        clel[i] = oc;
+        lmaxv[i] = L;
         om += 12LL * ns * ns;
         oa += nalm_of(L);
         oc += L + 1;
@@ -139,12 +143,18 @@ hpx_plan_s* group_create(const hpx_plan_desc* d, int* err) {
         ok = cudaMalloc(&G->d_idx, idx.size() * sizeof(int)) == cudaSuccess &&
              cudaMalloc(&G->d_mapoff, B * sizeof(int64_t)) == cudaSuccess &&
              cudaMalloc(&G->d_almoff, B * sizeof(int64_t)) == cudaSuccess &&
-             cudaMalloc(&G->d_cloff, B * sizeof(int64_t)) == cudaSuccess;
+             cudaMalloc(&G->d_cloff, B * sizeof(int64_t)) == cudaSuccess &&
+             cudaMalloc(&G->d_almel, B * sizeof(int64_t)) == cudaSuccess &&
+             cudaMalloc(&G->d_clel, B * sizeof(int64_t)) == cudaSuccess &&
+             cudaMalloc(&G->d_lmax, B * sizeof(int)) == cudaSuccess;
         if (ok) {
             cudaMemcpy(G->d_idx, idx.data(), idx.size() * sizeof(int), cudaMemcpyHostToDevice);
             cudaMemcpy(G->d_mapoff, mapoff.data(), B * sizeof(int64_t), cudaMemcpyHostToDevice);
             cudaMemcpy(G->d_almoff, almoff.data(), B * sizeof(int64_t), cudaMemcpyHostToDevice);
             cudaMemcpy(G->d_cloff, cloff.data(), B * sizeof(int64_t), cudaMemcpyHostToDevice);
+            cudaMemcpy(G->d_almel, almel.data(), B * sizeof(int64_t), cudaMemcpyHostToDevice);
+            cudaMemcpy(G->d_clel, clel.data(), B * sizeof(int64_t), cudaMemcpyHostToDevice);
+            cudaMemcpy(G->d_lmax, lmaxv.data(), B * sizeof(int), cudaMemcpyHostToDevice);
         } else {
             *err = HPX_ERR_OOM;
         }
@@ -166,6 +176,9 @@ void group_free(hpx_plan_s* G) {
     if (G->d_mapoff) cudaFree(G->d_mapoff);
     if (G->d_almoff) cudaFree(G->d_almoff);
     if (G->d_cloff) cudaFree(G->d_cloff);
+    if (G->d_almel) cudaFree(G->d_almel);
+    if (G->d_clel) cudaFree(G->d_clel);
+    if (G->d_lmax) cudaFree(G->d_lmax);
 }
 
 int group_analyze(hpx_plan_s* G, const void* maps, void* alm) {
@@ -209,6 +222,10 @@ int group_alm_to_maps(hpx_plan_s* G, const void* alm, void* maps, int (*fn)(hpx_
 }  // namespace
 
 int group_synthesize(hpx_plan_s* G, const void* alm, void* maps) { return group_alm_to_maps(G, alm, maps, hpx_synthesize); }
+
+int group_analyze_vjp(hpx_plan_s* G, const void* galm, void* gmaps) {
+    return group_alm_to_maps(G, galm, gmaps, hpx_analyze_vjp);
+}
 
 int group_sh_synthesis(hpx_plan_s* G, const void* alm, void* maps) {
     return group_alm_to_maps(G, alm, maps, hpx_sh_synthesis);

@@ -305,7 +305,7 @@ __global__ void pole_adj_kernel(const cplx<T>* __restrict__ Y, T* __restrict__ m
 }
 
 template <class T>
-void launch_adjoint(const hpx_plan_s* P, const T* alm, T* maps, cudaStream_t s) {
+void launch_adjoint(const hpx_plan_s* P, const T* alm, T* maps, cudaStream_t s, T wpos) {
     const auto& g = P->g;
     const auto& t = P->t;
     {
@@ -314,7 +314,7 @@ void launch_adjoint(const hpx_plan_s* P, const T* alm, T* maps, cudaStream_t s) 
         const int blocks = (nitems * 32 + 127) / 128;
         constexpr int KMAX = sizeof(T) == 4 ? 32 : 16;
         rot_adj_kernel<T, KMAX><<<blocks, 128, 0, s>>>(alm, (T*)P->beta, t.skOff, (const cplx<T>*)t.skewT, t.nq,
-                                                       g.P2, g.L, g.p, g.B, g.nalm, ngroups, nitems, T(2), true);
+                                                       g.P2, g.L, g.p, g.B, g.nalm, ngroups, nitems, wpos, true);
     }
     {
         const int nmp = g.L / 2 + 1;
@@ -480,7 +480,7 @@ void launch_sh_synthesis(const hpx_plan_s* P, const T* alm, T* maps, cudaStream_
 template void launch_sh_synthesis<float>(const hpx_plan_s*, const float*, float*, cudaStream_t);
 template void launch_sh_synthesis<double>(const hpx_plan_s*, const double*, double*, cudaStream_t);
 
-template void launch_adjoint<float>(const hpx_plan_s*, const float*, float*, cudaStream_t);
-template void launch_adjoint<double>(const hpx_plan_s*, const double*, double*, cudaStream_t);
+template void launch_adjoint<float>(const hpx_plan_s*, const float*, float*, cudaStream_t, float);
+template void launch_adjoint<double>(const hpx_plan_s*, const double*, double*, cudaStream_t, double);
 
 }  // namespace hpx

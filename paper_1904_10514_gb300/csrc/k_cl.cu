@@ -71,6 +71,46 @@ void launch_cl(const hpx_plan_s* P, const T* alm, double* cl, cudaStream_t s) {
     cl_kernel<T><<<grid, 32 * kSlices, 0, s>>>((const cplx<T>*)alm, cl, g.L, g.nalm);
 }
 
+// Vector-Jacobian product of Eq. (APS): for a loss L(C) with g_l = dL/dC_l, the
+// gradient with respect to the packed coefficients (torch's convention for a
+// complex input: dL/dRe a + i dL/dIm a) is
+//     dL/da_lm = g_l 2 w_m a_lm / (2l + 1),   w_0 = 1, w_m = 2 (m > 0).
+// One block per (order m, map b); the threads run over the degrees l = m..L_b.
+// Maps are located through almoff / cloff (element offsets of map b's
+// coefficients and spectrum) and lmax[b], so concatenated uneven batches work
+// in place; a map with m > L_b has nothing to do for this block.
+template <class T>
+__global__ void __launch_bounds__(256) cl_vjp_kernel(const cplx<T>* __restrict__ alm, const double* __restrict__ gcl,
+                                                     cplx<T>* __restrict__ galm, const int64_t* __restrict__ almoff,
+                                                     const int64_t* __restrict__ cloff, const int* __restrict__ lmax,
+                                                     int Lu, int64_t nalm_u) {
+    const int m = blockIdx.x, b = blockIdx.y;
+    const int L = lmax ? lmax[b] : Lu;
+    if (m > L) return;
+    const int64_t ao = almoff ? almoff[b] : (int64_t)b * nalm_u;
+    const int64_t co = cloff ? cloff[b] : (int64_t)b * (Lu + 1);
+    const int64_t i0 = ao + (int64_t)m * (2 * L + 1 - m) / 2;
+    const double w = m == 0 ? 2.0 : 4.0;
+    for (int l = m + threadIdx.x; l <= L; l += blockDim.x) {
+        const T f = (T)(gcl[co + l] * w / (2.0 * l + 1.0));
+        const cplx<T> a = alm[i0 + l];
+        galm[i0 + l] = mk<T>(f * a.r, f * a.i);
+    }
+}
+
+template <class T>
+void launch_cl_vjp(const T* alm, const double* gcl, T* galm, const int64_t* almoff, const int64_t* cloff,
+                   const int* lmax, int Lmax_all, int B, int Lu, int64_t nalm_u, cudaStream_t s) {
+    dim3 grid(Lmax_all + 1, B);
+    cl_vjp_kernel<T><<<grid, 256, 0, s>>>((const cplx<T>*)alm, gcl, (cplx<T>*)galm, almoff, cloff, lmax, Lu,
+                                          nalm_u);
+}
+
+template void launch_cl_vjp<float>(const float*, const double*, float*, const int64_t*, const int64_t*, const int*,
+                                   int, int, int, int64_t, cudaStream_t);
+template void launch_cl_vjp<double>(const double*, const double*, double*, const int64_t*, const int64_t*,
+                                    const int*, int, int, int, int64_t, cudaStream_t);
+
 template <class T>
 __global__ void finite_check_kernel(const T* __restrict__ x, int64_t n, int* __restrict__ status) {
     bool bad = false;

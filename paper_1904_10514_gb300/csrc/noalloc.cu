@@ -20,6 +20,7 @@
 
 #include <cstring>
 #include <mutex>
+#include <new>
 #include <vector>
 
 #include "../../include/hpx.h"
@@ -99,23 +100,34 @@ extern "C" int hpx_analyze_noalloc(int nside, int lmax, const float* maps, float
     cudaStream_t s = (cudaStream_t)stream;
 
     if (st.nside != nside || st.lmax != L) {
+        // A rebuild copies on the stream and waits for it: not possible while the
+        // stream is being captured (the copy would invalidate the caller's capture).
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) return fail(HPX_ERR_CUDA);
+        if (cs != cudaStreamCaptureStatusNone) return fail(HPX_ERR_STATE);
         // Tables for this size: FP64 on the host, rounded to FP32, packed in the
         // order they take in the device array, followed by the workspace.
         hpx::PlanTables tb;
-        if (!hpx::build_tables(nside, L, false, tb).empty()) return fail(HPX_ERR_ARG);
         Image img;
         Offsets o;
-        o.nphi = img.vec(tb.nphi); o.startN = img.vec(tb.startN); o.startS = img.vec(tb.startS);
-        o.pow2 = img.vec(tb.pow2); o.logn = img.vec(tb.logn); o.fftL = img.vec(tb.fftL); o.logL = img.vec(tb.logL);
-        o.shOff = img.vec(tb.shOff); o.chOff = img.vec(tb.chOff); o.bhOff = img.vec(tb.bhOff);
-        o.shift = img.real(tb.shift); o.chirp = img.real(tb.chirp); o.bhat = img.real(tb.bhat);
-        o.twid = img.real(tb.twid);
-        o.poleN = img.vec(tb.poleN); o.poleS = img.vec(tb.poleS); o.polew = img.vec(tb.polew);
-        o.npole = (int)tb.polew.size();
-        o.rowptr = img.vec(tb.rowptr); o.ent = img.vec(tb.ent); o.entw = img.real(tb.entw);
-        o.dec = img.real(tb.dec); o.D = img.real(tb.D); o.angOff = img.vec(tb.angOff); o.ang = img.real(tb.ang);
-        o.skOff = img.vec(tb.skOff); o.skew = img.real(tb.skew); st.nq = tb.nq;
-        o.nstart = img.vec(tb.nstart); o.swts = img.real(tb.swts); st.spreadE = tb.spreadE;
+        try {
+            if (!hpx::build_tables(nside, L, false, tb).empty()) return fail(HPX_ERR_ARG);
+            o.nphi = img.vec(tb.nphi); o.startN = img.vec(tb.startN); o.startS = img.vec(tb.startS);
+            o.pow2 = img.vec(tb.pow2); o.logn = img.vec(tb.logn); o.fftL = img.vec(tb.fftL); o.logL = img.vec(tb.logL);
+            o.shOff = img.vec(tb.shOff); o.chOff = img.vec(tb.chOff); o.bhOff = img.vec(tb.bhOff);
+            o.shift = img.real(tb.shift); o.chirp = img.real(tb.chirp); o.bhat = img.real(tb.bhat);
+            o.twid = img.real(tb.twid);
+            o.poleN = img.vec(tb.poleN); o.poleS = img.vec(tb.poleS); o.polew = img.vec(tb.polew);
+            o.npole = (int)tb.polew.size();
+            o.rowptr = img.vec(tb.rowptr); o.ent = img.vec(tb.ent); o.entw = img.real(tb.entw);
+            o.dec = img.real(tb.dec); o.D = img.real(tb.D); o.angOff = img.vec(tb.angOff); o.ang = img.real(tb.ang);
+            o.skOff = img.vec(tb.skOff); o.skew = img.real(tb.skew); st.nq = tb.nq;
+            o.nstart = img.vec(tb.nstart); o.swts = img.real(tb.swts); st.spreadE = tb.spreadE;
+        } catch (const std::bad_alloc&) {   // no exception leaves the C interface
+            return fail(HPX_ERR_OOM);
+        } catch (...) {
+            return fail(HPX_ERR_ARG);
+        }
         const size_t ySize = (size_t)tb.Q * (tb.p + 1) * 8;    // step-1 coefficients (complex FP32)
         const size_t bSize = (size_t)(tb.p + 1) * 2 * tb.P2 * 8;
         o.Y = align256(img.bytes.size());

@@ -110,6 +110,9 @@ struct hpx_plan_s {
     int64_t* d_mapoff = nullptr;             // byte offset of map i in the caller's arrays
     int64_t* d_almoff = nullptr;
     int64_t* d_cloff = nullptr;
+    int64_t* d_almel = nullptr;              // element offsets of map i's coefficients / spectrum
+    int64_t* d_clel = nullptr;
+    int* d_lmax = nullptr;                   // lmax of map i
     std::vector<void*> stage_maps, stage_alm, stage_cl;   // per sub-plan staging (gathered runs)
     int64_t total_npix = 0, total_nalm = 0, total_ncl = 0;
 
@@ -151,7 +154,9 @@ template <class T> void launch_synth_apply(const hpx_plan_s* P, const T* alm, cu
 __host__ __device__ inline int64_t tc_elem(int rp, int r, int k) {
     return (int64_t)(k >> 5) * rp * 32 + (r >> 3) * 256 + ((k & 31) >> 2) * 32 + (r & 7) * 4 + (k & 3);
 }
-template <class T> void launch_adjoint(const hpx_plan_s* P, const T* alm, T* maps, cudaStream_t s);
+// transpose of the analysis; wpos = weight of the m > 0 coefficients (2: the
+// adjoint under the real-map inner product, 1: under the plain Euclidean one)
+template <class T> void launch_adjoint(const hpx_plan_s* P, const T* alm, T* maps, cudaStream_t s, T wpos = T(2));
 template <class T> void launch_sh_synthesis(const hpx_plan_s* P, const T* alm, T* maps, cudaStream_t s);
 int group_sh_synthesis(hpx_plan_s* P, const void* alm, void* maps);
 // uneven batches (group.cu)
@@ -159,7 +164,13 @@ hpx_plan_s* group_create(const hpx_plan_desc* d, int* err);
 int group_analyze(hpx_plan_s* P, const void* maps, void* alm);
 int group_synthesize(hpx_plan_s* P, const void* alm, void* maps);
 int group_cl(hpx_plan_s* P, const void* alm, double* cl);
+int group_analyze_vjp(hpx_plan_s* P, const void* galm, void* gmaps);
 void group_free(hpx_plan_s* P);
 template <class T> void launch_cl(const hpx_plan_s* P, const T* alm, double* cl, cudaStream_t s);
+// dL/da of Eq. (APS) for gcl = dL/dC (k_cl.cu); almoff / cloff / lmax: per-map
+// element offsets and degrees (NULL for a uniform batch: b nalm_u, b (Lu + 1), Lu)
+template <class T>
+void launch_cl_vjp(const T* alm, const double* gcl, T* galm, const int64_t* almoff, const int64_t* cloff,
+                   const int* lmax, int Lmax_all, int B, int Lu, int64_t nalm_u, cudaStream_t s);
 
 }  // namespace hpx

@@ -40,17 +40,38 @@ def per_l_error(a, ref, lmax, floor=1e-6):
     return e
 
 
-def sampled_per_l_error(cols_gpu, cols_ref, ref_norm_l, lmax):
+def sampled_per_l_errors(cols_gpu, cols_ref, ref_norm_l, lmax):
     """Estimate of e_l from a sample of orders: cols_* = {m: (lmax-m+1,)},
     ref_norm_l = ||a_l|| of the input sky (from the seeded generator).
-    Returns the max over l of sqrt(mean_m |da_lm|^2 * (2l+1)) / ref_norm_l."""
-    worst = 0.0
+    Returns sqrt(mean_m |da_lm|^2 * (2l+1)) / ref_norm_l per degree (0 where no
+    sampled order reaches l or the sky has no power there)."""
+    out = np.zeros(lmax + 1)
     for l in range(lmax + 1):
         if ref_norm_l[l] <= 0:
             continue
         ds = [abs(cols_gpu[m][l - m] - cols_ref[m][l - m]) ** 2 for m in cols_ref if m <= l]
         if not ds:
             continue
-        est = np.sqrt(np.mean(ds) * (2 * l + 1)) / ref_norm_l[l]
-        worst = max(worst, est)
-    return worst
+        out[l] = np.sqrt(np.mean(ds) * (2 * l + 1)) / ref_norm_l[l]
+    return out
+
+
+def sampled_per_l_error(cols_gpu, cols_ref, ref_norm_l, lmax):
+    """The largest per-degree estimate of sampled_per_l_errors."""
+    return float(sampled_per_l_errors(cols_gpu, cols_ref, ref_norm_l, lmax).max())
+
+
+def ring_perm(nside, quarter):
+    """Pixel permutation of a quarter turn (lambda -> lambda + pi/2: every ring
+    shifts by nphi/4 pixels) or of the north-south mirror."""
+    from oracle import geometry
+    rings = geometry.ring_table(nside)
+    perm = np.empty(geometry.npix(nside), dtype=np.int64)
+    R = len(rings)
+    for i, r in enumerate(rings):
+        k = np.arange(r["nphi"])
+        if quarter:
+            perm[r["start"] + k] = r["start"] + (k + r["nphi"] // 4) % r["nphi"]
+        else:
+            perm[r["start"] + k] = rings[R - 1 - i]["start"] + k
+    return perm

@@ -53,3 +53,13 @@ def test_fallback_peak_without_measurements():
     work = bench.stage_work(64, 128, 8)
     roof, _ = bench.roofline_report(work, {"spread": 1.0, "lat_fft": 0.5}, {})
     assert roof["peak_source"] == "fallback" and roof["peak"] == 6800.0
+
+
+def test_cpu_cost_model_separates_fixed_and_per_order_time():
+    """The oracle's time for n orders is fixed + n * per_order; two sample sizes
+    recover both, and the full map is fixed + 2049 * per_order (not the small
+    sample's time scaled by 2049 / n, which counts the fixed part 2049 / n times)."""
+    fixed, per = bench.fit_cost_model(2, 7.0 + 2 * 0.5, 16, 7.0 + 16 * 0.5)
+    assert abs(fixed - 7.0) < 1e-12 and abs(per - 0.5) < 1e-12
+    assert abs(bench.full_map_seconds(fixed, per) - (7.0 + 2049 * 0.5)) < 1e-9
+    assert abs(bench.cpu_gpix(100.0) - 12 * 1024 * 1024 / 100.0 / 1e9) < 1e-18

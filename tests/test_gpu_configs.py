@@ -1,15 +1,16 @@
 """The remaining workload configurations at their full sizes, through the C ABI:
 64 maps at Nside 512 (two 32-map column tiles of the tensor-core kernel), an
 uneven batch of 200 maps with Nside drawn from {64, ..., 1024} replayed as one
-CUDA graph, and 8 maps at Nside 2048 (checked through properties that hold at
-any size, since the oracle's dense least squares at that size takes too long)."""
+CUDA graph, and 8 maps at Nside 2048 (the run-time Givens sweeps): against the
+oracle on a sample of orders, through a full-size dot test of the adjoint and
+the gradient of a C_l loss, and through properties that hold at any size."""
 
 import numpy as np
 import pytest
 
 import skies
-from helpers import per_l_error, per_l_norms, sampled_per_l_error
-from oracle import geometry, hp2sph
+from helpers import per_l_error, per_l_norms, ring_perm, sampled_per_l_error
+from oracle import dense, geometry, hp2sph
 from oracle.legendre import pbar_table
 
 torch = pytest.importorskip("torch")
@@ -91,21 +92,6 @@ def test_uneven_200_maps_graph(hp):
     assert seen == {64, 128, 256, 512, 1024}
 
 
-def _ring_perm(nside, quarter):
-    """Pixel permutation of a quarter turn (lambda -> lambda + pi/2: every ring
-    shifts by nphi/4 pixels) or of the north-south mirror."""
-    rings = geometry.ring_table(nside)
-    perm = np.empty(geometry.npix(nside), dtype=np.int64)
-    R = len(rings)
-    for i, r in enumerate(rings):
-        k = np.arange(r["nphi"])
-        if quarter:
-            perm[r["start"] + k] = r["start"] + (k + r["nphi"] // 4) % r["nphi"]
-        else:
-            perm[r["start"] + k] = rings[R - 1 - i]["start"] + k
-    return perm
-
-
 @pytest.mark.slow
 def test_nside2048_properties(hp):
     """8 FP32 maps at Nside 2048, lmax 4096 (the plan takes the sweeps: the
@@ -123,7 +109,7 @@ def test_nside2048_properties(hp):
     l = np.concatenate([np.arange(mm, L + 1) for mm in range(L + 1)])
     scale = np.sqrt(np.mean(np.abs(a0[:2]) ** 2))
     for quarter, factor in ((True, np.exp(0.5j * np.pi * m)), (False, (-1.0) ** (l + m))):
-        perm = _ring_perm(ns, quarter)
+        perm = ring_perm(ns, quarter)
         g = f[:2][:, perm]
         a1 = plan.analyze(torch.as_tensor(np.ascontiguousarray(np.concatenate([g, f[2:]])), device="cuda"))
         a1 = a1.cpu().numpy().astype(np.complex128)[:2]
@@ -150,3 +136,79 @@ def test_nside2048_properties(hp):
     a2 = plan.analyze(torch.as_tensor(batch, device="cuda")).cpu().numpy().astype(np.complex128)[0]
     e = per_l_error(a2, coef, L)
     assert e.max() < TOL, (e.max(), int(np.argmax(e)))
+
+
+@pytest.mark.slow
+def test_nside2048_workload_oracle_adjoint_gradient(hp):
+    """The differentiation workload: 8 FP32 maps at Nside 2048, lmax 4096 (the plan
+    runs the Givens sweeps per call).  Maps 0 and 7 are the workload's seeded
+    power-law skies; maps 1-6 are quarter turns and north-south mirrors of them
+    (the same spectra, without synthesising six more 50M-pixel skies).
+    (1) Maps 0 and 7 against the oracle on 12 orders spread over 0..L plus the
+        edge orders 0, 1, 2, L-1, L (per-degree estimate and element checks).
+    (2) Full-size dot test <A f, a> = <f, A^T a> of hpx_synthesize.
+    (3) One backward() of the loss sum_l w_l (C_l - C*_l)^2 (w_l = 1/l, l >= 2,
+        C*_l a seeded power law): its directional derivative along a random map d
+        equals the one computed from the forward analysis of d."""
+    ns, L, B = 2048, 4096, 8
+    m0, a0 = skies.workload_maps("w5_nside2048x8", nmaps=1, first=0, dtype=np.float32, return_alm=True)
+    m7, a7 = skies.workload_maps("w5_nside2048x8", nmaps=1, first=7, dtype=np.float32, return_alm=True)
+    q, mir = ring_perm(ns, True), ring_perm(ns, False)
+    maps = np.stack([m0[0], m0[0][q], m0[0][mir], m0[0][q][q], m7[0][q], m7[0][mir], m7[0][q][mir], m7[0]])
+    plan = hp.Plan(ns, L, B, "fp32")
+    assert plan.flags & hp.HPX_FLAG_SWEEPS
+    x = torch.as_tensor(maps, device="cuda")
+    a = plan.analyze(x)
+    plan.sync()
+    a_np = a.cpu().numpy().astype(np.complex128)
+
+    # (1) oracle on sampled orders
+    strat = [int((k + 0.5) * (L + 1) / 12) for k in range(12)]
+    low = [0, 1, 2, L - 1, L]
+    ref = hp2sph.analyze_columns(np.stack([m0[0], m7[0]]).astype(np.float64), ns, L, strat + low)
+    for k, (b, alms) in enumerate(((0, a0[0]), (7, a7[0]))):
+        got = {m: a_np[b][hp2sph.alm_index(m, m, L):hp2sph.alm_index(m, m, L) + L - m + 1] for m in strat + low}
+        norms = per_l_norms(alms, L)
+        err = sampled_per_l_error({m: got[m] for m in strat}, {m: ref[m][k] for m in strat}, norms, L)
+        assert err < TOL, (b, err)
+        for m in low:
+            l = np.arange(max(m, 2), L + 1)
+            d = np.abs(got[m][l - m] - ref[m][k][l - m]) / norms[l]
+            assert d.max() < TOL, (b, m, d.max())
+
+    # (2) full-size dot test of the adjoint
+    rng = np.random.default_rng(2049)
+    coef = (rng.standard_normal((B, plan.nalm)) + 1j * rng.standard_normal((B, plan.nalm))).astype(np.complex64)
+    Ata = plan.synthesize(torch.as_tensor(coef, device="cuda")).cpu().numpy().astype(np.float64)
+    plan.sync()
+    for b in (0, 7):
+        lhs = dense.alm_dot(a_np[b], coef[b].astype(np.complex128), L)
+        rhs = float(np.dot(maps[b].astype(np.float64), Ata[b]))
+        assert abs(lhs - rhs) <= 2e-5 * np.linalg.norm(maps[b]) * np.linalg.norm(Ata[b]), (b, lhs, rhs)
+
+    # (3) gradient of a C_l loss through autograd (hpx_cl_vjp, hpx_analyze_vjp)
+    w = np.zeros(L + 1)
+    w[2:] = 1.0 / np.arange(2, L + 1)
+    cstar = skies.power_law(L, 2.0) * rng.uniform(0.5, 1.5, L + 1)
+    wl, cs = torch.as_tensor(w, device="cuda"), torch.as_tensor(cstar, device="cuda")
+    xg = x.clone().requires_grad_(True)
+    c = hp.cl(hp.analyze(xg, plan), plan)
+    loss = torch.sum(wl * (c - cs) ** 2)
+    loss.backward()
+    g = xg.grad.detach().double()
+    d = torch.as_tensor(rng.standard_normal(maps.shape).astype(np.float32), device="cuda")
+    ad = plan.analyze(d).cpu().numpy().astype(np.complex128)
+    cl_np = c.detach().cpu().numpy()
+    m_idx = np.concatenate([np.full(L - mm + 1, mm) for mm in range(L + 1)])
+    l_idx = np.concatenate([np.arange(mm, L + 1) for mm in range(L + 1)])
+    wm = np.where(m_idx == 0, 1.0, 2.0)
+    expect, size = 0.0, 0.0
+    for b in range(B):
+        dcl = np.bincount(l_idx, weights=wm * 2.0 * np.real(np.conj(a_np[b]) * ad[b]), minlength=L + 1)
+        dcl /= 2.0 * np.arange(L + 1) + 1.0
+        terms = 2.0 * w * (cl_np[b] - cstar) * dcl
+        expect += float(np.sum(terms))
+        size += float(np.sum(np.abs(terms)))
+    got = float(torch.sum(g * d.double()).item())
+    # FP32 products: the tolerance is relative to the sum of the terms' magnitudes
+    assert abs(got - expect) <= 1e-4 * size, (got, expect, size)

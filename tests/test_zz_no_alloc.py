@@ -52,7 +52,9 @@ def _noalloc(hp, maps, nside, lmax):
 
 
 def test_noalloc_matches_plan_two_calls_in_a_row(hp):
-    calls = [(16, -1, 1), (16, -1, 2), (64, 100, 3), (64, 100, 4)]   # two pairs of consecutive calls
+    # pairs of consecutive calls of one size, up to the largest size the array takes
+    calls = [(16, -1, 1), (16, -1, 2), (64, 100, 3), (64, 100, 4), (128, -1, 5), (128, -1, 6),
+             (128, 200, 7), (128, 200, 8)]
     for nside, lmax, seed in calls:
         maps, _ = skies.small_powerlaw_maps(nside, 1, seed=seed, alpha=2.0, noise=1e-3)
         m32 = maps[0].astype(np.float32)
