@@ -102,6 +102,8 @@ def stage_work(ns, L, B, es=8):
         "spread": ("hbm", B * (L + 1) * (Q * es + (4 * ns + 1) * es)),
         # grid FFT: read U, write the right-hand sides
         "lat_fft": ("hbm", B * (L + 1) * ((4 * ns + 1) * es + 2 * P2 * es)),
+        # spreading and grid FFT in one kernel: read the L+1 used columns of Y, write the right-hand sides
+        "nufft": ("hbm", B * (L + 1) * (Q * es + 2 * P2 * es)),
         "lat_solve": ("alu", B * dense),
         "rot_sweep": ("alu", B * rotation_count(L) * 12),
         # per-order operators on the tensor cores: read M (n_alm x P2 entries of 4 bytes, an FP16
@@ -278,6 +280,8 @@ def main():
                     help="time only the device-resident step (for profiler runs): no e2e, FP64 or CPU legs")
     ap.add_argument("--nside", type=int, default=NSIDE, help="smaller cases for profiler captures")
     ap.add_argument("--batch", type=int, default=BATCH)
+    ap.add_argument("--sweeps", action="store_true",
+                    help="with --kernels-only: the run-time Givens sweeps instead of the per-order operators")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -309,7 +313,7 @@ def main():
     else:
         maps_np = skies.small_powerlaw_maps(ns, nb, seed=6000 + rank, alpha=2.0, noise=1e-3)[0].astype(np.float32)
     t_plan0 = time.perf_counter()
-    plan = hp.Plan(ns, 2 * ns, nb, "fp32")
+    plan = hp.Plan(ns, 2 * ns, nb, "fp32", sweeps=args.sweeps and args.kernels_only)
     torch.cuda.synchronize()
     plan_build_s = time.perf_counter() - t_plan0
     maps = torch.from_numpy(maps_np).cuda()
@@ -438,13 +442,18 @@ def main():
         plan_syn.sh_synthesis(alm, out=maps_syn)
     torch.cuda.synchronize()
     nsyn = max(2, min(args.steps, 5))
+    hp.hpx_set_profiling(plan_syn.handle, 1)
     e0.record(stream)
     for _ in range(nsyn):
         plan_syn.sh_synthesis(alm, out=maps_syn)
     e1.record(stream)
     torch.cuda.synchronize()
+    syn_ms, syn_calls = hp.hpx_stage_times(plan_syn.handle)
+    hp.hpx_set_profiling(plan_syn.handle, 0)
     t_syn = e0.elapsed_time(e1) / nsyn / 1e3
     synthesis = {"value": npix_step / t_syn / 1e9, "unit": "Gpix/s", "ms_per_step": t_syn * 1e3,
+                 "stages_ms_per_launch": {n: syn_ms[k] / max(syn_calls, 1)
+                                          for k, n in enumerate(hp.STAGES_SYNTH) if n != "unused"},
                  "plan_build_s": syn_build_s,
                  "path": "per-order synthesis operators" if plan_syn.flags & hp.HPX_FLAG_SWEEPS == 0 else "sweeps"}
     plan_syn.close()
@@ -526,8 +535,7 @@ def main():
 
     # roofline of the dominant kernel (and of every stage)
     work = stage_work(NSIDE, LMAX, BATCH)
-    names = [n for n in plan.stages if n != "unused"]
-    per_launch = {n: stage_ms[k] / max(ncalls, 1) for k, n in enumerate(names)}
+    per_launch = {n: stage_ms[k] / max(ncalls, 1) for k, n in enumerate(plan.stages) if n != "unused"}
     peaks = json.load(open(MEASURED)) if os.path.exists(MEASURED) else {}
     roof, per_stage = roofline_report(work, per_launch, peaks)
 

@@ -101,6 +101,12 @@ extern "C" {
  *   (FP32) or 1e-14 (FP64). */
 #define HPX_FLAG_CG 64u
 
+/* Information bit of hpx_plan_flags (not a request): the plan's analysis runs
+ * the latitude NUFFT's spreading and grid FFT as one kernel (FP32 plans whose
+ * grid has 4096..16384 points); its stage 2 then holds both and stage 3 is
+ * empty (hpx_stage_times). */
+#define HPX_INFO_NUFFT_FUSED (1u << 16)
+
 typedef struct hpx_plan_s hpx_plan_s;
 
 typedef struct hpx_plan_desc {
@@ -213,9 +219,13 @@ int hpx_plan_launches(const hpx_plan_s* plan);
 
 /* Stage timing for profiling.  With profiling enabled (enable = 1) every
  * hpx_analyze records CUDA events on the plan's stream around each of its
- * kernels (ring FFT, poles, NUFFT spreading, NUFFT grid FFT, then either the
+ * kernels (ring FFT, poles, NUFFT spreading (with HPX_INFO_NUFFT_FUSED: the
+ * whole NUFFT), NUFFT grid FFT (then empty), then either the
  * per-order operators and an empty stage, or with HPX_FLAG_SWEEPS the latitude
- * operator D and the rotation sweeps; up to 256 calls are kept).  hpx_stage_times waits for those events, writes
+ * operator D and the rotation sweeps; up to 256 calls are kept), and every
+ * hpx_sh_synthesis around its three stages (the order-m to latitude-Fourier
+ * conversion, the type-2 NUFFT, the ring folding and inverse FFTs; the other
+ * three stages empty).  hpx_stage_times waits for those events, writes
  * the summed device time of each stage in milliseconds to ms[0..n-1]
  * (n >= HPX_NSTAGES), sets *ncalls to the number of calls summed, and clears
  * the record. */

@@ -89,9 +89,11 @@ int analyze_impl(hpx_plan_s* P, const void* maps, void* alm) {
     if (ev) cudaEventRecord(ev[1], s);
     hpx::launch_poles<T>(P, (const T*)maps, s);
     if (ev) cudaEventRecord(ev[2], s);
-    hpx::launch_spread<T>(P, s);
+    const bool fusedNufft = hpx::nufft_fused(P);
+    if (fusedNufft) hpx::launch_nufft_fused(P, s);   // spreading and grid FFT in one kernel
+    else hpx::launch_spread<T>(P, s);
     if (ev) cudaEventRecord(ev[3], s);
-    hpx::launch_lat_fft<T>(P, s);
+    if (!fusedNufft) hpx::launch_lat_fft<T>(P, s);
     if (ev) cudaEventRecord(ev[4], s);
     if (P->fusedM) {
         if constexpr (sizeof(T) == 4) {
@@ -193,22 +195,29 @@ hpx_plan_s* hpx_plan_ex(const hpx_plan_desc* d) {
     t.twid = up.real(tb.twid, fp64);
     t.poleN = up.vec(tb.poleN); t.poleS = up.vec(tb.poleS); t.polew = up.vec(tb.polew);
     t.npole = (int)tb.polew.size();
-    {   // ring pairs grouped by transform length, longest first
-        std::vector<std::pair<int, int>> byN;
-        for (int i = 0; i < tb.npairs; ++i) byN.push_back({tb.pow2[i] ? tb.nphi[i] : tb.fftL[i], i});
-        std::stable_sort(byN.begin(), byN.end(), [](const std::pair<int, int>& a, const std::pair<int, int>& b) {
-            return a.first > b.first;
+    {   // ring pairs grouped by transform length (longest first), and from
+        // kRingCtMin points up also by kind (plain rings, then Bluestein rings)
+        struct Key {
+            int N, blue, i;
+        };
+        std::vector<Key> byN;
+        for (int i = 0; i < tb.npairs; ++i)
+            byN.push_back({tb.pow2[i] ? tb.nphi[i] : tb.fftL[i], tb.pow2[i] ? 0 : 1, i});
+        std::stable_sort(byN.begin(), byN.end(), [](const Key& a, const Key& b) {
+            if (a.N != b.N) return a.N > b.N;
+            return a.N >= hpx::kRingCtMin && a.blue < b.blue;
         });
         std::vector<int> list;
         for (size_t k = 0; k < byN.size(); ++k) {
             // transforms of kRingMergeN points or fewer share one launch, with
             // blocks sized for the longest of them: alone, each of these short
             // launches is bound by its latency, not by its work
-            const bool merged = byN[k].first <= kRingMergeN && k > 0 && byN[k - 1].first <= kRingMergeN;
-            if (k == 0 || (byN[k].first != byN[k - 1].first && !merged))
-                P->ringClasses.push_back({byN[k].first, (int)k, 0});
+            const bool merged = byN[k].N <= kRingMergeN && k > 0 && byN[k - 1].N <= kRingMergeN;
+            const bool newkind = byN[k].N >= hpx::kRingCtMin && k > 0 && byN[k].blue != byN[k - 1].blue;
+            if (k == 0 || (byN[k].N != byN[k - 1].N && !merged) || newkind)
+                P->ringClasses.push_back({byN[k].N, (int)k, 0, byN[k].blue != 0});
             P->ringClasses.back().count++;
-            list.push_back(byN[k].second);
+            list.push_back(byN[k].i);
         }
         P->ringList = up.vec(list);
     }
@@ -218,6 +227,7 @@ hpx_plan_s* hpx_plan_ex(const hpx_plan_desc* d) {
     t.hstart = up.vec(tb.hstart); t.hwts = up.real(tb.hwts, fp64); t.spreadH = tb.spreadH;
     t.spreadRows = tb.spreadRows;
     t.spreadD = tb.spreadD;
+    t.spreadRowsC = tb.spreadRowsC;
     t.D = up.real(tb.D, fp64);
     if (d->flags & HPX_FLAG_CG) {
         std::vector<double> H;
@@ -535,8 +545,12 @@ int hpx_sh_synthesis(hpx_plan_s* P, const void* alm, void* maps) {
         hpx::launch_finite_check(alm, n, P->precision == HPX_FP64, P->d_status, P->stream);
     }
     if (P->group) return set_err(hpx::group_sh_synthesis(P, alm, maps));
-    if (P->precision == HPX_FP64) hpx::launch_sh_synthesis<double>(P, (const double*)alm, (double*)maps, P->stream);
-    else hpx::launch_sh_synthesis<float>(P, (const float*)alm, (float*)maps, P->stream);
+    cudaEvent_t* ev = nullptr;
+    if (P->prof && P->nprof < hpx_plan_s::kMaxProf) ev = P->ev + (size_t)P->nprof++ * (hpx_plan_s::kStages + 1);
+    if (P->precision == HPX_FP64)
+        hpx::launch_sh_synthesis<double>(P, (const double*)alm, (double*)maps, P->stream, ev);
+    else
+        hpx::launch_sh_synthesis<float>(P, (const float*)alm, (float*)maps, P->stream, ev);
     if (cudaGetLastError() != cudaSuccess) return set_err(HPX_ERR_CUDA);
     return set_err(HPX_OK);
 }
@@ -614,7 +628,12 @@ int64_t hpx_npix(const hpx_plan_s* P) { return P ? P->g.npix : 0; }
 int64_t hpx_nalm(const hpx_plan_s* P) { return P ? P->g.nalm : 0; }
 int hpx_plan_lmax(const hpx_plan_s* P) { return P ? P->g.L : -1; }
 int64_t hpx_plan_bytes(const hpx_plan_s* P) { return P ? P->bytes : 0; }
-int hpx_plan_flags(const hpx_plan_s* P) { return P ? (int)P->flags : -1; }
+int hpx_plan_flags(const hpx_plan_s* P) {
+    if (!P) return -1;
+    unsigned f = P->flags;
+    if (!P->group && hpx::nufft_fused(P)) f |= HPX_INFO_NUFFT_FUSED;
+    return (int)f;
+}
 
 int hpx_plan_launches(const hpx_plan_s* P) {
     if (!P) return -1;
@@ -625,7 +644,7 @@ int hpx_plan_launches(const hpx_plan_s* P) {
         return n;
     }
     int n = P->ringList ? (int)P->ringClasses.size() : 1;   // ring FFTs
-    n += 3;                                                 // poles, spreading, grid FFTs
+    n += hpx::nufft_fused(P) ? 2 : 3;                       // poles, spreading and grid FFTs
     if (P->flags & HPX_FLAG_CG) n += 1;                     // CG solves
     n += P->fusedM ? 1 : 2;                                 // operators, or D (or C) and the sweeps
     if (P->flags & HPX_FLAG_CHECKED) n += 1;

@@ -439,9 +439,10 @@ __global__ void __launch_bounds__(256) ring_synth_kernel(
 }
 
 template <class T>
-void launch_sh_synthesis(const hpx_plan_s* P, const T* alm, T* maps, cudaStream_t s) {
+void launch_sh_synthesis(const hpx_plan_s* P, const T* alm, T* maps, cudaStream_t s, cudaEvent_t* ev) {
     const auto& g = P->g;
     const auto& t = P->t;
+    if (ev) cudaEventRecord(ev[0], s);
     if (P->synM) {
         launch_synth_apply<T>(P, alm, s);   // the sweeps and Es composed per (m, c)
     } else {
@@ -456,6 +457,7 @@ void launch_sh_synthesis(const hpx_plan_s* P, const T* alm, T* maps, cudaStream_
         dense_adj_kernel<T><<<grid, 256, 0, s>>>((const T*)t.Es, (const cplx<T>*)P->beta, (cplx<T>*)P->bvec, g.P2,
                                                  g.p, g.L, g.B);
     }
+    if (ev) cudaEventRecord(ev[1], s);
     {
         int logM = 0;
         while ((1 << logM) < g.M) ++logM;
@@ -466,6 +468,7 @@ void launch_sh_synthesis(const hpx_plan_s* P, const T* alm, T* maps, cudaStream_
                                                     (const T*)t.nentw, (const T*)t.dec, (const cplx<T>*)t.twid,
                                                     g.Lmax, g.M, logM, g.p, g.Q, g.P2);
     }
+    if (ev) cudaEventRecord(ev[2], s);
     {
         const size_t smem = (size_t)g.smem_ring * sizeof(cplx<T>);
         cudaFuncSetAttribute(ring_synth_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -475,10 +478,12 @@ void launch_sh_synthesis(const hpx_plan_s* P, const T* alm, T* maps, cudaStream_
             t.chOff, t.bhOff, (const cplx<T>*)t.chirp, (const cplx<T>*)t.bhat, (const cplx<T>*)t.twid, g.Lmax, g.p,
             g.L, g.Q, g.npix, g.npairs);
     }
+    if (ev)
+        for (int k = 3; k <= hpx_plan_s::kStages; ++k) cudaEventRecord(ev[k], s);
 }
 
-template void launch_sh_synthesis<float>(const hpx_plan_s*, const float*, float*, cudaStream_t);
-template void launch_sh_synthesis<double>(const hpx_plan_s*, const double*, double*, cudaStream_t);
+template void launch_sh_synthesis<float>(const hpx_plan_s*, const float*, float*, cudaStream_t, cudaEvent_t*);
+template void launch_sh_synthesis<double>(const hpx_plan_s*, const double*, double*, cudaStream_t, cudaEvent_t*);
 
 template void launch_adjoint<float>(const hpx_plan_s*, const float*, float*, cudaStream_t, float);
 template void launch_adjoint<double>(const hpx_plan_s*, const double*, double*, cudaStream_t, double);

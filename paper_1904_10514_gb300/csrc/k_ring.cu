@@ -18,11 +18,72 @@
 // coefficients m = 0..p of latitude node r (r = ring index + 1).
 #include <algorithm>
 
+#include "fft_ct.cuh"
 #include "plan.h"
 
 namespace hpx {
 
 constexpr int kRingThreads = 512;
+
+// The same step for the launches of one transform length N = 2^LOGN >= 4096
+// whose ring pairs are all of one kind (BLUE: Bluestein rings of convolution
+// length N; else rings of N points): the FFT length, the thread count
+// (N / 16 or N / 32) and the pass structure are compile-time constants
+// (fft_ct.cuh), and the kind of ring is known, so neither transform carries
+// the other's code.
+template <class T, int LOGN, int NT, bool BLUE>
+__global__ void __launch_bounds__(NT, (LOGN <= 13 ? 1024 / NT : 1)) ring_ct_kernel(
+    const T* __restrict__ maps, cplx<T>* __restrict__ Y, const int* __restrict__ nphi_t,
+    const int* __restrict__ startN_t, const int* __restrict__ startS_t, const int64_t* __restrict__ shOff_t,
+    const int64_t* __restrict__ chOff_t, const int64_t* __restrict__ bhOff_t, const cplx<T>* __restrict__ shift,
+    const cplx<T>* __restrict__ chirp, const cplx<T>* __restrict__ bhat, const cplx<T>* __restrict__ tw, int twlen,
+    int p, int Q, int64_t npix, const int* __restrict__ ringlist) {
+    extern __shared__ unsigned char smem_raw[];
+    cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw);
+    const int i = ringlist[blockIdx.y];
+    const int b = blockIdx.x;
+    const int n = nphi_t[i];
+    const int sN = startN_t[i], sS = startS_t[i];
+    const bool equator = (sN == sS);
+    const T* f = maps + (int64_t)b * npix;
+    const int tid = threadIdx.x;
+    const int twstep = twlen >> LOGN;
+    auto sample = [&](int k) { return mk<T>(f[sN + k], equator ? T(0) : f[sS + k]); };
+    auto to_smem = [&](int, int pi, cplx<T> v) { buf[pi] = v; };
+    if constexpr (!BLUE) {
+        ct::fft<T, LOGN, NT, false, false>(buf, tw, twstep, [&](int k, int) { return sample(k); }, to_smem);
+    } else {
+        // Bluestein: chirped samples in, times the transformed kernel out; the
+        // inverse transform applies the output chirp in its last pass
+        const cplx<T>* ch = chirp + chOff_t[i];
+        const cplx<T>* bh = bhat + bhOff_t[i];
+        ct::fft<T, LOGN, NT, false, false>(
+            buf, tw, twstep, [&](int k, int) { return k < n ? mul(sample(k), ch[k]) : mk<T>(T(0), T(0)); },
+            [&](int j, int pi, cplx<T> v) { buf[pi] = mul(v, bh[j]); });
+        ct::fft<T, LOGN, NT, true, true>(
+            buf, tw, twstep, [&](int, int pi) { return buf[pi]; },
+            [&](int j, int pi, cplx<T> v) { buf[pi] = j < n ? mul(v, ch[j]) : v; });
+    }
+    const int h = n >> 1;
+    const cplx<T>* ph = shift + shOff_t[i];
+    cplx<T>* rowN = Y + ((int64_t)b * Q + (i + 1)) * (p + 1);
+    cplx<T>* rowS = Y + ((int64_t)b * Q + (Q - 2 - i)) * (p + 1);
+    for (int m = tid; m <= p; m += NT) {
+        cplx<T> cN = mk<T>(T(0), T(0)), cS = cN;
+        if (m <= h) {
+            const cplx<T> zm = buf[ct::padc(m)];
+            const cplx<T> zc = conjg(buf[ct::padc(m == 0 ? 0 : n - m)]);
+            const cplx<T> fn = scale(add(zm, zc), T(0.5));              // n * c~_m (north)
+            const cplx<T> d = sub(zm, zc);
+            const cplx<T> fs = mk<T>(T(0.5) * d.i, T(-0.5) * d.r);      // n * c~_m (south)
+            const cplx<T> w = ph[m];
+            cN = mul(fn, w);
+            cS = mul(fs, w);
+        }
+        rowN[m] = cN;
+        if (!equator) rowS[m] = cS;
+    }
+}
 
 template <class T, int E>
 __global__ void __launch_bounds__(kRingThreads, (E <= 16 ? 2 : 1)) ring_fft_kernel(
@@ -166,8 +227,33 @@ void launch_ring_fft(const hpx_plan_s* P, const T* maps, cudaStream_t s) {
         launch(g.smem_ring, g.npairs, nullptr);
         return;
     }
-    // one launch per transform length, blocks sized to it, longest first
-    for (const auto& c : P->ringClasses) launch(c.N, c.count, P->ringList + c.first);
+    // one launch per transform length (and kind, from 4096 points up), blocks
+    // sized to it, longest first
+    for (const auto& c : P->ringClasses) {
+        if (c.N < kRingCtMin) {
+            launch(c.N, c.count, P->ringList + c.first);
+            continue;
+        }
+        const size_t smem = (size_t)(c.N + c.N / 16) * sizeof(cplx<T>);
+        dim3 grid(g.B, c.count);
+        auto run = [&](auto kern, int threads) {
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            kern<<<grid, threads, smem, s>>>(maps, (cplx<T>*)P->Y, t.nphi, t.startN, t.startS, t.shOff, t.chOff,
+                                             t.bhOff, (const cplx<T>*)t.shift, (const cplx<T>*)t.chirp,
+                                             (const cplx<T>*)t.bhat, (const cplx<T>*)t.twid, g.Lmax, g.p, g.Q,
+                                             g.npix, P->ringList + c.first);
+        };
+        if (c.N == 4096) {
+            if (c.blue) run(ring_ct_kernel<T, 12, 256, true>, 256);
+            else run(ring_ct_kernel<T, 12, 256, false>, 256);
+        } else if (c.N == 8192) {
+            if (c.blue) run(ring_ct_kernel<T, 13, 512, true>, 512);
+            else run(ring_ct_kernel<T, 13, 512, false>, 512);
+        } else {
+            if (c.blue) run(ring_ct_kernel<T, 14, 512, true>, 512);
+            else run(ring_ct_kernel<T, 14, 512, false>, 512);
+        }
+    }
 }
 
 template <class T>

@@ -30,6 +30,63 @@
 
 namespace hpx {
 
+// Ring slots per warp of the staged form (sweep_pass_staged): copies run RB - 1
+// steps ahead of their use.
+constexpr int kRotRing = 8;
+
+// FP32: the same work with the angle rows and chain inputs staged through
+// shared memory ahead of use (sweep_pass_staged); every lane of a warp runs
+// the passes (lanes without a map neither load nor store chain values).
+template <int KMAX>
+__global__ void __launch_bounds__(64, 6) rot_staged_kernel(cplx<float>* __restrict__ beta2, cplx<float>* __restrict__ alm,
+                                                        const int64_t* __restrict__ skOff,
+                                                        const cplx<float>* __restrict__ skew, int nq, int P2, int L,
+                                                        int B, int64_t nalm, int ngroups, int nitems) {
+    constexpr int SL = SweepRing<kRotRing>::kSlot;
+    __shared__ __align__(16) cplx<float> rings[2][kRotRing * SL];
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp >= nitems) return;   // whole warps leave together (nitems counts warps)
+    cplx<float>* ring = rings[(threadIdx.x >> 5) & 1];
+    const int g = warp % ngroups;
+    const int c = (warp / ngroups) & 1;
+    const int m = L - warp / (2 * ngroups);
+    const int m0 = m & 1;
+    const int S = (m - m0) >> 1;
+    const int col = 32 * g + lane;
+    const bool live = col < B;
+    const int par = (m0 + c) & 1;
+    const int q0 = (m0 == 1 && c == 1) ? 1 : 0;
+    cplx<float>* chain = beta2 + (((int64_t)m * 2 + par) * P2 + q0) * B + (live ? col : 0);
+    const int64_t ldc = B;
+    int n = chain_len(m0, c, L);
+    int s0 = 0;
+    auto block = [&](int s) {
+        return skew + (skOff[(size_t)(m0 * 2 + c) * nq + (s >> 5)] + 2 * (s & 31)) * 32;
+    };
+    while (S - s0 >= KMAX && n > 0) {
+        sweep_pass_staged<float, KMAX, kRotRing>(chain, ldc, n, live, block(s0), s0 & 31, ring);
+        n -= KMAX;
+        s0 += KMAX;
+    }
+#define HPX_SUBPASS(KK)                                                                   \
+    if (KK < KMAX && S - s0 >= KK && n > 0) {                                             \
+        sweep_pass_staged<float, KK, kRotRing>(chain, ldc, n, live, block(s0), s0 & 31, ring); \
+        n -= KK;                                                                          \
+        s0 += KK;                                                                         \
+    }
+    HPX_SUBPASS(16)
+    HPX_SUBPASS(8)
+    HPX_SUBPASS(4)
+    HPX_SUBPASS(2)
+    HPX_SUBPASS(1)
+#undef HPX_SUBPASS
+    if (!live) return;
+    cplx<float>* out = alm + (int64_t)col * nalm;
+    const int64_t base = (int64_t)m * (2 * L + 1 - m) / 2 + m + c;
+    for (int i = 0; i < n; ++i) out[base + 2 * i] = chain[(int64_t)i * ldc];
+}
+
 template <class T, int KMAX>
 __global__ void __launch_bounds__(64) rot_kernel(cplx<T>* __restrict__ beta2, cplx<T>* __restrict__ alm,
                                                   const int64_t* __restrict__ skOff,
@@ -181,10 +238,15 @@ void launch_rot(const hpx_plan_s* P, T* alm, cudaStream_t s) {
         const int nitems = (g.L + 1) * 2 * ngroups;
         const int threads = 64;
         const int blocks = (nitems * 32 + threads - 1) / threads;
-        constexpr int KMAX = sizeof(T) == 4 ? 32 : 16;
-        rot_kernel<T, KMAX><<<blocks, threads, 0, s>>>((cplx<T>*)P->beta, (cplx<T>*)alm, P->t.skOff,
-                                                      (const cplx<T>*)P->t.skew, P->t.nq, g.P2, g.L, g.B,
-                                                      g.nalm, ngroups, nitems);
+        if constexpr (sizeof(T) == 4) {
+            rot_staged_kernel<32><<<blocks, threads, 0, s>>>((cplx<float>*)P->beta, (cplx<float>*)alm, P->t.skOff,
+                                                            (const cplx<float>*)P->t.skew, P->t.nq, g.P2, g.L,
+                                                            g.B, g.nalm, ngroups, nitems);
+        } else {
+            rot_kernel<T, 16><<<blocks, threads, 0, s>>>((cplx<T>*)P->beta, (cplx<T>*)alm, P->t.skOff,
+                                                        (const cplx<T>*)P->t.skew, P->t.nq, g.P2, g.L, g.B,
+                                                        g.nalm, ngroups, nitems);
+        }
         return;
     }
     const int nmax = g.L / 2 + 1;

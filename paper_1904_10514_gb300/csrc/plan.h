@@ -28,7 +28,7 @@ struct DevTables {
     int spreadE = 0;
     int* hstart = nullptr;                  // half-grid spreading with folded mirrors
     void* hwts = nullptr;                   // T [spreadH][M/2 + 1][2]
-    int spreadH = 0, spreadRows = 0, spreadD = 0;
+    int spreadH = 0, spreadRows = 0, spreadD = 0, spreadRowsC = 0;
     void* D = nullptr;                      // T [2][2][P2][P2]
     void* C = nullptr;                      // T [2][2][P2][P2]: change of basis alone (HPX_FLAG_CG)
     void* cgH = nullptr;                    // cplx<T> [4][2][cgN]: CG matrix-vector tables
@@ -70,6 +70,7 @@ struct hpx_plan_s {
     // Bluestein length): ring pairs ringList[first .. first + count - 1]
     struct RingClass {
         int N, first, count;
+        bool blue;   // N >= kRingCtMin: every ring of the class is a Bluestein ring (else none is)
     };
     std::vector<RingClass> ringClasses;
     int* ringList = nullptr;
@@ -128,11 +129,19 @@ struct hpx_plan_s {
 
 namespace hpx {
 
+// ring transforms of this many points or more run in launches of one length and
+// one kind (plain or Bluestein) with the compile-time FFT of fft_ct.cuh
+constexpr int kRingCtMin = 4096;
+
 template <class T> void launch_ring_fft(const hpx_plan_s* P, const T* maps, cudaStream_t s);
 template <class T> void launch_poles(const hpx_plan_s* P, const T* maps, cudaStream_t s);
 template <class T> void launch_nufft(const hpx_plan_s* P, cudaStream_t s);
 template <class T> void launch_spread(const hpx_plan_s* P, cudaStream_t s);
 template <class T> void launch_lat_fft(const hpx_plan_s* P, cudaStream_t s);
+// FP32 plans whose grid is 4096..16384 points: spreading and grid FFT in one
+// kernel (k_nufft.cu); launch_nufft_fused replaces launch_spread + launch_lat_fft
+bool nufft_fused(const hpx_plan_s* P);
+void launch_nufft_fused(const hpx_plan_s* P, cudaStream_t s);
 template <class T> void launch_dense(const hpx_plan_s* P, cudaStream_t s, const void* Dmat = nullptr);
 template <class T> void launch_cg(const hpx_plan_s* P, cudaStream_t s);
 template <class T> void launch_rot(const hpx_plan_s* P, T* alm, cudaStream_t s);
@@ -157,7 +166,9 @@ __host__ __device__ inline int64_t tc_elem(int rp, int r, int k) {
 // transpose of the analysis; wpos = weight of the m > 0 coefficients (2: the
 // adjoint under the real-map inner product, 1: under the plain Euclidean one)
 template <class T> void launch_adjoint(const hpx_plan_s* P, const T* alm, T* maps, cudaStream_t s, T wpos = T(2));
-template <class T> void launch_sh_synthesis(const hpx_plan_s* P, const T* alm, T* maps, cudaStream_t s);
+// ev: NULL, or kStages + 1 events recorded around its stages (profiling)
+template <class T>
+void launch_sh_synthesis(const hpx_plan_s* P, const T* alm, T* maps, cudaStream_t s, cudaEvent_t* ev = nullptr);
 int group_sh_synthesis(hpx_plan_s* P, const void* alm, void* maps);
 // uneven batches (group.cu)
 hpx_plan_s* group_create(const hpx_plan_desc* d, int* err);

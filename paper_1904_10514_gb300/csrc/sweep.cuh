@@ -53,4 +53,61 @@ __device__ __forceinline__ void sweep_pass(cplx<T>* chain, int64_t ldc, int n, c
     }
 }
 
+// The same pass for a whole warp whose lanes each own one column (live = the
+// lane has a column; every lane must call it, with the same n, A and coff),
+// with its memory traffic taken off the critical path: the skewed angle row
+// (32 complex, the same for all lanes) and each lane's input element of time
+// step t are brought into a per-warp ring of RB shared-memory slots by 8-byte
+// cp.async copies RB - 1 steps ahead of their use, so a step waits only for
+// shared-memory loads.  ring: RB x 64 complex of this warp's shared memory.
+template <int RB>
+struct SweepRing {
+    static constexpr int kSlot = 64;   // complex per slot: 32 angles + 32 lane inputs
+};
+
+template <class T, int K, int RB>
+__device__ __forceinline__ void sweep_pass_staged(cplx<T>* chain, int64_t ldc, int n, bool live,
+                                                  const cplx<T>* __restrict__ A, int coff, cplx<T>* ring) {
+    static_assert(sizeof(T) == 4, "staged sweeps: FP32 (8-byte complex copies)");
+    constexpr int SL = SweepRing<RB>::kSlot;
+    const int lane = threadIdx.x & 31;
+    cplx<T> carry[K], pipe[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) { carry[k] = mk<T>(T(0), T(0)); pipe[k] = carry[k]; }
+    const int steps = n + 2 * (K - 1);
+    const int nout = n - K;   // outputs of the last stage
+    auto issue = [&](int t) {
+        if (t < steps) {
+            cplx<T>* slot = ring + (t % RB) * SL;
+            cp_async8(slot + lane, A + (int64_t)t * 32 + lane, 8);
+            const bool have = live && t < n;
+            cp_async8(slot + 32 + lane, have ? chain + (int64_t)t * ldc : A, have ? 8 : 0);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+#pragma unroll
+    for (int q = 0; q < RB - 1; ++q) issue(q);
+    for (int t = 0; t < steps; ++t) {
+        __syncwarp();                 // every lane is done with the slot refilled next
+        issue(t + RB - 1);
+        asm volatile("cp.async.wait_group %0;" ::"n"(RB - 1) : "memory");
+        __syncwarp();                 // step t's copies of all lanes are visible
+        const cplx<T>* slot = ring + (t % RB) * SL;
+        const cplx<T> x0 = slot[32 + lane];
+        const cplx<T>* row = slot + coff;
+#pragma unroll
+        for (int k = K - 1; k >= 0; --k) {
+            const cplx<T> x = (k == 0) ? x0 : pipe[k - 1];
+            const cplx<T> cs = row[k];
+            const T c = cs.r, s = cs.i;
+            pipe[k] = mk<T>(c * carry[k].r + s * x.r, c * carry[k].i + s * x.i);
+            carry[k] = mk<T>(c * x.r - s * carry[k].r, c * x.i - s * carry[k].i);
+        }
+        const int j = t - 2 * K + 1;
+        if (live && j >= 0 && j < nout) chain[(int64_t)j * ldc] = pipe[K - 1];
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncwarp();
+}
+
 }  // namespace hpx
