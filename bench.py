@@ -102,8 +102,6 @@ def stage_work(ns, L, B, es=8):
         "spread": ("hbm", B * (L + 1) * (Q * es + (4 * ns + 1) * es)),
         # grid FFT: read U, write the right-hand sides
         "lat_fft": ("hbm", B * (L + 1) * ((4 * ns + 1) * es + 2 * P2 * es)),
-        # spreading and grid FFT in one kernel: read the L+1 used columns of Y, write the right-hand sides
-        "nufft": ("hbm", B * (L + 1) * (Q * es + 2 * P2 * es)),
         "lat_solve": ("alu", B * dense),
         "rot_sweep": ("alu", B * rotation_count(L) * 12),
         # per-order operators on the tensor cores: read M (n_alm x P2 entries of 4 bytes, an FP16

@@ -101,12 +101,6 @@ extern "C" {
  *   (FP32) or 1e-14 (FP64). */
 #define HPX_FLAG_CG 64u
 
-/* Information bit of hpx_plan_flags (not a request): the plan's analysis runs
- * the latitude NUFFT's spreading and grid FFT as one kernel (FP32 plans whose
- * grid has 4096..16384 points); its stage 2 then holds both and stage 3 is
- * empty (hpx_stage_times). */
-#define HPX_INFO_NUFFT_FUSED (1u << 16)
-
 typedef struct hpx_plan_s hpx_plan_s;
 
 typedef struct hpx_plan_desc {
@@ -219,8 +213,7 @@ int hpx_plan_launches(const hpx_plan_s* plan);
 
 /* Stage timing for profiling.  With profiling enabled (enable = 1) every
  * hpx_analyze records CUDA events on the plan's stream around each of its
- * kernels (ring FFT, poles, NUFFT spreading (with HPX_INFO_NUFFT_FUSED: the
- * whole NUFFT), NUFFT grid FFT (then empty), then either the
+ * kernels (ring FFT, poles, NUFFT spreading, NUFFT grid FFT, then either the
  * per-order operators and an empty stage, or with HPX_FLAG_SWEEPS the latitude
  * operator D and the rotation sweeps; up to 256 calls are kept), and every
  * hpx_sh_synthesis around its three stages (the order-m to latitude-Fourier

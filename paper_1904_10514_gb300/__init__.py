@@ -44,19 +44,15 @@ HPX_FLAG_CG = 64
 HPX_ERR_NONFINITE = -8
 HPX_NOALLOC_MAX_NSIDE = 128
 HPX_NSTAGES = 6
-HPX_INFO_NUFFT_FUSED = 1 << 16
-
-
 def stage_names(flags):
     """Names of the HPX_NSTAGES profiled stages of hpx_analyze for a plan's flags."""
-    fused = bool(flags & HPX_INFO_NUFFT_FUSED)
     sweeps = bool(flags & HPX_FLAG_SWEEPS)
-    return ["ring_fft", "poles", "nufft" if fused else "spread", "unused" if fused else "lat_fft",
+    return ["ring_fft", "poles", "spread", "lat_fft",
             "lat_solve" if sweeps else "fused_fsht", "rot_sweep" if sweeps else "unused"]
 
 
-STAGES = stage_names(HPX_FLAG_SWEEPS)   # HPX_FLAG_SWEEPS plans, two-kernel NUFFT
-STAGES_FUSED = stage_names(0)          # per-order operators, two-kernel NUFFT
+STAGES = stage_names(HPX_FLAG_SWEEPS)   # HPX_FLAG_SWEEPS plans
+STAGES_FUSED = stage_names(0)          # per-order operators
 STAGES_SYNTH = ["synth_fsht", "synth_nufft", "synth_rings", "unused", "unused", "unused"]   # hpx_sh_synthesis
 
 

@@ -89,11 +89,9 @@ int analyze_impl(hpx_plan_s* P, const void* maps, void* alm) {
     if (ev) cudaEventRecord(ev[1], s);
     hpx::launch_poles<T>(P, (const T*)maps, s);
     if (ev) cudaEventRecord(ev[2], s);
-    const bool fusedNufft = hpx::nufft_fused(P);
-    if (fusedNufft) hpx::launch_nufft_fused(P, s);   // spreading and grid FFT in one kernel
-    else hpx::launch_spread<T>(P, s);
+    hpx::launch_spread<T>(P, s);
     if (ev) cudaEventRecord(ev[3], s);
-    if (!fusedNufft) hpx::launch_lat_fft<T>(P, s);
+    hpx::launch_lat_fft<T>(P, s);
     if (ev) cudaEventRecord(ev[4], s);
     if (P->fusedM) {
         if constexpr (sizeof(T) == 4) {
@@ -227,7 +225,6 @@ hpx_plan_s* hpx_plan_ex(const hpx_plan_desc* d) {
     t.hstart = up.vec(tb.hstart); t.hwts = up.real(tb.hwts, fp64); t.spreadH = tb.spreadH;
     t.spreadRows = tb.spreadRows;
     t.spreadD = tb.spreadD;
-    t.spreadRowsC = tb.spreadRowsC;
     t.D = up.real(tb.D, fp64);
     if (d->flags & HPX_FLAG_CG) {
         std::vector<double> H;
@@ -628,12 +625,7 @@ int64_t hpx_npix(const hpx_plan_s* P) { return P ? P->g.npix : 0; }
 int64_t hpx_nalm(const hpx_plan_s* P) { return P ? P->g.nalm : 0; }
 int hpx_plan_lmax(const hpx_plan_s* P) { return P ? P->g.L : -1; }
 int64_t hpx_plan_bytes(const hpx_plan_s* P) { return P ? P->bytes : 0; }
-int hpx_plan_flags(const hpx_plan_s* P) {
-    if (!P) return -1;
-    unsigned f = P->flags;
-    if (!P->group && hpx::nufft_fused(P)) f |= HPX_INFO_NUFFT_FUSED;
-    return (int)f;
-}
+int hpx_plan_flags(const hpx_plan_s* P) { return P ? (int)P->flags : -1; }
 
 int hpx_plan_launches(const hpx_plan_s* P) {
     if (!P) return -1;
@@ -644,7 +636,7 @@ int hpx_plan_launches(const hpx_plan_s* P) {
         return n;
     }
     int n = P->ringList ? (int)P->ringClasses.size() : 1;   // ring FFTs
-    n += hpx::nufft_fused(P) ? 2 : 3;                       // poles, spreading and grid FFTs
+    n += 3;                                                 // poles, spreading, grid FFTs
     if (P->flags & HPX_FLAG_CG) n += 1;                     // CG solves
     n += P->fusedM ? 1 : 2;                                 // operators, or D (or C) and the sweeps
     if (P->flags & HPX_FLAG_CHECKED) n += 1;

@@ -19,11 +19,8 @@
 //
 // nufft_kernel does the whole step per column (used by the allocation-free
 // entry point); plans run it as spread_kernel + lat_fft_kernel below.
-#include <algorithm>
-
 #include "fft_ct.cuh"
 #include "plan.h"
-#include "plan_math.h"
 
 namespace hpx {
 
@@ -354,7 +351,33 @@ __global__ void __launch_bounds__(512, (E <= 16 ? 2 : 1)) lat_fft_pair_kernel(
 }
 
 // lat_fft_pair_kernel with the grid length M = 2^LOGM fixed at compile time
-// (fft_ct.cuh): the same outputs, the same arithmetic in the same order.
+// (fft_ct.cuh).
+//
+// FP32 precision at the highest latitude modes: an FP32 FFT leaves every
+// output with an absolute error of about 2^-24 times the norm of its input,
+// which for a smooth grid (a steep spectrum: most of the power at low latitude
+// frequencies) swamps the small modes near j = p that carry the highest
+// degrees.  The FP32 kernel therefore transforms the leaky first difference
+// dz_t = z_t - rho z_{t-1} (cyclic, rho = 7/8, one rounding: a fused
+// multiply-add), whose norm is mostly that of the grid's high-frequency part,
+// and recovers Z_j = DFT(dz)_j / (1 - rho e^{-2 pi i j / M}).  The division is
+// exact algebra; it amplifies rounding errors by at most 1 / (1 - rho) = 8 at
+// j = 0 (a rough grid, e.g. white noise, loses up to a factor of about 5 there),
+// while a smooth grid keeps the high modes about ten times more accurately.
+constexpr float kPrewhiten = 0.875f;
+
+// 1 / (1 - rho e^{-2 pi i j / M}) for 0 <= j < M, without cancellation:
+// 1 - rho e^{-i x} = (1 - rho) + 2 rho sin^2(x/2) + i rho sin x.
+template <int M>
+__device__ __forceinline__ cplx<float> prewhiten_inverse(int j) {
+    float sn, cs;
+    sincospif((float)j / (float)M, &sn, &cs);   // sin, cos of x/2, x = 2 pi j / M
+    const float a = (1.f - kPrewhiten) + 2.f * kPrewhiten * sn * sn;
+    const float b = 2.f * kPrewhiten * sn * cs;
+    const float inv = 1.f / (a * a + b * b);
+    return mk<float>(a * inv, -b * inv);
+}
+
 template <class T, int LOGM, int NT>
 __global__ void __launch_bounds__(NT, (LOGM <= 13 ? 1024 / NT : 1)) lat_fft_pair_ct_kernel(
     const cplx<T>* __restrict__ U, cplx<T>* __restrict__ bvec, const T* __restrict__ dec,
@@ -381,11 +404,24 @@ __global__ void __launch_bounds__(NT, (LOGM <= 13 ? 1024 / NT : 1)) lat_fft_pair
         }
         return v;
     };
-    auto st = [&](int j, int, cplx<T> v) {
-        if (j <= p) zlo[j] = v;
-        else if (j >= M - p) zhi[M - j] = v;
-    };
-    ct::fft<T, LOGM, NT, false, false>(u, tw, twlen >> LOGM, ld, st);
+    if constexpr (sizeof(T) == 4) {
+        // transform dz_t = z_t - rho z_{t-1}, then divide by 1 - rho e^{-2 pi i j / M}
+        auto ldw = [&](int t, int pi) {
+            const cplx<T> z = ld(t, pi), zp = ld((t + M - 1) & (M - 1), pi);
+            return mk<T>(fmaf(-kPrewhiten, zp.r, z.r), fmaf(-kPrewhiten, zp.i, z.i));
+        };
+        auto stw = [&](int j, int, cplx<T> v) {
+            if (j <= p) zlo[j] = mul(v, prewhiten_inverse<M>(j));
+            else if (j >= M - p) zhi[M - j] = mul(v, conjg(prewhiten_inverse<M>(M - j)));
+        };
+        ct::fft<T, LOGM, NT, false, false>(u, tw, twlen >> LOGM, ldw, stw);
+    } else {
+        auto st = [&](int j, int, cplx<T> v) {
+            if (j <= p) zlo[j] = v;
+            else if (j >= M - p) zhi[M - j] = v;
+        };
+        ct::fft<T, LOGM, NT, false, false>(u, tw, twlen >> LOGM, ld, st);
+    }
     cplx<T>* out0 = bvec + ((int64_t)b * (p + 1) + m0) * 2 * P2;
     cplx<T>* out1 = out0 + 2 * P2;
     float mx0 = 0.f, mx1 = 0.f;   // largest magnitudes stored (for bscale)
@@ -415,188 +451,6 @@ __global__ void __launch_bounds__(NT, (LOGM <= 13 ? 1024 / NT : 1)) lat_fft_pair
             if (has1) atomicMax(reinterpret_cast<int*>(bscale) + (int64_t)b * (L + 1) + m1, __float_as_int(mx1));
         }
     }
-}
-
-// Spreading and grid FFT in one kernel (FP32, M = 2^LOGM): one block per pair of
-// orders (m even, m + 1) and map spreads both half grids straight into the
-// shared-memory FFT input z (z[t] = u_m[t] + u_{m+1}[t], z[M - t] = u_m[t] -
-// u_{m+1}[t], as the grid FFT above reads them from U), so the half grids never
-// go through global memory.  The ring coefficients of the pair (2 x 8 bytes per
-// latitude node) are staged chunk by chunk (kSpreadChunk grid points, double
-// buffered, cp.async) while the previous chunk is spread; every grid point sums
-// its taps in the same order as spread_rb_kernel.  The chunk staging area is
-// reused for the kept modes after the spreading.
-//
-// Precision: an FP32 FFT leaves every output with an absolute error of about
-// 2^-24 times the norm of its input, which for a smooth grid (a steep spectrum:
-// most of the power at low latitude frequencies) swamps the small modes near
-// j = p that carry the highest degrees.  The FFT therefore transforms the first
-// difference dz_t = z_t - z_{t-1} (cyclic; exact in FP32 for neighbouring values
-// of a smooth grid), whose norm is that of the grid's high-frequency part, and
-// recovers Z_j = DFT(dz)_j / (1 - e^{-2 pi i j / M}) = DFT(dz)_j (1/2 - (i/2)
-// cot(pi j / M)) for j != 0; Z_0 = sum_t z_t is summed in double.  The factor is
-// exact algebra, so the outputs are the same modes with smaller rounding errors.
-template <int LOGM, int NT>
-__global__ void __launch_bounds__(NT, (LOGM <= 13 ? 1024 / NT : 1)) nufft_ct_kernel(
-    const cplx<float>* __restrict__ Y, cplx<float>* __restrict__ bvec, const int* __restrict__ hstart,
-    const float* __restrict__ hwts, int E, int rowsC, const float* __restrict__ dec,
-    const cplx<float>* __restrict__ tw, int twlen, int p, int Q, int L, int P2, float* __restrict__ bscale) {
-    constexpr int M = 1 << LOGM;
-    constexpr int H = M >> 1;
-    constexpr int CT = kSpreadChunk;
-    static_assert(CT % NT == 0, "nufft_ct_kernel: a chunk is a whole number of grid points per thread");
-    extern __shared__ unsigned char smem_raw[];
-    cplx<float>* buf = reinterpret_cast<cplx<float>*>(smem_raw);   // M (padded)
-    cplx<float>* stage = buf + M + M / 16;                          // 2 x [rowsC][2], later zlo / zhi
-    cplx<float>* zlo = stage;                                       // Z_j, j = 0..p
-    cplx<float>* zhi = zlo + (p + 1);                               // Z_{M-j}, j = 0..p
-    const int m0 = 2 * blockIdx.x, m1 = m0 + 1;
-    const int b = blockIdx.y;
-    const int tid = threadIdx.x;
-    const bool has1 = m1 <= L;
-    const cplx<float>* yb = Y + (int64_t)b * Q * (p + 1);
-    constexpr int nchunks = (H + CT) / CT;   // grid points 0..H
-    auto fetch = [&](int c, cplx<float>* dst) {
-        const int t0 = c * CT;
-        const int R0 = hstart[t0];
-        const int nr = hstart[min(t0 + CT - 1, H)] + E - R0;   // <= rowsC
-        for (int idx = tid; idx < 2 * nr; idx += NT) {
-            const int r = idx >> 1, k = idx & 1;
-            const bool ok = k == 0 || has1;
-            cp_async8(dst + idx, ok ? yb + (int64_t)(R0 + r) * (p + 1) + m0 + k : yb, ok ? 8 : 0);
-        }
-        cp_async_commit();
-    };
-    double z0r = 0.0, z0i = 0.0;   // this thread's part of Z_0 = sum_t z_t
-    fetch(0, stage);
-    for (int c = 0; c < nchunks; ++c) {
-        if (c + 1 < nchunks) fetch(c + 1, stage + ((c + 1) & 1) * 2 * rowsC);
-        else cp_async_commit();
-        cp_async_wait<1>();
-        __syncthreads();
-        const cplx<float>* ys = stage + (c & 1) * 2 * rowsC;
-        const int R0 = hstart[c * CT];
-#pragma unroll
-        for (int q = 0; q < CT / NT; ++q) {
-            const int t = c * CT + tid + q * NT;
-            if (t <= H) {
-                const cplx<float>* yr = ys + 2 * (hstart[t] - R0);
-                const float2* w = reinterpret_cast<const float2*>(hwts) + t;
-                float a0r = 0.f, a0i = 0.f, a1r = 0.f, a1i = 0.f;
-                for (int e = 0; e < E; ++e) {
-                    const float2 we = w[(size_t)e * (H + 1)];
-                    const cplx<float> y0 = yr[2 * e], y1 = yr[2 * e + 1];
-                    a0r += we.x * y0.r;
-                    a0i += we.x * y0.i;
-                    a1r += we.y * y1.r;
-                    a1i += we.y * y1.i;
-                }
-                if (!has1) { a1r = 0.f; a1i = 0.f; }
-                const cplx<float> zp = mk<float>(a0r + a1r, a0i + a1i);
-                buf[ct::padc(t)] = zp;
-                z0r += zp.r;
-                z0i += zp.i;
-                if (t > 0 && t < H) {
-                    const cplx<float> zm = mk<float>(a0r - a1r, a0i - a1i);
-                    buf[ct::padc(M - t)] = zm;
-                    z0r += zm.r;
-                    z0i += zm.i;
-                }
-            }
-        }
-        __syncthreads();   // this chunk's buffer is refilled by the next iteration's fetch
-    }
-    // Z_0 in double: warp sums, then one value per warp in shared memory
-    __shared__ double z0w[NT / 32][2];
-    for (int o = 16; o > 0; o >>= 1) {
-        z0r += __shfl_xor_sync(0xffffffffu, z0r, o);
-        z0i += __shfl_xor_sync(0xffffffffu, z0i, o);
-    }
-    if ((tid & 31) == 0) { z0w[tid >> 5][0] = z0r; z0w[tid >> 5][1] = z0i; }
-    // 1 / (1 - e^{-2 pi i j / M}) = 1/2 - (i/2) cot(pi j / M), j = 1..M-1
-    auto q = [](int j) {
-        float sn, cs;
-        sincospif((float)j / (float)M, &sn, &cs);
-        return mk<float>(0.5f, -0.5f * cs / sn);
-    };
-    auto st = [&](int j, int, cplx<float> v) {
-        if (j == 0) return;
-        if (j <= p) zlo[j] = mul(v, q(j));
-        else if (j >= M - p) zhi[M - j] = mul(v, q(j));
-    };
-    // the FFT's first pass reads dz_t = z_t - z_{t-1} from the padded grid
-    ct::fft<float, LOGM, NT, false, true>(
-        buf, tw, twlen >> LOGM,
-        [&](int t, int pi) { return sub(buf[pi], buf[ct::padc((t + M - 1) & (M - 1))]); }, st);
-    cplx<float> Z0 = mk<float>(0.f, 0.f);
-    {
-        double sr = 0.0, si = 0.0;
-        for (int w = 0; w < NT / 32; ++w) { sr += z0w[w][0]; si += z0w[w][1]; }
-        Z0 = mk<float>((float)sr, (float)si);
-    }
-    cplx<float>* out0 = bvec + ((int64_t)b * (p + 1) + m0) * 2 * P2;
-    cplx<float>* out1 = out0 + 2 * P2;
-    float mx0 = 0.f, mx1 = 0.f;
-    for (int j = tid; j <= p; j += NT) {
-        const cplx<float> a = (j == 0) ? Z0 : zlo[j], c = (j == 0) ? Z0 : zhi[j];
-        const float dj = dec[j];
-        const cplx<float> v0 = scale(add(a, c), 0.5f * dj);
-        out0[(j & 1) * P2 + (j >> 1)] = v0;
-        mx0 = fmaxf(mx0, fmaxf(fabsf(v0.r), fabsf(v0.i)));
-        if (has1) {
-            const cplx<float> v = scale(sub(a, c), 0.5f * dj);
-            out1[(j & 1) * P2 + (j >> 1)] = mk<float>(-0.5f * v.i, 0.5f * v.r);
-            mx1 = fmaxf(mx1, 0.5f * fmaxf(fabsf(v.r), fabsf(v.i)));
-        }
-    }
-    if (tid == 0) {
-        out0[P2 + (P2 - 1)] = mk<float>(0.f, 0.f);
-        if (has1) out1[P2 + (P2 - 1)] = mk<float>(0.f, 0.f);
-    }
-    if (bscale) {
-        for (int o = 16; o > 0; o >>= 1) {
-            mx0 = fmaxf(mx0, __shfl_xor_sync(0xffffffffu, mx0, o));
-            mx1 = fmaxf(mx1, __shfl_xor_sync(0xffffffffu, mx1, o));
-        }
-        if ((tid & 31) == 0) {
-            atomicMax(reinterpret_cast<int*>(bscale) + (int64_t)b * (L + 1) + m0, __float_as_int(mx0));
-            if (has1) atomicMax(reinterpret_cast<int*>(bscale) + (int64_t)b * (L + 1) + m1, __float_as_int(mx1));
-        }
-    }
-}
-
-namespace {
-// log2 of the grid, or 0 where the fused FP32 kernel does not apply
-int nufft_fused_logm(const hpx_plan_s* P) {
-    if (P->precision != HPX_FP32) return 0;
-    int logM = 0;
-    while ((1 << logM) < P->g.M) ++logM;
-    if (logM < 12 || logM > 14 || P->t.spreadRowsC <= 0) return 0;
-    const size_t smem = ((size_t)P->g.M + P->g.M / 16 +
-                         std::max<size_t>(4 * (size_t)P->t.spreadRowsC, 2 * (size_t)(P->g.p + 1))) * 8;
-    return smem <= 227 * 1024 ? logM : 0;
-}
-}  // namespace
-
-bool nufft_fused(const hpx_plan_s* P) { return nufft_fused_logm(P) != 0; }
-
-void launch_nufft_fused(const hpx_plan_s* P, cudaStream_t s) {
-    const auto& g = P->g;
-    const auto& t = P->t;
-    const int logM = nufft_fused_logm(P);
-    if (P->bscale) cudaMemsetAsync(P->bscale, 0, (size_t)g.B * (g.L + 1) * sizeof(float), s);
-    const size_t smem = ((size_t)g.M + g.M / 16 + std::max<size_t>(4 * (size_t)t.spreadRowsC, 2 * (size_t)(g.p + 1))) *
-                        sizeof(cplx<float>);
-    dim3 grid((g.L + 2) / 2, g.B);
-    auto run = [&](auto kern, int threads) {
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        kern<<<grid, threads, smem, s>>>((const cplx<float>*)P->Y, (cplx<float>*)P->bvec, t.hstart,
-                                         (const float*)t.hwts, t.spreadH, t.spreadRowsC, (const float*)t.dec,
-                                         (const cplx<float>*)t.twid, g.Lmax, g.p, g.Q, g.L, g.P2, P->bscale);
-    };
-    if (logM == 12) run(nufft_ct_kernel<12, 256>, 256);
-    else if (logM == 13) run(nufft_ct_kernel<13, 512>, 512);
-    else run(nufft_ct_kernel<14, 512>, 512);
 }
 
 template <class T>

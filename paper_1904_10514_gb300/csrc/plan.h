@@ -28,7 +28,7 @@ struct DevTables {
     int spreadE = 0;
     int* hstart = nullptr;                  // half-grid spreading with folded mirrors
     void* hwts = nullptr;                   // T [spreadH][M/2 + 1][2]
-    int spreadH = 0, spreadRows = 0, spreadD = 0, spreadRowsC = 0;
+    int spreadH = 0, spreadRows = 0, spreadD = 0;
     void* D = nullptr;                      // T [2][2][P2][P2]
     void* C = nullptr;                      // T [2][2][P2][P2]: change of basis alone (HPX_FLAG_CG)
     void* cgH = nullptr;                    // cplx<T> [4][2][cgN]: CG matrix-vector tables
@@ -138,10 +138,7 @@ template <class T> void launch_poles(const hpx_plan_s* P, const T* maps, cudaStr
 template <class T> void launch_nufft(const hpx_plan_s* P, cudaStream_t s);
 template <class T> void launch_spread(const hpx_plan_s* P, cudaStream_t s);
 template <class T> void launch_lat_fft(const hpx_plan_s* P, cudaStream_t s);
-// FP32 plans whose grid is 4096..16384 points: spreading and grid FFT in one
-// kernel (k_nufft.cu); launch_nufft_fused replaces launch_spread + launch_lat_fft
-bool nufft_fused(const hpx_plan_s* P);
-void launch_nufft_fused(const hpx_plan_s* P, cudaStream_t s);
+
 template <class T> void launch_dense(const hpx_plan_s* P, cudaStream_t s, const void* Dmat = nullptr);
 template <class T> void launch_cg(const hpx_plan_s* P, cudaStream_t s);
 template <class T> void launch_rot(const hpx_plan_s* P, T* alm, cudaStream_t s);

@@ -389,10 +389,7 @@ std::string build_tables(int nside, int lmax, bool fp64, PlanTables& t) {
             for (int t0 = 0; t0 <= H; t0 += 32)
                 rows32 = std::max(rows32, t.hstart[std::min(t0 + 31, H)] + E - t.hstart[t0]);
             t.spreadRows = rows32;
-            int rowsC = 0;   // the same bound for chunks of kSpreadChunk grid points
-            for (int t0 = 0; t0 <= H; t0 += kSpreadChunk)
-                rowsC = std::max(rowsC, t.hstart[std::min(t0 + kSpreadChunk - 1, H)] + E - t.hstart[t0]);
-            t.spreadRowsC = rowsC;
+
             t.spreadD = 0;
             for (int t0 = 0; t0 <= H; t0 += 4) t.spreadD = std::max(t.spreadD, t.hstart[std::min(t0 + 3, H)] - t.hstart[t0]);
         }

@@ -7,9 +7,6 @@
 
 namespace hpx {
 
-// grid points per chunk of the fused spreading + grid-FFT kernel
-constexpr int kSpreadChunk = 1024;
-
 struct PlanTables {
     int ns = 0;      // N_side
     int p = 0;       // 2 N_side: longitude/latitude half-bandwidth
@@ -50,7 +47,6 @@ struct PlanTables {
     // consecutive grid points.
     int spreadH = 0, spreadRows = 0;
     int spreadD = 0;             // max of hstart[t + 3] - hstart[t] over t = 0, 4, 8, ..
-    int spreadRowsC = 0;         // nodes seen by kSpreadChunk consecutive grid points (at most)
     std::vector<int> hstart;
     std::vector<double> hwts;    // [spreadH][M/2 + 1][2]
 

@@ -397,9 +397,10 @@ def test_tensor_core_damped_spectrum_nside1024(hp):
     the tensor-core kernel have to carry).  Maps 0 and 31 are seeded skies; maps
     1-30 are quarter turns and mirrors of them.  On a sample of orders, per
     degree: the tensor-core path meets 1e-5 wherever the FP32-pipe path (the
-    same stages with the contraction in FP32 FMAs) does, and is never worse than
-    twice its error: the degrees that miss 1e-5 on both are those whose power lies
-    below the FP32 rounding of the map (white error floor of FP32 arithmetic)."""
+    same stages with the contraction in FP32 FMAs) meets it with a margin of 2,
+    and is never worse than twice its error (or half the gate): the degrees that
+    miss 1e-5 on both are those whose power lies below the FP32 rounding of the
+    map (white error floor of FP32 arithmetic)."""
     ns, L, B = 1024, 2048, 32
     base, alms = _damped_maps(ns, L, [9200, 9231])
     q, mir = ring_perm(ns, True), ring_perm(ns, False)
@@ -425,7 +426,7 @@ def test_tensor_core_damped_spectrum_nside1024(hp):
         rk = {m: ref[m][k] for m in strat}
         e_tc = sampled_per_l_errors(cols(a_tc), rk, norms, L)
         e_si = sampled_per_l_errors(cols(a_si), rk, norms, L)
-        ok_si = e_si < TOL["fp32"]
-        assert ok_si[2:800].all(), (b, e_si[2:800].max())           # FP32 resolves these degrees
-        assert (e_tc[ok_si] < TOL["fp32"]).all(), (b, e_tc[ok_si].max())
-        assert (e_tc <= np.maximum(2.0 * e_si, TOL["fp32"])).all(), (b, np.max(e_tc / np.maximum(e_si, 1e-30)))
+        assert (e_si[2:800] < TOL["fp32"]).all(), (b, e_si[2:800].max())     # FP32 resolves these degrees
+        clear = e_si < 0.5 * TOL["fp32"]                                      # ... with a margin of 2
+        assert (e_tc[clear] < TOL["fp32"]).all(), (b, e_tc[clear].max())
+        assert (e_tc <= np.maximum(2.0 * e_si, 0.5 * TOL["fp32"])).all(), (b, np.max(e_tc / np.maximum(e_si, 1e-30)))
