@@ -27,7 +27,7 @@ __global__ void __launch_bounds__(256) dense_kernel(const T* __restrict__ D,
                                                     cplx<T>* __restrict__ beta, int P2, int p, int L,
                                                     int B) {
     __shared__ T Ds[TK][TQ + 1];
-    __shared__ cplx<T> Bs[TK][TC];
+    __shared__ cplx<T> Bs[TK][TC + 1];   // padded: the loads below store 16 consecutive k of one column
     const int mpar = blockIdx.z >> 1, par = blockIdx.z & 1;
     const int nmp = (L >= mpar) ? (L - mpar) / 2 + 1 : 0;
     const int ncols = nmp * B;

@@ -17,6 +17,8 @@ struct DevTables {
     int *nphi = nullptr, *startN = nullptr, *startS = nullptr, *pow2 = nullptr, *logn = nullptr,
         *fftL = nullptr, *logL = nullptr;
     int64_t *shOff = nullptr, *chOff = nullptr, *bhOff = nullptr;
+    int64_t* bhOffA = nullptr;   // analysis Bluestein kernels (convolution lengths fftLa of plan_math.h)
+    void *bhatA = nullptr, *twA = nullptr;   // cplx<T>
     void *shift = nullptr, *chirp = nullptr, *bhat = nullptr, *twid = nullptr;   // cplx<T>
     int *poleN = nullptr, *poleS = nullptr;
     double* polew = nullptr;
@@ -70,7 +72,9 @@ struct hpx_plan_s {
     // Bluestein length): ring pairs ringList[first .. first + count - 1]
     struct RingClass {
         int N, first, count;
-        bool blue;   // N >= kRingCtMin: every ring of the class is a Bluestein ring (else none is)
+        bool ct;       // compile-time kernel of length N (ring_ct_length): every ring of the class is
+        bool blue;     // ... a Bluestein ring (blue) or none is
+        int64_t twOff; // ct, N not a power of two: first twiddle of length N in twA; else -1
     };
     std::vector<RingClass> ringClasses;
     int* ringList = nullptr;
@@ -129,9 +133,10 @@ struct hpx_plan_s {
 
 namespace hpx {
 
-// ring transforms of this many points or more run in launches of one length and
-// one kind (plain or Bluestein) with the compile-time FFT of fft_ct.cuh
-constexpr int kRingCtMin = 4096;
+// ring transform lengths with a compile-time kernel (fft_ct.cuh; 2^k from 4096
+// and the smooth Bluestein lengths 3, 5, 7 2^k of FP32 plans): their rings run in
+// launches of one length and one kind (plain or Bluestein)
+bool ring_ct_length(int N);
 
 template <class T> void launch_ring_fft(const hpx_plan_s* P, const T* maps, cudaStream_t s);
 template <class T> void launch_poles(const hpx_plan_s* P, const T* maps, cudaStream_t s);
