@@ -112,6 +112,22 @@ def stage_work(ns, L, B, es=8):
     }
 
 
+def fused_compute_view(work, ms, peaks):
+    """The per-order operator stage under the survey's accounting of steps a-4 + a-5: its algorithmic
+    work is the flops of the latitude operator D and of the Givens sweeps it replaces (exact counts),
+    a compute-bound stage; the kernel runs on the tensor cores (FP16 pairs, three MMAs per product),
+    so the peak is the measured dense FP16/BF16 rate.  The operator stream and the MMA flops the kernel
+    executes are reported beside it."""
+    flops = work["lat_solve"][1] + work["rot_sweep"][1]
+    peak = peaks.get("bf16_tflops", 1900.0)
+    t = ms / 1e3
+    return {"bound": "tensor", "achieved": flops / t / 1e12, "peak": peak, "unit": "TFLOP/s",
+            "frac": flops / t / 1e12 / peak,
+            "peak_source": "measured bf16 dense (FP16 MMAs run at the same rate)" if "bf16_tflops" in peaks
+            else "fallback",
+            "algorithmic_flops": flops, "what": "D application + Givens sweeps (steps a-4, a-5), exact counts"}
+
+
 def stage_roofline(kind, amount, ms, peaks):
     """Roofline entry of one stage: algorithmic bytes (or flops) of one launch over its time."""
     t = ms / 1e3
@@ -137,11 +153,17 @@ def roofline_report(work, per_launch, peaks):
     names = [n for n in per_launch if n in work and work[n][1] > 0]
     dom = max(names, key=lambda n: per_launch[n])
     kind, amount = work[dom]
-    roof = stage_roofline(kind, amount, per_launch[dom], peaks)
     ratio = TRAFFIC_OVER_ALGORITHMIC.get(dom)
-    roof["traffic"] = amount * ratio if (ratio and kind == "hbm") else None
-    roof["traffic_source"] = ("ncu at Nside 512, 32 maps: %.4f x the algorithmic bytes, scaled" % ratio
-                              if roof["traffic"] else None)
+    if dom == "fused_fsht" and "lat_solve" in work:
+        roof = fused_compute_view(work, per_launch[dom], peaks)
+        stream = stage_roofline(kind, amount, per_launch[dom], peaks)
+        roof["operator_stream"] = {"bytes": amount, "achieved_gbs": stream["achieved"], "frac_hbm": stream["frac"]}
+        roof["traffic"] = amount * ratio if ratio else None
+    else:
+        roof = stage_roofline(kind, amount, per_launch[dom], peaks)
+        roof["traffic"] = amount * ratio if (ratio and kind == "hbm") else None
+    roof["traffic_source"] = ("ncu at Nside 512, 32 maps: %.4f x the operator stream bytes, scaled" % ratio
+                              if roof.get("traffic") else None)
     roof["kernel"] = dom
     roof["per_launch_ms"] = per_launch[dom]
     per_stage = {}
@@ -264,6 +286,100 @@ def run_reference(args, rank):
                                                          "full_map_s": float(np.mean(fulls))}},
             "e2e": {"value": v, "unit": "Gpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ other workloads
+def uneven_leg(hp, torch, stream, args):
+    """200 FP32 maps with Nside drawn from {64, 128, 256, 512, 1024} (probabilities .40/.30/.15/.10/.05,
+    skies.uneven_nsides), lmax = 2 Nside: one group plan replayed as one CUDA graph, and the same maps
+    as one uniform plan per Nside run one after the other (the sum of their times).  Timing inputs:
+    seeded white-noise maps of those sizes (the throughput does not depend on the sky)."""
+    import skies
+    nsides = [int(v) for v in skies.uneven_nsides(200)]
+    rng = np.random.default_rng(4000)
+    npix = [12 * n * n for n in nsides]
+    x = torch.as_tensor(rng.standard_normal(sum(npix)).astype(np.float32), device="cuda")
+    plan = hp.Plan(nsides=nsides, precision="fp32", graph=True)
+    alm = torch.empty(plan.nalm, dtype=torch.complex64, device="cuda")
+    cl = torch.empty(plan.ncl, dtype=torch.float64, device="cuda")
+    for _ in range(3):
+        plan.analyze(x, out=alm)
+        plan.cl(alm, out=cl)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n = max(3, min(args.steps, 10))
+    e0.record(stream)
+    for _ in range(n):
+        plan.analyze(x, out=alm)
+        plan.cl(alm, out=cl)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_group = e0.elapsed_time(e1) / n / 1e3
+    launches = hp.lib().hpx_plan_launches(plan.handle)
+    plan.close()
+    # one uniform plan per Nside, maps gathered by Nside
+    t_sum = 0.0
+    counts = {}
+    for ns in sorted(set(nsides)):
+        cnt = nsides.count(ns)
+        counts[ns] = cnt
+        p1 = hp.Plan(ns, 2 * ns, cnt, "fp32")
+        xs = torch.as_tensor(rng.standard_normal((cnt, 12 * ns * ns)).astype(np.float32), device="cuda")
+        a1 = p1.analyze(xs)
+        c1 = p1.cl(a1)
+        for _ in range(2):
+            p1.analyze(xs, out=a1)
+            p1.cl(a1, out=c1)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(n):
+            p1.analyze(xs, out=a1)
+            p1.cl(a1, out=c1)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_sum += e0.elapsed_time(e1) / n / 1e3
+        p1.close()
+    pix = float(sum(npix))
+    return {"value": pix / t_group / 1e9, "unit": "Gpix/s", "ms_per_step": t_group * 1e3,
+            "maps_per_nside": counts, "pixels": int(pix), "graph_nodes_kernels": launches,
+            "separate_uniform_plans": {"value": pix / t_sum / 1e9, "unit": "Gpix/s", "ms_per_step": t_sum * 1e3},
+            "inputs": "seeded white-noise maps of the workload's sizes"}
+
+
+def gradient_leg(hp, torch, stream, args):
+    """8 FP32 maps at Nside 2048, lmax 4096: loss = sum_l w_l (C_l - C*_l)^2 (w_l = 1/l, l >= 2) and its
+    gradient with respect to the maps (analysis, C_l, then the C_l and analysis vector-Jacobian products
+    in the library).  Timing inputs: seeded white-noise maps."""
+    ns, L, B = 2048, 4096, 8
+    rng = np.random.default_rng(2048)
+    x = torch.as_tensor(rng.standard_normal((B, 12 * ns * ns)).astype(np.float32), device="cuda")
+    plan = hp.Plan(ns, L, B, "fp32")
+    w = torch.zeros(L + 1, dtype=torch.float64, device="cuda")
+    w[2:] = 1.0 / torch.arange(2, L + 1, dtype=torch.float64, device="cuda")
+    cstar = torch.as_tensor(np.r_[0.0, 0.0, np.arange(2, L + 1, dtype=np.float64) ** -2.0], device="cuda")
+
+    def step():
+        xg = x.detach().requires_grad_(True)
+        c = hp.cl(hp.analyze(xg, plan), plan)
+        loss = torch.sum(w * (c - cstar) ** 2)
+        loss.backward()
+        return xg.grad
+
+    for _ in range(2):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n = 3
+    e0.record(stream)
+    for _ in range(n):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / n / 1e3
+    path = "sweeps" if plan.flags & hp.HPX_FLAG_SWEEPS else "per-order operators"
+    plan.close()
+    return {"value": B * 12 * ns * ns / t / 1e9, "unit": "Gpix/s (loss + map gradient)", "ms_per_step": t * 1e3,
+            "path": path, "inputs": "seeded white-noise maps"}
 
 
 # ------------------------------------------------------------------ GPU arm
@@ -506,6 +622,13 @@ def main():
     plan_sw.close()
     del alm_sw
 
+    # uneven batch (200 maps, Nside drawn from {64, ..., 1024}, lmax = 2 Nside) in one plan replayed
+    # as one CUDA graph, against the same maps as separate uniform plans (one per Nside)
+    uneven = uneven_leg(hp, torch, stream, args)
+    # differentiation workload: 8 maps at Nside 2048, C_l loss, gradient through the library's
+    # vector-Jacobian products (hpx_cl_vjp, hpx_analyze_vjp)
+    diffw = gradient_leg(hp, torch, stream, args)
+
     # the plain FP64 single-map form on the same GPU
     plan64 = hp.Plan(NSIDE, LMAX, 1, "fp64")
     m64 = maps[:1].double().contiguous()
@@ -572,7 +695,7 @@ def main():
             "data": "synthetic",
             "config": config_dict(), "roofline": roof, "roofline_stages": per_stage, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": (hp.lib().hpx_plan_launches(plan.handle) + 1) * args.steps, "clocks": clk, "fp64_single_map": fp64, "sh_synthesis_fp32": synthesis, "ablation_cg_latitude_solve": cg,
-            "sweeps_path": sweeps,
+            "sweeps_path": sweeps, "uneven_batch_200": uneven, "differentiation_nside2048x8": diffw,
             "fp32_batched_over_fp64_single": value / world / fp64["value"],
             "stages_ms_per_launch": per_launch, "plan_build_s": plan_build_s, "plan_gb": plan.nbytes / 1e9,
             "plan_path": "sweeps" if plan.flags & hp.HPX_FLAG_SWEEPS else "per-order operators"}

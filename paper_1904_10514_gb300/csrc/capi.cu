@@ -68,7 +68,7 @@ void free_plan(hpx_plan_s* P) {
     auto& t = P->t;
     void* ptrs[] = {t.nphi, t.startN, t.startS, t.pow2, t.logn, t.fftL, t.logL, t.shOff, t.chOff,
                     t.bhOff, t.shift, t.chirp, t.bhat, t.twid, t.poleN, t.poleS, t.polew, t.rowptr,
-                    t.ent, t.entw, t.dec, t.D, t.bhOffA, t.bhatA, t.twA, t.angOff, t.ang, t.skOff, t.skew, t.skewT, t.nrowptr, t.nent, t.nentw, t.nstart, t.swts, t.hstart, t.hwts, t.Es, t.shifted, t.C, t.cgH, P->Y, P->U, P->bvec,
+                    t.ent, t.entw, t.dec, t.D, t.tstart, t.hwn, t.angOff, t.ang, t.skOff, t.skew, t.skewT, t.nrowptr, t.nent, t.nentw, t.nstart, t.swts, t.hstart, t.hwts, t.Es, t.shifted, t.C, t.cgH, P->Y, P->U, P->bvec,
                     P->fusedM, P->fusedOff, P->fusedTiles, P->tcOff, P->tcFirst, P->tcRinv, P->bscale, P->d_status, P->synM, P->ringList};
     for (void* q : ptrs)
         if (q) cudaFree(q);
@@ -193,46 +193,39 @@ hpx_plan_s* hpx_plan_ex(const hpx_plan_desc* d) {
     t.twid = up.real(tb.twid, fp64);
     t.poleN = up.vec(tb.poleN); t.poleS = up.vec(tb.poleS); t.polew = up.vec(tb.polew);
     t.npole = (int)tb.polew.size();
-    {   // ring pairs grouped by transform length (longest first), and for the
-        // compile-time kernels also by kind (plain rings, then Bluestein rings)
+    {   // ring pairs grouped by transform length (longest first), and from
+        // kRingCtMin points up also by kind (plain rings, then Bluestein rings)
         struct Key {
             int N, blue, i;
         };
         std::vector<Key> byN;
         for (int i = 0; i < tb.npairs; ++i)
-            byN.push_back({tb.pow2[i] ? tb.nphi[i] : tb.fftLa[i], tb.pow2[i] ? 0 : 1, i});
+            byN.push_back({tb.pow2[i] ? tb.nphi[i] : tb.fftL[i], tb.pow2[i] ? 0 : 1, i});
         std::stable_sort(byN.begin(), byN.end(), [](const Key& a, const Key& b) {
             if (a.N != b.N) return a.N > b.N;
-            return hpx::ring_ct_length(a.N) && a.blue < b.blue;
+            return a.N >= hpx::kRingCtMin && a.blue < b.blue;
         });
         std::vector<int> list;
         for (size_t k = 0; k < byN.size(); ++k) {
             // transforms of kRingMergeN points or fewer share one launch, with
             // blocks sized for the longest of them: alone, each of these short
             // launches is bound by its latency, not by its work
-            const int N = byN[k].N;
-            const bool ct = hpx::ring_ct_length(N);
-            const bool merged = !ct && N <= kRingMergeN && k > 0 && byN[k - 1].N <= kRingMergeN &&
-                                !hpx::ring_ct_length(byN[k - 1].N);
-            const bool newkind = ct && k > 0 && byN[k].blue != byN[k - 1].blue;
-            if (k == 0 || (N != byN[k - 1].N && !merged) || newkind) {
-                int64_t twOff = -1;
-                for (size_t c = 0; c < tb.smoothL.size(); ++c)
-                    if (tb.smoothL[c] == N) twOff = tb.twAOff[c];
-                P->ringClasses.push_back({N, (int)k, 0, ct, byN[k].blue != 0, twOff});
-            }
+            const bool merged = byN[k].N <= kRingMergeN && k > 0 && byN[k - 1].N <= kRingMergeN;
+            const bool newkind = byN[k].N >= hpx::kRingCtMin && k > 0 && byN[k].blue != byN[k - 1].blue;
+            if (k == 0 || (byN[k].N != byN[k - 1].N && !merged) || newkind)
+                P->ringClasses.push_back({byN[k].N, (int)k, 0, byN[k].blue != 0});
             P->ringClasses.back().count++;
             list.push_back(byN[k].i);
         }
         P->ringList = up.vec(list);
-        t.bhOffA = up.vec(tb.bhOffA);
-        t.bhatA = up.real(tb.bhatA, fp64);
-        t.twA = up.real(tb.twA, fp64);
     }
     t.rowptr = up.vec(tb.rowptr); t.ent = up.vec(tb.ent);
     t.entw = up.real(tb.entw, fp64); t.dec = up.real(tb.dec, fp64);
     t.nstart = up.vec(tb.nstart); t.swts = up.real(tb.swts, fp64); t.spreadE = tb.spreadE;
     t.hstart = up.vec(tb.hstart); t.hwts = up.real(tb.hwts, fp64); t.spreadH = tb.spreadH;
+    t.tstart = up.vec(tb.tstart); t.hwn = up.real(tb.hwn, fp64); t.interpE = tb.interpE;
+    t.interpRows = tb.interpRows;
+    t.interpD = tb.interpD;
     t.spreadRows = tb.spreadRows;
     t.spreadD = tb.spreadD;
     t.D = up.real(tb.D, fp64);

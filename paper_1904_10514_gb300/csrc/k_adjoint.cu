@@ -15,6 +15,7 @@
 //   ring_adj   y -> ring samples: transposed shift/Nyquist/padding and inverse
 //              DFT per ring pair (Sec. 3.1)
 //   pole_adj   adds the transposed pole fit (Sec. 3.2.1) to the 3 rings per cap
+#include "fft_ct.cuh"
 #include "plan.h"
 #include "plan_math.h"
 
@@ -330,7 +331,8 @@ void launch_adjoint(const hpx_plan_s* P, const T* alm, T* maps, cudaStream_t s, 
         // columns m > lmax carry no coefficients: their rows of Y are zero
         cudaMemsetAsync(P->Y, 0, (size_t)g.B * g.Q * (g.p + 1) * sizeof(cplx<T>), s);
         dim3 grid(g.L + 1, g.B);
-        nufft_adj_kernel<T><<<grid, 512, smem, s>>>((const cplx<T>*)P->bvec, (cplx<T>*)P->Y, t.nrowptr, t.nent,
+        if (!launch_nufft2(P, s))
+            nufft_adj_kernel<T><<<grid, 512, smem, s>>>((const cplx<T>*)P->bvec, (cplx<T>*)P->Y, t.nrowptr, t.nent,
                                                     (const T*)t.nentw, (const T*)t.dec, (const cplx<T>*)t.twid,
                                                     g.Lmax, g.M, logM, g.p, g.Q, g.P2);
     }
@@ -367,10 +369,10 @@ __global__ void __launch_bounds__(256) ring_synth_kernel(
     const int* __restrict__ pow2_t, const int* __restrict__ logn_t, const int* __restrict__ fftL_t,
     const int* __restrict__ logL_t, const int64_t* __restrict__ chOff_t, const int64_t* __restrict__ bhOff_t,
     const cplx<T>* __restrict__ chirp, const cplx<T>* __restrict__ bhat, const cplx<T>* __restrict__ tw, int twlen,
-    int p, int L, int Q, int64_t npix, int npairs) {
+    int p, int L, int Q, int64_t npix, int npairs, const int* __restrict__ ringlist) {
     extern __shared__ unsigned char smem_raw[];
     cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw);
-    const int i = npairs - 1 - (int)blockIdx.x;
+    const int i = ringlist ? ringlist[blockIdx.x] : npairs - 1 - (int)blockIdx.x;
     const int b = blockIdx.y;
     const int n = nphi_t[i];
     const int sN = startN_t[i], sS = startS_t[i];
@@ -438,6 +440,124 @@ __global__ void __launch_bounds__(256) ring_synth_kernel(
     }
 }
 
+// ring_synth_kernel for the launches of one transform length N = 2^LOGN >= 4096
+// (the ring classes of the analysis: N = nphi for plain rings, the Bluestein
+// convolution length otherwise) with the compile-time FFT of fft_ct.cuh: the
+// fold of the orders is the first pass's input and the pixels are written from
+// shared memory after the transform.
+template <class T, int LOGN, int NT, bool BLUE>
+__global__ void __launch_bounds__(NT, (LOGN <= 13 ? 1024 / NT : 1)) ring_synth_ct_kernel(
+    const cplx<T>* __restrict__ Y, T* __restrict__ maps, const int* __restrict__ nphi_t,
+    const int* __restrict__ startN_t, const int* __restrict__ startS_t, const int* __restrict__ shifted_t,
+    const int64_t* __restrict__ chOff_t, const int64_t* __restrict__ bhOff_t, const cplx<T>* __restrict__ chirp,
+    const cplx<T>* __restrict__ bhat, const cplx<T>* __restrict__ tw, int twlen, int p, int L, int Q,
+    int64_t npix, const int* __restrict__ ringlist) {
+    const int twstep = twlen >> LOGN;
+    extern __shared__ unsigned char smem_raw[];
+    cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw);
+    const int i = ringlist[blockIdx.y];
+    const int b = blockIdx.x;
+    const int n = nphi_t[i];
+    const int sN = startN_t[i], sS = startS_t[i];
+    const bool equator = (sN == sS);
+    const int sh = shifted_t[i];
+    const int tid = threadIdx.x;
+    const cplx<T>* rowN = Y + ((int64_t)b * Q + (i + 1)) * (p + 1);
+    const cplx<T>* rowS = Y + ((int64_t)b * Q + (Q - 2 - i)) * (p + 1);
+    // G_m = F_m e^{i m phi0}, phi0 = sh pi / n; F_m = Y / 2 for even m (ring weight 2)
+    auto G = [&](const cplx<T>* row, int m) {
+        cplx<T> v = row[m];
+        if (!(m & 1)) v = scale(v, T(0.5));
+        if (m == 0) return mk<T>(v.r, T(0));
+        if (!sh) return v;
+        const int r = m % (2 * n);
+        T sn, cs;
+        if constexpr (sizeof(T) == 4) {
+            sincospif((float)r / (float)n, &sn, &cs);
+        } else {
+            sincospi((double)r / (double)n, &sn, &cs);
+        }
+        return mul(v, mk<T>(cs, sn));
+    };
+    // conj(z_k), z = (folded north) + i (folded south)
+    auto fold = [&](int k) {
+        cplx<T> cN = mk<T>(T(0), T(0)), cS = cN;
+        for (int m = k; m <= L; m += n) {
+            cN = add(cN, G(rowN, m));
+            if (!equator) cS = add(cS, G(rowS, m));
+        }
+        for (int m = n - k; m <= L; m += n) {
+            if (m == 0) continue;
+            cN = add(cN, conjg(G(rowN, m)));
+            if (!equator) cS = add(cS, conjg(G(rowS, m)));
+        }
+        return mk<T>(cN.r - cS.i, -(cN.i + cS.r));
+    };
+    auto to_smem = [&](int, int pi, cplx<T> v) { buf[pi] = v; };
+    if constexpr (!BLUE) {
+        ct::fft<T, LOGN, NT, false, false>(buf, tw, twstep, [&](int k, int) { return fold(k); }, to_smem);
+    } else {
+        const cplx<T>* ch = chirp + chOff_t[i];
+        const cplx<T>* bh = bhat + bhOff_t[i];
+        ct::fft<T, LOGN, NT, false, false>(
+            buf, tw, twstep, [&](int k, int) { return k < n ? mul(fold(k), ch[k]) : mk<T>(T(0), T(0)); },
+            [&](int j, int pi, cplx<T> v) { buf[pi] = mul(v, bh[j]); });
+        ct::fft<T, LOGN, NT, true, true>(
+            buf, tw, twstep, [&](int, int pi) { return buf[pi]; },
+            [&](int j, int pi, cplx<T> v) { buf[pi] = j < n ? mul(v, ch[j]) : v; });
+    }
+    // Z = conj(DFT(conj z)): north = Re Z, south = Im Z = -Im DFT(conj z)
+    T* f = maps + (int64_t)b * npix;
+    for (int k = tid; k < n; k += NT) {
+        const cplx<T> v = buf[ct::padc(k)];
+        f[sN + k] = v.r;
+        if (!equator) f[sS + k] = -v.i;
+    }
+}
+
+template <class T>
+void launch_ring_synth(const hpx_plan_s* P, T* maps, cudaStream_t s) {
+    const auto& g = P->g;
+    const auto& t = P->t;
+    auto old = [&](int blocks, size_t smem, const int* list) {
+        cudaFuncSetAttribute(ring_synth_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        dim3 grid(blocks, g.B);
+        ring_synth_kernel<T><<<grid, 256, smem, s>>>(
+            (const cplx<T>*)P->Y, maps, t.nphi, t.startN, t.startS, t.shifted, t.pow2, t.logn, t.fftL, t.logL,
+            t.chOff, t.bhOff, (const cplx<T>*)t.chirp, (const cplx<T>*)t.bhat, (const cplx<T>*)t.twid, g.Lmax, g.p,
+            g.L, g.Q, g.npix, g.npairs, list);
+    };
+    if (!P->ringList) {
+        old(g.npairs, (size_t)g.smem_ring * sizeof(cplx<T>), nullptr);
+        return;
+    }
+    for (const auto& c : P->ringClasses) {
+        if (c.N < kRingCtMin) {   // short rings: the radix-2 kernel, sized for the class's longest transform
+            old(c.count, (size_t)c.N * sizeof(cplx<T>), P->ringList + c.first);
+            continue;
+        }
+        const size_t smem = (size_t)(c.N + c.N / 16) * sizeof(cplx<T>);
+        dim3 grid(g.B, c.count);
+        auto run = [&](auto kern, int threads) {
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            kern<<<grid, threads, smem, s>>>((const cplx<T>*)P->Y, maps, t.nphi, t.startN, t.startS, t.shifted,
+                                             t.chOff, t.bhOff, (const cplx<T>*)t.chirp, (const cplx<T>*)t.bhat,
+                                             (const cplx<T>*)t.twid, g.Lmax, g.p, g.L, g.Q, g.npix,
+                                             P->ringList + c.first);
+        };
+        if (c.N == 4096) {
+            if (c.blue) run(ring_synth_ct_kernel<T, 12, 256, true>, 256);
+            else run(ring_synth_ct_kernel<T, 12, 256, false>, 256);
+        } else if (c.N == 8192) {
+            if (c.blue) run(ring_synth_ct_kernel<T, 13, 512, true>, 512);
+            else run(ring_synth_ct_kernel<T, 13, 512, false>, 512);
+        } else {
+            if (c.blue) run(ring_synth_ct_kernel<T, 14, 512, true>, 512);
+            else run(ring_synth_ct_kernel<T, 14, 512, false>, 512);
+        }
+    }
+}
+
 template <class T>
 void launch_sh_synthesis(const hpx_plan_s* P, const T* alm, T* maps, cudaStream_t s, cudaEvent_t* ev) {
     const auto& g = P->g;
@@ -464,20 +584,13 @@ void launch_sh_synthesis(const hpx_plan_s* P, const T* alm, T* maps, cudaStream_
         const size_t smem = (size_t)g.M * sizeof(cplx<T>);
         cudaFuncSetAttribute(nufft_adj_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         dim3 grid(g.L + 1, g.B);
-        nufft_adj_kernel<T><<<grid, 512, smem, s>>>((const cplx<T>*)P->bvec, (cplx<T>*)P->Y, t.nrowptr, t.nent,
-                                                    (const T*)t.nentw, (const T*)t.dec, (const cplx<T>*)t.twid,
-                                                    g.Lmax, g.M, logM, g.p, g.Q, g.P2);
+        if (!launch_nufft2(P, s))
+            nufft_adj_kernel<T><<<grid, 512, smem, s>>>((const cplx<T>*)P->bvec, (cplx<T>*)P->Y, t.nrowptr, t.nent,
+                                                        (const T*)t.nentw, (const T*)t.dec, (const cplx<T>*)t.twid,
+                                                        g.Lmax, g.M, logM, g.p, g.Q, g.P2);
     }
     if (ev) cudaEventRecord(ev[2], s);
-    {
-        const size_t smem = (size_t)g.smem_ring * sizeof(cplx<T>);
-        cudaFuncSetAttribute(ring_synth_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        dim3 grid(g.npairs, g.B);
-        ring_synth_kernel<T><<<grid, 256, smem, s>>>(
-            (const cplx<T>*)P->Y, maps, t.nphi, t.startN, t.startS, t.shifted, t.pow2, t.logn, t.fftL, t.logL,
-            t.chOff, t.bhOff, (const cplx<T>*)t.chirp, (const cplx<T>*)t.bhat, (const cplx<T>*)t.twid, g.Lmax, g.p,
-            g.L, g.Q, g.npix, g.npairs);
-    }
+    launch_ring_synth<T>(P, maps, s);
     if (ev)
         for (int k = 3; k <= hpx_plan_s::kStages; ++k) cudaEventRecord(ev[k], s);
 }

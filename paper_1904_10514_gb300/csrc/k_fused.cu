@@ -187,14 +187,15 @@ __global__ void __launch_bounds__(TR* TC) fused_apply_kernel(const T* __restrict
 // (rows i = degrees of the chain, columns k = latitude modes), and the
 // cosine/sine coefficients of F_m are the transposed contraction
 //     X[map][m][par][k] = sum_i S_{m,c}[i][k] a_{m+c+2i}^m[map].
-// Block = one (m, c, tile of 128 modes) x 16 maps; 256 threads, each 4 modes x
-// 2 maps; degrees in chunks of 16 staged in shared memory.
-template <class T>
+// Block = one (m, c, tile of 128 modes) x MB maps (16, or 32 so that batches of
+// 17+ maps read each operator once); 256 threads, each 4 modes x MB/8 maps;
+// degrees in chunks of 16 staged in shared memory.
+template <class T, int MB>
 __global__ void __launch_bounds__(256) synth_apply_kernel(const T* __restrict__ S, const int64_t* __restrict__ moff,
                                                           const cplx<T>* __restrict__ alm, cplx<T>* __restrict__ bvec,
                                                           int P2, int ldm, int p, int L, int B, int64_t nalm,
                                                           int nkt) {
-    constexpr int KT = 128, MB = 16, IC = 16;
+    constexpr int KT = 128, IC = 16, QB = MB / 8;
     __shared__ __align__(16) T As[IC][KT];
     __shared__ cplx<T> Bs[IC][MB];
     const int item = blockIdx.x;
@@ -206,11 +207,11 @@ __global__ void __launch_bounds__(256) synth_apply_kernel(const T* __restrict__ 
     const T* A = S + moff[(size_t)m * 2 + c] * ldm;
     const int64_t base = (int64_t)m * (2 * L + 1 - m) / 2 + m + c;
     const int tid = threadIdx.x, tk = tid & 31, tb = tid >> 5;
-    T accr[4][2], acci[4][2];
+    T accr[4][QB], acci[4][QB];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int q = 0; q < 2; ++q) { accr[a][q] = T(0); acci[a][q] = T(0); }
+        for (int q = 0; q < QB; ++q) { accr[a][q] = T(0); acci[a][q] = T(0); }
     for (int i0 = 0; i0 < nrows; i0 += IC) {
         for (int e = tid; e < IC * KT; e += 256) {
             const int ii = e / KT, kk = e % KT;
@@ -228,20 +229,22 @@ __global__ void __launch_bounds__(256) synth_apply_kernel(const T* __restrict__ 
             T a[4];
 #pragma unroll
             for (int r = 0; r < 4; ++r) a[r] = As[ii][tk * 4 + r];
-            const cplx<T> x0 = Bs[ii][tb * 2], x1 = Bs[ii][tb * 2 + 1];
+            cplx<T> x[QB];
 #pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                accr[r][0] += a[r] * x0.r;
-                acci[r][0] += a[r] * x0.i;
-                accr[r][1] += a[r] * x1.r;
-                acci[r][1] += a[r] * x1.i;
-            }
+            for (int q = 0; q < QB; ++q) x[q] = Bs[ii][tb * QB + q];
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int q = 0; q < QB; ++q) {
+                    accr[r][q] += a[r] * x[q].r;
+                    acci[r][q] += a[r] * x[q].i;
+                }
         }
         __syncthreads();
     }
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {
-        const int b = b0 + tb * 2 + q;
+    for (int q = 0; q < QB; ++q) {
+        const int b = b0 + tb * QB + q;
         if (b >= B) continue;
         cplx<T>* out = bvec + (((int64_t)b * (p + 1) + m) * 2 + par) * P2;
 #pragma unroll
@@ -256,9 +259,17 @@ template <class T>
 void launch_synth_apply(const hpx_plan_s* P, const T* alm, cudaStream_t s) {
     const auto& g = P->g;
     const int nkt = (g.P2 + 127) / 128;
-    dim3 grid((g.L + 1) * 2 * nkt, (g.B + 15) / 16);
-    synth_apply_kernel<T><<<grid, 256, 0, s>>>((const T*)P->synM, P->fusedOff, (const cplx<T>*)alm,
-                                               (cplx<T>*)P->bvec, g.P2, P->fused_ldm, g.p, g.L, g.B, g.nalm, nkt);
+    if (g.B > 16) {
+        dim3 grid((g.L + 1) * 2 * nkt, (g.B + 31) / 32);
+        synth_apply_kernel<T, 32><<<grid, 256, 0, s>>>((const T*)P->synM, P->fusedOff, (const cplx<T>*)alm,
+                                                       (cplx<T>*)P->bvec, g.P2, P->fused_ldm, g.p, g.L, g.B, g.nalm,
+                                                       nkt);
+    } else {
+        dim3 grid((g.L + 1) * 2 * nkt, (g.B + 15) / 16);
+        synth_apply_kernel<T, 16><<<grid, 256, 0, s>>>((const T*)P->synM, P->fusedOff, (const cplx<T>*)alm,
+                                                       (cplx<T>*)P->bvec, g.P2, P->fused_ldm, g.p, g.L, g.B, g.nalm,
+                                                       nkt);
+    }
 }
 
 template void launch_synth_apply<float>(const hpx_plan_s*, const float*, cudaStream_t);

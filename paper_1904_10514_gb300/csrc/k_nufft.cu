@@ -405,13 +405,9 @@ __global__ void __launch_bounds__(NT, (LOGM <= 13 ? 1024 / NT : 1)) lat_fft_pair
         return v;
     };
     if constexpr (sizeof(T) == 4) {
-        // transform dz_t = z_t - rho z_{t-1}, then divide by 1 - rho e^{-2 pi i j / M}.
-        // The first pass's element t = k + r M/16 of thread k has its predecessor in
-        // thread k - 1 (the lane below), so only lane 0 loads it.
+        // transform dz_t = z_t - rho z_{t-1}, then divide by 1 - rho e^{-2 pi i j / M}
         auto ldw = [&](int t, int pi) {
-            const cplx<T> z = ld(t, pi);
-            cplx<T> zp = mk<T>(__shfl_up_sync(0xffffffffu, z.r, 1), __shfl_up_sync(0xffffffffu, z.i, 1));
-            if ((threadIdx.x & 31) == 0) zp = ld((t + M - 1) & (M - 1), pi);
+            const cplx<T> z = ld(t, pi), zp = ld((t + M - 1) & (M - 1), pi);
             return mk<T>(fmaf(-kPrewhiten, zp.r, z.r), fmaf(-kPrewhiten, zp.i, z.i));
         };
         auto stw = [&](int j, int, cplx<T> v) {

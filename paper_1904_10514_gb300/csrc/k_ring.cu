@@ -25,21 +25,18 @@ namespace hpx {
 
 constexpr int kRingThreads = 512;
 
-// The same step for the launches of one transform length N whose ring pairs
-// are all of one kind (BLUE: Bluestein rings of convolution length N; else
-// rings of N points): the FFT length, the thread count (N / 16, or N / 32 for
-// 16384) and the pass structure are compile-time constants (fft_ct.cuh), and
-// the kind of ring is known, so neither transform carries the other's code.
-// N is 2^k (from 4096) or, for the Bluestein rings of FP32 plans, the
-// smallest 3 2^k, 5 2^k or 7 2^k >= 2 nphi - 1 when that is shorter than the
-// power of two (a radix-3, 5 or 7 pass after the radix-16 passes): 2560..14336
-// points instead of 4096..16384.  tw[t] = e^{-2 pi i t / (twstep N)}.
-template <class T, int N, int NT, bool BLUE>
-__global__ void __launch_bounds__(NT, (NT <= 256 ? 4 : NT <= 512 ? 2 : 1)) ring_ct_kernel(
+// The same step for the launches of one transform length N = 2^LOGN >= 4096
+// whose ring pairs are all of one kind (BLUE: Bluestein rings of convolution
+// length N; else rings of N points): the FFT length, the thread count
+// (N / 16 or N / 32) and the pass structure are compile-time constants
+// (fft_ct.cuh), and the kind of ring is known, so neither transform carries
+// the other's code.
+template <class T, int LOGN, int NT, bool BLUE>
+__global__ void __launch_bounds__(NT, (LOGN <= 13 ? 1024 / NT : 1)) ring_ct_kernel(
     const T* __restrict__ maps, cplx<T>* __restrict__ Y, const int* __restrict__ nphi_t,
     const int* __restrict__ startN_t, const int* __restrict__ startS_t, const int64_t* __restrict__ shOff_t,
     const int64_t* __restrict__ chOff_t, const int64_t* __restrict__ bhOff_t, const cplx<T>* __restrict__ shift,
-    const cplx<T>* __restrict__ chirp, const cplx<T>* __restrict__ bhat, const cplx<T>* __restrict__ tw, int twstep,
+    const cplx<T>* __restrict__ chirp, const cplx<T>* __restrict__ bhat, const cplx<T>* __restrict__ tw, int twlen,
     int p, int Q, int64_t npix, const int* __restrict__ ringlist) {
     extern __shared__ unsigned char smem_raw[];
     cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw);
@@ -50,19 +47,20 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 4 : NT <= 512 ? 2 : 1)) ring_
     const bool equator = (sN == sS);
     const T* f = maps + (int64_t)b * npix;
     const int tid = threadIdx.x;
+    const int twstep = twlen >> LOGN;
     auto sample = [&](int k) { return mk<T>(f[sN + k], equator ? T(0) : f[sS + k]); };
     auto to_smem = [&](int, int pi, cplx<T> v) { buf[pi] = v; };
     if constexpr (!BLUE) {
-        ct::fft_n<T, N, NT, false, false>(buf, tw, twstep, [&](int k, int) { return sample(k); }, to_smem);
+        ct::fft<T, LOGN, NT, false, false>(buf, tw, twstep, [&](int k, int) { return sample(k); }, to_smem);
     } else {
         // Bluestein: chirped samples in, times the transformed kernel out; the
         // inverse transform applies the output chirp in its last pass
         const cplx<T>* ch = chirp + chOff_t[i];
         const cplx<T>* bh = bhat + bhOff_t[i];
-        ct::fft_n<T, N, NT, false, false>(
+        ct::fft<T, LOGN, NT, false, false>(
             buf, tw, twstep, [&](int k, int) { return k < n ? mul(sample(k), ch[k]) : mk<T>(T(0), T(0)); },
             [&](int j, int pi, cplx<T> v) { buf[pi] = mul(v, bh[j]); });
-        ct::fft_n<T, N, NT, true, true>(
+        ct::fft<T, LOGN, NT, true, true>(
             buf, tw, twstep, [&](int, int pi) { return buf[pi]; },
             [&](int j, int pi, cplx<T> v) { buf[pi] = j < n ? mul(v, ch[j]) : v; });
     }
@@ -232,51 +230,29 @@ void launch_ring_fft(const hpx_plan_s* P, const T* maps, cudaStream_t s) {
     // one launch per transform length (and kind, from 4096 points up), blocks
     // sized to it, longest first
     for (const auto& c : P->ringClasses) {
-        if (!c.ct) {
+        if (c.N < kRingCtMin) {
             launch(c.N, c.count, P->ringList + c.first);
             continue;
         }
         const size_t smem = (size_t)(c.N + c.N / 16) * sizeof(cplx<T>);
         dim3 grid(g.B, c.count);
-        // power-of-two lengths use the plan's twiddle table, the others their own
-        const cplx<T>* tw = c.twOff < 0 ? (const cplx<T>*)t.twid : (const cplx<T>*)t.twA + c.twOff;
-        const int twstep = c.twOff < 0 ? g.Lmax / c.N : 1;
         auto run = [&](auto kern, int threads) {
             cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             kern<<<grid, threads, smem, s>>>(maps, (cplx<T>*)P->Y, t.nphi, t.startN, t.startS, t.shOff, t.chOff,
-                                             t.bhOffA, (const cplx<T>*)t.shift, (const cplx<T>*)t.chirp,
-                                             (const cplx<T>*)t.bhatA, tw, twstep, g.p, g.Q,
+                                             t.bhOff, (const cplx<T>*)t.shift, (const cplx<T>*)t.chirp,
+                                             (const cplx<T>*)t.bhat, (const cplx<T>*)t.twid, g.Lmax, g.p, g.Q,
                                              g.npix, P->ringList + c.first);
         };
-#define HPX_RING_CT(NN, TT)                                          \
-    case NN:                                                         \
-        if (c.blue) run(ring_ct_kernel<T, NN, TT, true>, TT);        \
-        else run(ring_ct_kernel<T, NN, TT, false>, TT);              \
-        break;
-        switch (c.N) {
-            HPX_RING_CT(2560, 160)
-            HPX_RING_CT(3072, 192)
-            HPX_RING_CT(3584, 224)
-            HPX_RING_CT(4096, 256)
-            HPX_RING_CT(5120, 320)
-            HPX_RING_CT(6144, 384)
-            HPX_RING_CT(7168, 448)
-            HPX_RING_CT(8192, 512)
-            HPX_RING_CT(10240, 640)
-            HPX_RING_CT(12288, 768)
-            HPX_RING_CT(14336, 896)
-            HPX_RING_CT(16384, 512)
-            default: break;   // not a length of the compile-time kernels (the plan never groups one)
+        if (c.N == 4096) {
+            if (c.blue) run(ring_ct_kernel<T, 12, 256, true>, 256);
+            else run(ring_ct_kernel<T, 12, 256, false>, 256);
+        } else if (c.N == 8192) {
+            if (c.blue) run(ring_ct_kernel<T, 13, 512, true>, 512);
+            else run(ring_ct_kernel<T, 13, 512, false>, 512);
+        } else {
+            if (c.blue) run(ring_ct_kernel<T, 14, 512, true>, 512);
+            else run(ring_ct_kernel<T, 14, 512, false>, 512);
         }
-#undef HPX_RING_CT
-    }
-}
-
-bool ring_ct_length(int N) {
-    switch (N) {
-        case 2560: case 3072: case 3584: case 4096: case 5120: case 6144: case 7168: case 8192:
-        case 10240: case 12288: case 14336: case 16384: return true;
-        default: return false;
     }
 }
 

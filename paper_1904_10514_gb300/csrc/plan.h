@@ -17,8 +17,6 @@ struct DevTables {
     int *nphi = nullptr, *startN = nullptr, *startS = nullptr, *pow2 = nullptr, *logn = nullptr,
         *fftL = nullptr, *logL = nullptr;
     int64_t *shOff = nullptr, *chOff = nullptr, *bhOff = nullptr;
-    int64_t* bhOffA = nullptr;   // analysis Bluestein kernels (convolution lengths fftLa of plan_math.h)
-    void *bhatA = nullptr, *twA = nullptr;   // cplx<T>
     void *shift = nullptr, *chirp = nullptr, *bhat = nullptr, *twid = nullptr;   // cplx<T>
     int *poleN = nullptr, *poleS = nullptr;
     double* polew = nullptr;
@@ -28,6 +26,9 @@ struct DevTables {
     int* nstart = nullptr;                  // dense spreading table: first node per grid point
     void* swts = nullptr;                   // T [spreadE][M]
     int spreadE = 0;
+    int* tstart = nullptr;                  // interpolation (transpose of the half-grid spreading)
+    void* hwn = nullptr;                    // T [interpE][Q][2]
+    int interpE = 0, interpRows = 0, interpD = 0;
     int* hstart = nullptr;                  // half-grid spreading with folded mirrors
     void* hwts = nullptr;                   // T [spreadH][M/2 + 1][2]
     int spreadH = 0, spreadRows = 0, spreadD = 0;
@@ -72,9 +73,7 @@ struct hpx_plan_s {
     // Bluestein length): ring pairs ringList[first .. first + count - 1]
     struct RingClass {
         int N, first, count;
-        bool ct;       // compile-time kernel of length N (ring_ct_length): every ring of the class is
-        bool blue;     // ... a Bluestein ring (blue) or none is
-        int64_t twOff; // ct, N not a power of two: first twiddle of length N in twA; else -1
+        bool blue;   // N >= kRingCtMin: every ring of the class is a Bluestein ring (else none is)
     };
     std::vector<RingClass> ringClasses;
     int* ringList = nullptr;
@@ -133,10 +132,9 @@ struct hpx_plan_s {
 
 namespace hpx {
 
-// ring transform lengths with a compile-time kernel (fft_ct.cuh; 2^k from 4096
-// and the smooth Bluestein lengths 3, 5, 7 2^k of FP32 plans): their rings run in
-// launches of one length and one kind (plain or Bluestein)
-bool ring_ct_length(int N);
+// ring transforms of this many points or more run in launches of one length and
+// one kind (plain or Bluestein) with the compile-time FFT of fft_ct.cuh
+constexpr int kRingCtMin = 4096;
 
 template <class T> void launch_ring_fft(const hpx_plan_s* P, const T* maps, cudaStream_t s);
 template <class T> void launch_poles(const hpx_plan_s* P, const T* maps, cudaStream_t s);
@@ -167,6 +165,9 @@ __host__ __device__ inline int64_t tc_elem(int rp, int r, int k) {
 }
 // transpose of the analysis; wpos = weight of the m > 0 coefficients (2: the
 // adjoint under the real-map inner product, 1: under the plain Euclidean one)
+// type-2 latitude NUFFT of the adjoint and the synthesis in two kernels
+// (k_nufft2.cu); false where they do not apply (then nufft_adj_kernel runs)
+bool launch_nufft2(const hpx_plan_s* P, cudaStream_t s);
 template <class T> void launch_adjoint(const hpx_plan_s* P, const T* alm, T* maps, cudaStream_t s, T wpos = T(2));
 // ev: NULL, or kStages + 1 events recorded around its stages (profiling)
 template <class T>

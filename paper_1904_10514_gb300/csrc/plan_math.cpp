@@ -2,7 +2,6 @@
 #include "plan_math.h"
 
 #include <algorithm>
-#include <stdexcept>
 #include <cmath>
 #include <complex>
 #include <cstring>
@@ -45,47 +44,6 @@ void fft_host(std::vector<cd>& a) {
             }
         }
     }
-}
-
-// Forward DFT of any length whose prime factors are 2, 3, 5 or 7 (FP64,
-// recursive decimation in time; lengths up to 2^14 * 7 here).
-void fft_host_smooth(std::vector<cd>& a) {
-    const int n = (int)a.size();
-    if (n == 1) return;
-    int f = 0;
-    for (int c : {2, 3, 5, 7})
-        if (n % c == 0) { f = c; break; }
-    if (f == 0) throw std::runtime_error("fft_host_smooth: length with a prime factor above 7");
-    const int m = n / f;
-    std::vector<std::vector<cd>> sub(f, std::vector<cd>(m));
-    for (int k = 0; k < m; ++k)
-        for (int r = 0; r < f; ++r) sub[r][k] = a[(size_t)k * f + r];
-    for (int r = 0; r < f; ++r) fft_host_smooth(sub[r]);
-    for (int q = 0; q < n; ++q) {
-        cd acc(0.0, 0.0);
-        for (int r = 0; r < f; ++r) {
-            const long long e = ((long long)r * q) % n;
-            const double ang = -2.0 * kPi * (double)e / (double)n;
-            acc += sub[r][q % m] * cd(std::cos(ang), std::sin(ang));
-        }
-        a[q] = acc;
-    }
-}
-
-// The Bluestein convolution length of the compile-time ring kernels for a ring
-// of n points: the smallest L >= 2n - 1 of the form 2^k, 3 2^k, 5 2^k or 7 2^k
-// with 2560 <= L <= 16384 (lengths a kernel is instantiated for), else the power
-// of two the other ring kernels use.
-int smooth_bluestein_length(int n) {
-    const int need = 2 * n - 1;
-    int best = 1 << ilog2(need);
-    for (int r : {3, 5, 7}) {
-        int L = r;
-        while (L < need) L *= 2;
-        if (L < best) best = L;
-    }
-    if (best < 2560 || best > 16384) return 1 << ilog2(need);
-    return best;
 }
 
 // theta of north ring j (1-based, j <= 2 N_side), Eq. (healpts).
@@ -203,8 +161,7 @@ std::string build_tables(int nside, int lmax, bool fp64, PlanTables& t) {
     t.logn.resize(np); t.fftL.resize(np); t.logL.resize(np);
     t.shOff.resize(np); t.chOff.resize(np); t.bhOff.resize(np);
     std::vector<double> phi0(np), theta(np);
-    int64_t shN = 0, chN = 0, bhN = 0, bhNA = 0;
-    t.fftLa.clear(); t.bhOffA.clear(); t.smoothL.clear(); t.twAOff.clear(); t.twA.clear();
+    int64_t shN = 0, chN = 0, bhN = 0;
     int lmaxfft = 8 * ns;   // the latitude NUFFT grid
     t.smem_ring = 0;
     for (int i = 0; i < np; ++i) {
@@ -227,24 +184,7 @@ std::string build_tables(int nside, int lmax, bool fp64, PlanTables& t) {
         t.shOff[i] = shN; shN += n / 2 + 1;
         t.chOff[i] = chN; t.bhOff[i] = bhN;
         if (!t.pow2[i]) { chN += n; bhN += Lb; }
-        const int La = (!t.pow2[i] && !fp64) ? smooth_bluestein_length(n) : Lb;
-        t.fftLa.push_back(La);
-        t.bhOffA.push_back(bhNA);
-        if (!t.pow2[i]) bhNA += La;
-        if (!is_pow2(La) && std::find(t.smoothL.begin(), t.smoothL.end(), La) == t.smoothL.end())
-            t.smoothL.push_back(La);
     }
-    // e^{-2 pi i t / L}, t < L, for every smooth (non-power-of-two) length
-    std::sort(t.smoothL.begin(), t.smoothL.end());
-    for (int La : t.smoothL) {
-        t.twAOff.push_back((int64_t)t.twA.size() / 2);
-        for (int k = 0; k < La; ++k) {
-            const double ang = -2.0 * kPi * (double)k / (double)La;
-            t.twA.push_back(std::cos(ang));
-            t.twA.push_back(std::sin(ang));
-        }
-    }
-    t.bhatA.assign(2 * bhNA, 0.0);
     t.Lmax = lmaxfft;
     t.shift.assign(2 * shN, 0.0);
     t.chirp.assign(2 * chN, 0.0);
@@ -280,21 +220,6 @@ std::string build_tables(int nside, int lmax, bool fp64, PlanTables& t) {
             for (int k = 0; k < Lb; ++k) {
                 t.bhat[2 * (t.bhOff[i] + k)] = b[k].real() / Lb;
                 t.bhat[2 * (t.bhOff[i] + k) + 1] = b[k].imag() / Lb;
-            }
-            // the same kernel for the analysis ring kernels' convolution length
-            const int La = t.fftLa[i];
-            std::vector<cd> ba(La, cd(0.0, 0.0));
-            for (int k = 0; k < n; ++k) {
-                const long long r = ((long long)k * k) % (2LL * n);
-                const double ang = kPi * (double)r / (double)n;
-                ba[k] = cd(std::cos(ang), std::sin(ang));
-                if (k > 0) ba[La - k] = ba[k];
-            }
-            if (is_pow2(La)) fft_host(ba);
-            else fft_host_smooth(ba);
-            for (int k = 0; k < La; ++k) {
-                t.bhatA[2 * (t.bhOffA[i] + k)] = ba[k].real() / La;
-                t.bhatA[2 * (t.bhOffA[i] + k) + 1] = ba[k].imag() / La;
             }
         }
     }
@@ -472,6 +397,8 @@ std::string build_tables(int nside, int lmax, bool fp64, PlanTables& t) {
                 std::vector<int> tlo(Q, H + 1), thi(Q, -1);
                 for (int i = 0; i <= H; ++i)
                     for (int e = 0; e < E; ++e) {
+                        const size_t k = ((size_t)e * (H + 1) + i) * 2;
+                        if (t.hwts[k] == 0.0 && t.hwts[k + 1] == 0.0) continue;   // outside the kernel's support
                         const int r = t.hstart[i] + e;
                         tlo[r] = std::min(tlo[r], i);
                         thi[r] = std::max(thi[r], i);
@@ -498,6 +425,9 @@ std::string build_tables(int nside, int lmax, bool fp64, PlanTables& t) {
                 for (int r0 = 0; r0 < Q; r0 += 32)
                     rows32 = std::max(rows32, t.tstart[std::min(r0 + 31, Q - 1)] + En - t.tstart[r0]);
                 t.interpRows = rows32;
+                t.interpD = 0;   // spread of the run starts over 4 consecutive nodes (from r = 0, 4, 8, ..)
+                for (int r0 = 0; r0 < Q; r0 += 4)
+                    t.interpD = std::max(t.interpD, t.tstart[std::min(r0 + 3, Q - 1)] - t.tstart[r0]);
             }
 
             t.spreadD = 0;

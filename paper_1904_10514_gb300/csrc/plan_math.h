@@ -22,16 +22,6 @@ struct PlanTables {
     std::vector<double> shift;   // complex: (1/nphi) e^{-i m phi0}, Nyquist split folded in
     std::vector<double> chirp;   // complex: e^{-i pi k^2 / nphi} (Bluestein rings)
     std::vector<double> bhat;    // complex: FFT_L of the conjugate chirp, divided by L
-    // The analysis ring kernels of FP32 plans convolve at the smallest length
-    // 2^k, 3 2^k, 5 2^k or 7 2^k >= 2 nphi - 1 (2560..16384; else as fftL):
-    // fftLa per ring pair, its transformed kernel bhatA from bhOffA, and for
-    // every smooth length smoothL[c] the twiddles e^{-2 pi i t / L} from twAOff[c].
-    std::vector<int> fftLa;
-    std::vector<int64_t> bhOffA;
-    std::vector<double> bhatA;
-    std::vector<int> smoothL;
-    std::vector<int64_t> twAOff;
-    std::vector<double> twA;
     int Lmax = 0;                // twiddle table covers FFT lengths up to Lmax
     std::vector<double> twid;    // complex: e^{-2 pi i k / Lmax}, k < Lmax/2
     int smem_ring = 0;           // largest in-CTA FFT length of step 1
@@ -63,7 +53,7 @@ struct PlanTables {
     // node r takes the grid points tstart[r] .. tstart[r] + interpE - 1 with
     // weights hwn[e][r][2] (even m, odd m); interpRows bounds the grid points
     // that 32 consecutive nodes see.
-    int interpE = 0, interpRows = 0;
+    int interpE = 0, interpRows = 0, interpD = 0;
     std::vector<int> tstart;
     std::vector<double> hwn;     // [interpE][Q][2]
 

@@ -47,6 +47,11 @@ def test_traffic_scaled_for_captured_kernel():
     ratio = bench.TRAFFIC_OVER_ALGORITHMIC["fused_fsht"]
     assert roof["traffic"] == pytest.approx(work["fused_fsht"][1] * ratio)
     assert 1.0 <= ratio < 1.2                   # padding only: no re-reads
+    # the operator stage is compute-bound under the survey's accounting: the flops of D and the sweeps
+    assert roof["bound"] == "tensor"
+    flops = work["lat_solve"][1] + work["rot_sweep"][1]
+    assert roof["achieved"] == pytest.approx(flops / 2.4e-3 / 1e12)
+    assert roof["operator_stream"]["bytes"] == work["fused_fsht"][1]
 
 
 def test_fallback_peak_without_measurements():
