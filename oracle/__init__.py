@@ -32,6 +32,7 @@ geometry   HEALPix rings, Eq. (healpts)
 legendre   orthonormal associated Legendre functions and Y_l^m (Appendix A)
 hp2sph     Algorithm 1 step by step, C_l (Eq. APS)
 dense      dense analysis matrix A and its transpose at small Nside
+healpix    the HEALPix software analysis of Sec. 2.2 (equal weights, Jacobi iteration)
 """
 
-from . import geometry, legendre, hp2sph, dense  # noqa: F401
+from . import geometry, legendre, hp2sph, dense, healpix  # noqa: F401

@@ -464,3 +464,49 @@ def test_synthesis_then_analysis_exact_subspace():
         a[hp2sph.alm_index(l, 1, L)] = rng.standard_normal() + 1j * rng.standard_normal()
     back = hp2sph.analyze(hp2sph.synthesize(a, ns, L), ns, L)
     np.testing.assert_allclose(back, a, atol=1e-12)
+
+
+# ---------------------------------------------------------------- Sec. 2.2 (HEALPix software analysis)
+def test_equal_weight_matches_brute_force_scipy():
+    """Eq. (healsph): (4 pi / N) sum_i conj(Y_l^m(x_i)) f_i, against scipy's Y_l^m at every
+    pixel of Nside 2 (a plain double loop)."""
+    from scipy.special import sph_harm_y
+    from oracle import healpix
+    ns, L = 2, 4
+    rng = np.random.default_rng(1)
+    f = rng.standard_normal(geometry.npix(ns))
+    a = healpix.equal_weight(f, ns, L)
+    th, ph = geometry.pixel_angles(ns)
+    for m in range(L + 1):
+        for l in range(m, L + 1):
+            ref = 4 * np.pi / f.size * np.sum(np.conj(sph_harm_y(l, m, th, ph)) * f)
+            assert abs(a[hp2sph.alm_index(l, m, L)] - ref) < 1e-14
+
+
+def test_equal_weight_is_scaled_adjoint_of_synthesis():
+    """A = (4 pi / N) S^*: <S a, f> = (N / 4 pi) <a, A f> with the real-map coefficient
+    inner product (weight 2 for m > 0), S being the pinned synthesis of Eq. (synthesis)."""
+    from oracle import healpix
+    ns, L = 8, 16
+    rng = np.random.default_rng(2)
+    f = rng.standard_normal(geometry.npix(ns))
+    a = rng.standard_normal(hp2sph.n_alm(L)) + 1j * rng.standard_normal(hp2sph.n_alm(L))
+    lhs = float(np.dot(f, hp2sph.synthesize(a, ns, L)))
+    rhs = dense.alm_dot(a, healpix.equal_weight(f, ns, L) * geometry.npix(ns) / (4 * np.pi), L)
+    assert abs(lhs - rhs) < 1e-11 * abs(lhs)
+
+
+def test_jacobi_converges_to_band_limited_coefficients():
+    """Eq. (richardson) is Richardson iteration on the normal equations: for a map
+    synthesised from coefficients of degree <= Nside (S of full column rank) it converges
+    to those coefficients, the error shrinking by more than 10x per iteration here."""
+    from oracle import healpix
+    ns, L = 8, 8
+    rng = np.random.default_rng(3)
+    at = rng.standard_normal(hp2sph.n_alm(L)) + 1j * rng.standard_normal(hp2sph.n_alm(L))
+    for l in range(L + 1):
+        at[hp2sph.alm_index(l, 0, L)] = at[hp2sph.alm_index(l, 0, L)].real
+    f = hp2sph.synthesize(at, ns, L)
+    errs = [np.abs(healpix.jacobi(f, ns, L, k) - at).max() for k in (0, 1, 2, 3)]
+    assert all(errs[k + 1] < 0.1 * errs[k] for k in range(3)), errs
+    assert np.abs(healpix.jacobi(f, ns, L, 12) - at).max() < 1e-12
