@@ -100,6 +100,10 @@ extern "C" {
  *   operators; implies HPX_FLAG_SWEEPS.  Stops at a relative residual of 1e-7
  *   (FP32) or 1e-14 (FP64). */
 #define HPX_FLAG_CG 64u
+/* HPX_FLAG_JACOBI: also allocate the workspace of hpx_healpix_analysis (one map
+ *   buffer and one coefficient buffer of the batch); implies HPX_FLAG_SYNTHESIS.
+ *   Uniform plans only (else HPX_ERR_ARG). */
+#define HPX_FLAG_JACOBI 128u
 
 typedef struct hpx_plan_s hpx_plan_s;
 
@@ -108,7 +112,7 @@ typedef struct hpx_plan_desc {
     int lmax;         /* largest degree returned, 0 <= lmax <= 2 nside; -1 = 2 nside */
     int batch;        /* number of maps processed per call, >= 1                  */
     int precision;    /* HPX_FP32 or HPX_FP64                                     */
-    unsigned flags;   /* HPX_FLAG_* (SWEEPS, GRAPH, SIMT, CHECKED, AUTOTUNE, SYNTHESIS, CG), or 0 */
+    unsigned flags;   /* HPX_FLAG_* (SWEEPS, GRAPH, SIMT, CHECKED, AUTOTUNE, SYNTHESIS, CG, JACOBI), or 0 */
     /* Uneven batches: NULL, or `batch` values giving the nside of every map
      * (then `nside` is ignored).  Maps, coefficients and spectra are then
      * concatenated in the given order: map i occupies 12 nside_i^2 elements of
@@ -184,6 +188,23 @@ int hpx_analyze_vjp(hpx_plan_s* plan, const void* galm, void* gmaps);
  * Uneven batches: alm, gcl and galm concatenated as for hpx_cl.  galm may not
  * alias alm.  Asynchronous. */
 int hpx_cl_vjp(hpx_plan_s* plan, const void* alm, const double* gcl, void* galm);
+
+/* The transpose of hpx_sh_synthesis with respect to the library's real inner
+ * products (maps: sum_i f_i g_i; coefficients: weight 2 for m > 0):
+ *     alm_l^m = sum_i conj(Y_l^m(x_i)) f(x_i),   m >= 0,
+ * the unweighted pixel sum of Eq. (healsph) (Sec. 2.2).  maps -> alm in the
+ * plan's layouts; requires a uniform plan made with HPX_FLAG_SYNTHESIS (else
+ * HPX_ERR_STATE).  Asynchronous. */
+int hpx_sh_synthesis_adjoint(hpx_plan_s* plan, const void* maps, void* alm);
+
+/* The analysis of the HEALPix software that the paper compares HP2SPH with
+ * (Sec. 2.2): the equal-weight quadrature of Eq. (healsph),
+ * a = (4 pi / N) S^* f, followed by `niter` steps of the Jacobi (Richardson)
+ * iteration of Eqs. (uzawa) / (richardson), a <- a + (4 pi / N) S^* (f - S a),
+ * S = hpx_sh_synthesis (the software's default is niter = 3).  maps -> alm in the
+ * plan's layouts; requires a plan made with HPX_FLAG_JACOBI (else
+ * HPX_ERR_STATE); 0 <= niter <= 1000.  Asynchronous. */
+int hpx_healpix_analysis(hpx_plan_s* plan, const void* maps, void* alm, int niter);
 
 /* Angular power spectrum of Eq. (APS) for real maps,
  * C_l = (|a_l0|^2 + 2 sum_{m=1}^{l} |a_lm|^2) / (2l + 1),

@@ -33,7 +33,7 @@ EXPORTS = ["hpx_plan", "hpx_plan_ex", "hpx_set_stream", "hpx_analyze", "hpx_synt
            "hpx_sync", "hpx_destroy", "hpx_npix", "hpx_nalm", "hpx_plan_lmax", "hpx_plan_bytes",
            "hpx_last_error", "hpx_strerror", "hpx_set_profiling", "hpx_stage_times",
            "hpx_analyze_noalloc", "hpx_plan_flags", "hpx_selftest_timeout", "hpx_sh_synthesis", "hpx_plan_launches",
-           "hpx_analyze_vjp", "hpx_cl_vjp"]
+           "hpx_analyze_vjp", "hpx_cl_vjp", "hpx_sh_synthesis_adjoint", "hpx_healpix_analysis"]
 HPX_FLAG_SWEEPS = 1
 HPX_FLAG_GRAPH = 2
 HPX_FLAG_SIMT = 4
@@ -41,6 +41,7 @@ HPX_FLAG_CHECKED = 8
 HPX_FLAG_AUTOTUNE = 16
 HPX_FLAG_SYNTHESIS = 32
 HPX_FLAG_CG = 64
+HPX_FLAG_JACOBI = 128
 HPX_ERR_NONFINITE = -8
 HPX_NOALLOC_MAX_NSIDE = 128
 HPX_NSTAGES = 6
@@ -107,6 +108,8 @@ def lib():
             "hpx_sh_synthesis": (i32, [vp, vp, vp]),
             "hpx_plan_launches": (i32, [vp]),
             "hpx_analyze_vjp": (i32, [vp, vp, vp]),
+            "hpx_sh_synthesis_adjoint": (i32, [vp, vp, vp]),
+            "hpx_healpix_analysis": (i32, [vp, vp, vp, i32]),
             "hpx_cl_vjp": (i32, [vp, vp, vp, vp]),
             "hpx_stage_times": (i32, [vp, ctypes.POINTER(ctypes.c_float), i32, ctypes.POINTER(ctypes.c_int)]),
         }
@@ -210,7 +213,7 @@ class Plan:
     """Owns one C plan; tensors must live on the plan's CUDA device."""
 
     def __init__(self, nside=None, lmax=-1, batch=1, precision="fp32", sweeps=False, graph=False, nsides=None,
-                 simt=False, lmaxs=None, checked=False, autotune=False, synthesis=False, cg=False):
+                 simt=False, lmaxs=None, checked=False, autotune=False, synthesis=False, cg=False, jacobi=False):
         """Uniform batch (nside, batch), or uneven batch (nsides = nside of every map
         and/or lmaxs = lmax of every map; maps, alm and C_l are then 1-D tensors
         holding the maps concatenated)."""
@@ -231,7 +234,7 @@ class Plan:
         flags = ((HPX_FLAG_SWEEPS if sweeps else 0) | (HPX_FLAG_GRAPH if graph else 0) |
                  (HPX_FLAG_SIMT if simt else 0) | (HPX_FLAG_CHECKED if checked else 0) |
                  (HPX_FLAG_AUTOTUNE if autotune else 0) | (HPX_FLAG_SYNTHESIS if synthesis else 0) |
-                 (HPX_FLAG_CG if cg else 0))
+                 (HPX_FLAG_CG if cg else 0) | (HPX_FLAG_JACOBI if jacobi else 0))
         h = hpx_plan_ex(self.nside, lmax, self.batch, self.precision, flags, self.nsides, self.lmaxs)
         if not h:
             raise HpxError(hpx_last_error(), "hpx_plan_ex")
@@ -322,6 +325,28 @@ class Plan:
             out = self.torch.empty(self._shape(self.npix), dtype=self.rdtype, device=alm.device)
         self._stream()
         self._check(lib().hpx_sh_synthesis(self.handle, alm.data_ptr(), out.data_ptr()), "hpx_sh_synthesis")
+        return out
+
+    def sh_synthesis_adjoint(self, maps, out=None):
+        """sum_i conj(Y_lm(x_i)) f_i (the transpose of sh_synthesis; plan made with synthesis=True):
+        maps (batch, npix) -> alm (batch, n_alm)."""
+        maps = self._maps(maps)
+        if out is None:
+            out = self.torch.empty(self._shape(self.nalm), dtype=self.cdtype, device=maps.device)
+        self._stream()
+        self._check(lib().hpx_sh_synthesis_adjoint(self.handle, maps.data_ptr(), out.data_ptr()),
+                    "hpx_sh_synthesis_adjoint")
+        return out
+
+    def healpix_analysis(self, maps, niter=3, out=None):
+        """The HEALPix software's analysis (equal weights + niter Jacobi steps; plan made with
+        jacobi=True): maps (batch, npix) -> alm (batch, n_alm)."""
+        maps = self._maps(maps)
+        if out is None:
+            out = self.torch.empty(self._shape(self.nalm), dtype=self.cdtype, device=maps.device)
+        self._stream()
+        self._check(lib().hpx_healpix_analysis(self.handle, maps.data_ptr(), out.data_ptr(), int(niter)),
+                    "hpx_healpix_analysis")
         return out
 
     def cl(self, alm, out=None):

@@ -69,7 +69,8 @@ void free_plan(hpx_plan_s* P) {
     void* ptrs[] = {t.nphi, t.startN, t.startS, t.pow2, t.logn, t.fftL, t.logL, t.shOff, t.chOff,
                     t.bhOff, t.shift, t.chirp, t.bhat, t.twid, t.poleN, t.poleS, t.polew, t.rowptr,
                     t.ent, t.entw, t.dec, t.D, t.tstart, t.hwn, t.angOff, t.ang, t.skOff, t.skew, t.skewT, t.nrowptr, t.nent, t.nentw, t.nstart, t.swts, t.hstart, t.hwts, t.Es, t.shifted, t.C, t.cgH, P->Y, P->U, P->bvec,
-                    P->fusedM, P->fusedOff, P->fusedTiles, P->tcOff, P->tcFirst, P->tcRinv, P->bscale, P->d_status, P->synM, P->ringList};
+                    P->fusedM, P->fusedOff, P->fusedTiles, P->tcOff, P->tcFirst, P->tcRinv, P->bscale, P->d_status, P->synM, P->ringList,
+                    P->jres, P->jalm};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     if (P->ev) {
@@ -129,10 +130,29 @@ extern "C" {
 hpx_plan_s* hpx_plan_ex(const hpx_plan_desc* d) {
     if (!d) { set_err(HPX_ERR_ARG); return nullptr; }
     if ((d->flags & ~(unsigned)(HPX_FLAG_SWEEPS | HPX_FLAG_GRAPH | HPX_FLAG_SIMT | HPX_FLAG_CHECKED |
-                                HPX_FLAG_AUTOTUNE | HPX_FLAG_SYNTHESIS | HPX_FLAG_CG)) != 0 ||
+                                HPX_FLAG_AUTOTUNE | HPX_FLAG_SYNTHESIS | HPX_FLAG_CG | HPX_FLAG_JACOBI)) != 0 ||
         d->batch < 1) {
         set_err(HPX_ERR_ARG);
         return nullptr;
+    }
+    if (d->flags & HPX_FLAG_JACOBI) {   // the Jacobi iteration needs the synthesis
+        hpx_plan_desc dj = *d;
+        dj.flags = (d->flags & ~HPX_FLAG_JACOBI) | HPX_FLAG_SYNTHESIS;
+        if (d->nsides || d->lmaxs) { set_err(HPX_ERR_ARG); return nullptr; }   // uniform plans only
+        hpx_plan_s* P = hpx_plan_ex(&dj);
+        if (!P) return nullptr;
+        const size_t es = d->precision == HPX_FP64 ? 8 : 4;
+        if (cudaMalloc(&P->jres, (size_t)P->g.B * P->g.npix * es) != cudaSuccess ||
+            cudaMalloc(&P->jalm, (size_t)P->g.B * P->g.nalm * 2 * es) != cudaSuccess) {
+            cudaGetLastError();
+            free_plan(P);
+            set_err(HPX_ERR_OOM);
+            return nullptr;
+        }
+        P->bytes += (int64_t)((size_t)P->g.B * P->g.npix * es + (size_t)P->g.B * P->g.nalm * 2 * es);
+        P->flags |= HPX_FLAG_JACOBI;
+        set_err(HPX_OK);
+        return P;
     }
     if (d->precision != HPX_FP32 && d->precision != HPX_FP64) { set_err(HPX_ERR_ARG); return nullptr; }
     if (d->nsides || d->lmaxs) {
@@ -551,6 +571,30 @@ int hpx_sh_synthesis(hpx_plan_s* P, const void* alm, void* maps) {
         hpx::launch_sh_synthesis<double>(P, (const double*)alm, (double*)maps, P->stream, ev);
     else
         hpx::launch_sh_synthesis<float>(P, (const float*)alm, (float*)maps, P->stream, ev);
+    if (cudaGetLastError() != cudaSuccess) return set_err(HPX_ERR_CUDA);
+    return set_err(HPX_OK);
+}
+
+int hpx_sh_synthesis_adjoint(hpx_plan_s* P, const void* maps, void* alm) {
+    if (!P || !alm || !maps) return set_err(HPX_ERR_ARG);
+    if (P->group || !(P->flags & HPX_FLAG_SYNTHESIS)) return set_err(HPX_ERR_STATE);
+    if ((P->flags & HPX_FLAG_CHECKED) && (!device_pointer(P, maps) || !device_pointer(P, alm)))
+        return set_err(HPX_ERR_ARG);
+    if (P->precision == HPX_FP64) hpx::launch_sh_adjoint<double>(P, (const double*)maps, (double*)alm, P->stream, 1.0);
+    else hpx::launch_sh_adjoint<float>(P, (const float*)maps, (float*)alm, P->stream, 1.0f);
+    if (cudaGetLastError() != cudaSuccess) return set_err(HPX_ERR_CUDA);
+    return set_err(HPX_OK);
+}
+
+int hpx_healpix_analysis(hpx_plan_s* P, const void* maps, void* alm, int niter) {
+    if (!P || !alm || !maps || niter < 0 || niter > 1000) return set_err(HPX_ERR_ARG);
+    if (P->group || !(P->flags & HPX_FLAG_JACOBI)) return set_err(HPX_ERR_STATE);
+    if ((P->flags & HPX_FLAG_CHECKED) && (!device_pointer(P, maps) || !device_pointer(P, alm)))
+        return set_err(HPX_ERR_ARG);
+    if (P->precision == HPX_FP64)
+        hpx::launch_healpix_jacobi<double>(P, (const double*)maps, (double*)alm, niter, P->stream);
+    else
+        hpx::launch_healpix_jacobi<float>(P, (const float*)maps, (float*)alm, niter, P->stream);
     if (cudaGetLastError() != cudaSuccess) return set_err(HPX_ERR_CUDA);
     return set_err(HPX_OK);
 }

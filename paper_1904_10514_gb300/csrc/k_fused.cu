@@ -280,22 +280,23 @@ template void launch_synth_apply<double>(const hpx_plan_s*, const double*, cudaS
 int fused_tile_rows(int B) { return B > 8 ? 128 : (B > 2 ? 256 : 512); }
 
 template <class T>
-void launch_fused(const hpx_plan_s* P, T* alm, cudaStream_t s) {
+void launch_fused(const hpx_plan_s* P, T* alm, cudaStream_t s, const void* Mrows) {
     const auto& g = P->g;
     const int ldm = P->fused_ldm;
+    const T* M = (const T*)(Mrows ? Mrows : P->fusedM);
     if (g.B > 8) {
         dim3 grid(P->fused_ntiles, (g.B + 31) / 32);
-        fused_apply_kernel<T, 16, 16><<<grid, 256, 0, s>>>((const T*)P->fusedM, P->fusedOff, P->fusedTiles,
+        fused_apply_kernel<T, 16, 16><<<grid, 256, 0, s>>>(M, P->fusedOff, P->fusedTiles,
                                                            (const cplx<T>*)P->bvec, (cplx<T>*)alm, g.P2, ldm,
                                                            g.p, g.L, g.B, g.nalm);
     } else if (g.B > 2) {
         dim3 grid(P->fused_ntiles, (g.B + 7) / 8);
-        fused_apply_kernel<T, 32, 4><<<grid, 128, 0, s>>>((const T*)P->fusedM, P->fusedOff, P->fusedTiles,
+        fused_apply_kernel<T, 32, 4><<<grid, 128, 0, s>>>(M, P->fusedOff, P->fusedTiles,
                                                           (const cplx<T>*)P->bvec, (cplx<T>*)alm, g.P2, ldm,
                                                           g.p, g.L, g.B, g.nalm);
     } else {
         dim3 grid(P->fused_ntiles, (g.B + 1) / 2);
-        fused_apply_kernel<T, 64, 1><<<grid, 64, 0, s>>>((const T*)P->fusedM, P->fusedOff, P->fusedTiles,
+        fused_apply_kernel<T, 64, 1><<<grid, 64, 0, s>>>(M, P->fusedOff, P->fusedTiles,
                                                          (const cplx<T>*)P->bvec, (cplx<T>*)alm, g.P2, ldm,
                                                          g.p, g.L, g.B, g.nalm);
     }
@@ -326,8 +327,8 @@ int build_fused(hpx_plan_s* P, const double* D64, const cplx<double>* skew64, cu
     return e == cudaSuccess ? 0 : -1;
 }
 
-template void launch_fused<float>(const hpx_plan_s*, float*, cudaStream_t);
-template void launch_fused<double>(const hpx_plan_s*, double*, cudaStream_t);
+template void launch_fused<float>(const hpx_plan_s*, float*, cudaStream_t, const void*);
+template void launch_fused<double>(const hpx_plan_s*, double*, cudaStream_t, const void*);
 template int build_fused<float>(hpx_plan_s*, const double*, const cplx<double>*, cudaStream_t, void*, bool);
 template int build_fused<double>(hpx_plan_s*, const double*, const cplx<double>*, cudaStream_t, void*, bool);
 

@@ -25,6 +25,50 @@ namespace hpx {
 
 constexpr int kRingThreads = 512;
 
+// Output rows of step 1 from the ring pair's DFT (z = DFT of f_N + i f_S, n
+// points, element k at buf[pad(k)]).
+//   ew == 0 (the analysis, Sec. 3.1): c_m = c~_m e^{-i m phi0} for m <= n/2 with the
+//     Nyquist split, 0 above (table ph = (1/n) e^{-i m phi0} with that split folded in).
+//   ew != 0 (the transpose of the synthesis' ring stage, used by the equal-weight
+//     quadrature of Sec. 2.2): for every m <= L the ring's Fourier sum
+//     D_m = sum_k f_k e^{-i m lambda_k} (m taken mod n, so the polar rings alias),
+//     weighted like the synthesis folds the orders (1/2 at m = 0, 1 for even m,
+//     2 for odd m) and scaled by ew; 0 for L < m <= p.
+template <class T, class BUF>
+__device__ __forceinline__ void ring_rows_out(BUF zat, int n, int p, int L, const cplx<T>* __restrict__ ph, bool sh,
+                                              T ew, cplx<T>* rowN, cplx<T>* rowS, bool equator, int tid, int nt) {
+    const int h = n >> 1;
+    for (int m = tid; m <= p; m += nt) {
+        cplx<T> cN = mk<T>(T(0), T(0)), cS = cN;
+        if (ew == T(0) ? m <= h : m <= L) {
+            const int k = m % n;
+            const cplx<T> zm = zat(k);
+            const cplx<T> zc = conjg(zat(k == 0 ? 0 : n - k));
+            const cplx<T> fn = scale(add(zm, zc), T(0.5));              // n * c~_m (north)
+            const cplx<T> d = sub(zm, zc);
+            const cplx<T> fs = mk<T>(T(0.5) * d.i, T(-0.5) * d.r);      // n * c~_m (south)
+            cplx<T> w;
+            if (ew == T(0)) {
+                w = ph[m];
+            } else {
+                const T wm = ew * (m == 0 ? T(0.5) : (m & 1) ? T(2) : T(1));
+                if (sh) {   // e^{-i m pi / n}
+                    T sn, cs;
+                    if constexpr (sizeof(T) == 4) sincospif(-(float)(m % (2 * n)) / (float)n, &sn, &cs);
+                    else sincospi(-(double)(m % (2 * n)) / (double)n, &sn, &cs);
+                    w = mk<T>(wm * cs, wm * sn);
+                } else {
+                    w = mk<T>(wm, T(0));
+                }
+            }
+            cN = mul(fn, w);
+            cS = mul(fs, w);
+        }
+        rowN[m] = cN;
+        if (!equator) rowS[m] = cS;
+    }
+}
+
 // The same step for the launches of one transform length N = 2^LOGN >= 4096
 // whose ring pairs are all of one kind (BLUE: Bluestein rings of convolution
 // length N; else rings of N points): the FFT length, the thread count
@@ -37,7 +81,7 @@ __global__ void __launch_bounds__(NT, (LOGN <= 13 ? 1024 / NT : 1)) ring_ct_kern
     const int* __restrict__ startN_t, const int* __restrict__ startS_t, const int64_t* __restrict__ shOff_t,
     const int64_t* __restrict__ chOff_t, const int64_t* __restrict__ bhOff_t, const cplx<T>* __restrict__ shift,
     const cplx<T>* __restrict__ chirp, const cplx<T>* __restrict__ bhat, const cplx<T>* __restrict__ tw, int twlen,
-    int p, int Q, int64_t npix, const int* __restrict__ ringlist) {
+    int p, int Q, int64_t npix, const int* __restrict__ ringlist, T ew, const int* __restrict__ shifted_t, int L) {
     extern __shared__ unsigned char smem_raw[];
     cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw);
     const int i = ringlist[blockIdx.y];
@@ -64,25 +108,10 @@ __global__ void __launch_bounds__(NT, (LOGN <= 13 ? 1024 / NT : 1)) ring_ct_kern
             buf, tw, twstep, [&](int, int pi) { return buf[pi]; },
             [&](int j, int pi, cplx<T> v) { buf[pi] = j < n ? mul(v, ch[j]) : v; });
     }
-    const int h = n >> 1;
-    const cplx<T>* ph = shift + shOff_t[i];
     cplx<T>* rowN = Y + ((int64_t)b * Q + (i + 1)) * (p + 1);
     cplx<T>* rowS = Y + ((int64_t)b * Q + (Q - 2 - i)) * (p + 1);
-    for (int m = tid; m <= p; m += NT) {
-        cplx<T> cN = mk<T>(T(0), T(0)), cS = cN;
-        if (m <= h) {
-            const cplx<T> zm = buf[ct::padc(m)];
-            const cplx<T> zc = conjg(buf[ct::padc(m == 0 ? 0 : n - m)]);
-            const cplx<T> fn = scale(add(zm, zc), T(0.5));              // n * c~_m (north)
-            const cplx<T> d = sub(zm, zc);
-            const cplx<T> fs = mk<T>(T(0.5) * d.i, T(-0.5) * d.r);      // n * c~_m (south)
-            const cplx<T> w = ph[m];
-            cN = mul(fn, w);
-            cS = mul(fs, w);
-        }
-        rowN[m] = cN;
-        if (!equator) rowS[m] = cS;
-    }
+    ring_rows_out<T>([&](int k) { return buf[ct::padc(k)]; }, n, p, L, shift + shOff_t[i], shifted_t[i] != 0, ew,
+                     rowN, rowS, equator, tid, NT);
 }
 
 template <class T, int E>
@@ -94,7 +123,7 @@ __global__ void __launch_bounds__(kRingThreads, (E <= 16 ? 2 : 1)) ring_fft_kern
     const int64_t* __restrict__ chOff_t, const int64_t* __restrict__ bhOff_t,
     const cplx<T>* __restrict__ shift, const cplx<T>* __restrict__ chirp,
     const cplx<T>* __restrict__ bhat, const cplx<T>* __restrict__ tw, int twlen, int p, int Q,
-    int64_t npix, int npairs, const int* __restrict__ ringlist) {
+    int64_t npix, int npairs, const int* __restrict__ ringlist, T ew, const int* __restrict__ shifted_t, int L) {
     extern __shared__ unsigned char smem_raw[];
     cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw);
     // largest rings first: blockIdx.y = 0 is the equator
@@ -147,25 +176,10 @@ __global__ void __launch_bounds__(kRingThreads, (E <= 16 ? 2 : 1)) ring_fft_kern
         __syncthreads();
     }
 
-    const int h = n >> 1;
-    const cplx<T>* ph = shift + shOff_t[i];
     cplx<T>* rowN = Y + ((int64_t)b * Q + (i + 1)) * (p + 1);
     cplx<T>* rowS = Y + ((int64_t)b * Q + (Q - 2 - i)) * (p + 1);
-    for (int m = tid; m <= p; m += nt) {
-        cplx<T> cN = mk<T>(T(0), T(0)), cS = cN;
-        if (m <= h) {
-            const cplx<T> zm = buf[pad(m)];
-            const cplx<T> zc = conjg(buf[pad(m == 0 ? 0 : n - m)]);
-            const cplx<T> fn = scale(add(zm, zc), T(0.5));              // n * c~_m (north)
-            const cplx<T> d = sub(zm, zc);
-            const cplx<T> fs = mk<T>(T(0.5) * d.i, T(-0.5) * d.r);      // n * c~_m (south)
-            const cplx<T> w = ph[m];
-            cN = mul(fn, w);
-            cS = mul(fs, w);
-        }
-        rowN[m] = cN;
-        if (!equator) rowS[m] = cS;
-    }
+    ring_rows_out<T>([&](int k) { return buf[pad(k)]; }, n, p, L, shift + shOff_t[i], shifted_t[i] != 0, ew, rowN,
+                     rowS, equator, tid, nt);
 }
 
 // Pole values (Sec. 3.2.1): a fixed linear functional of the samples of the
@@ -207,7 +221,7 @@ __global__ void pole_kernel(const T* __restrict__ maps, cplx<T>* __restrict__ Y,
 }
 
 template <class T>
-void launch_ring_fft(const hpx_plan_s* P, const T* maps, cudaStream_t s) {
+void launch_ring_fft(const hpx_plan_s* P, const T* maps, cudaStream_t s, T ew) {
     const auto& g = P->g;
     const auto& t = P->t;
     auto launch = [&](int N, int nrings, const int* list) {
@@ -221,7 +235,7 @@ void launch_ring_fft(const hpx_plan_s* P, const T* maps, cudaStream_t s) {
         kern<<<grid, threads, smem, s>>>(
             maps, (cplx<T>*)P->Y, t.nphi, t.startN, t.startS, t.pow2, t.logn, t.fftL, t.logL, t.shOff,
             t.chOff, t.bhOff, (const cplx<T>*)t.shift, (const cplx<T>*)t.chirp, (const cplx<T>*)t.bhat,
-            (const cplx<T>*)t.twid, g.Lmax, g.p, g.Q, g.npix, g.npairs, list);
+            (const cplx<T>*)t.twid, g.Lmax, g.p, g.Q, g.npix, g.npairs, list, ew, t.shifted, g.L);
     };
     if (!P->ringList) {   // one launch sized for the largest transform
         launch(g.smem_ring, g.npairs, nullptr);
@@ -241,7 +255,7 @@ void launch_ring_fft(const hpx_plan_s* P, const T* maps, cudaStream_t s) {
             kern<<<grid, threads, smem, s>>>(maps, (cplx<T>*)P->Y, t.nphi, t.startN, t.startS, t.shOff, t.chOff,
                                              t.bhOff, (const cplx<T>*)t.shift, (const cplx<T>*)t.chirp,
                                              (const cplx<T>*)t.bhat, (const cplx<T>*)t.twid, g.Lmax, g.p, g.Q,
-                                             g.npix, P->ringList + c.first);
+                                             g.npix, P->ringList + c.first, ew, t.shifted, g.L);
         };
         if (c.N == 4096) {
             if (c.blue) run(ring_ct_kernel<T, 12, 256, true>, 256);
@@ -263,8 +277,8 @@ void launch_poles(const hpx_plan_s* P, const T* maps, cudaStream_t s) {
                                        P->t.npole, g.p, g.Q, g.npix);
 }
 
-template void launch_ring_fft<float>(const hpx_plan_s*, const float*, cudaStream_t);
-template void launch_ring_fft<double>(const hpx_plan_s*, const double*, cudaStream_t);
+template void launch_ring_fft<float>(const hpx_plan_s*, const float*, cudaStream_t, float);
+template void launch_ring_fft<double>(const hpx_plan_s*, const double*, cudaStream_t, double);
 template void launch_poles<float>(const hpx_plan_s*, const float*, cudaStream_t);
 template void launch_poles<double>(const hpx_plan_s*, const double*, cudaStream_t);
 

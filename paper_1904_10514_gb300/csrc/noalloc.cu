@@ -38,7 +38,7 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Offsets {
     size_t nphi, startN, startS, pow2, logn, fftL, logL, shOff, chOff, bhOff, shift, chirp, bhat, twid,
-        poleN, poleS, polew, rowptr, ent, entw, dec, D, angOff, ang, skOff, skew, nstart, swts;
+        poleN, poleS, polew, rowptr, ent, entw, dec, D, angOff, ang, skOff, skew, nstart, swts, shifted;
     size_t Y, bvec;
     int npole;
 };
@@ -123,6 +123,7 @@ extern "C" int hpx_analyze_noalloc(int nside, int lmax, const float* maps, float
             o.dec = img.real(tb.dec); o.D = img.real(tb.D); o.angOff = img.vec(tb.angOff); o.ang = img.real(tb.ang);
             o.skOff = img.vec(tb.skOff); o.skew = img.real(tb.skew); st.nq = tb.nq;
             o.nstart = img.vec(tb.nstart); o.swts = img.real(tb.swts); st.spreadE = tb.spreadE;
+            o.shifted = img.vec(tb.shifted);
         } catch (const std::bad_alloc&) {   // no exception leaves the C interface
             return fail(HPX_ERR_OOM);
         } catch (...) {
@@ -161,6 +162,7 @@ extern "C" int hpx_analyze_noalloc(int nside, int lmax, const float* maps, float
     t.angOff = (int64_t*)(b + o.angOff); t.ang = b + o.ang;
     t.skOff = (int64_t*)(b + o.skOff); t.skew = b + o.skew; t.nq = st.nq;
     t.nstart = (int*)(b + o.nstart); t.swts = b + o.swts; t.spreadE = st.spreadE;
+    t.shifted = (int*)(b + o.shifted);
     P.g = st.geo;
     P.precision = HPX_FP32;
     P.device = dev;

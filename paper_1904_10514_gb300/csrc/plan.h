@@ -102,6 +102,8 @@ struct hpx_plan_s {
     int* d_status = nullptr;       // device status word (timed-out waits, non-finite inputs)
     int64_t fused_bytes = 0;       // bytes of M
     void* synM = nullptr;          // T, n_alm x ldm row-major: synthesis operators R_{m,c} Es (HPX_FLAG_SYNTHESIS)
+    void* jres = nullptr;          // T [B][npix]: Jacobi residual maps (HPX_FLAG_JACOBI)
+    void* jalm = nullptr;          // cplx<T> [B][n_alm]: Jacobi update
     float tuned_ms[2] = {0.f, 0.f};   // HPX_FLAG_AUTOTUNE: ms per analysis, operators / sweeps
 
     // uneven batches (group plans): one uniform sub-plan per distinct nside
@@ -136,7 +138,9 @@ namespace hpx {
 // one kind (plain or Bluestein) with the compile-time FFT of fft_ct.cuh
 constexpr int kRingCtMin = 4096;
 
-template <class T> void launch_ring_fft(const hpx_plan_s* P, const T* maps, cudaStream_t s);
+// ew != 0: the rows of the equal-weight quadrature's ring stage (every m <= lmax,
+// aliased mod nphi, synthesis fold weights, times ew) instead of the analysis'
+template <class T> void launch_ring_fft(const hpx_plan_s* P, const T* maps, cudaStream_t s, T ew = T(0));
 template <class T> void launch_poles(const hpx_plan_s* P, const T* maps, cudaStream_t s);
 template <class T> void launch_nufft(const hpx_plan_s* P, cudaStream_t s);
 template <class T> void launch_spread(const hpx_plan_s* P, cudaStream_t s);
@@ -146,7 +150,13 @@ template <class T> void launch_dense(const hpx_plan_s* P, cudaStream_t s, const 
 template <class T> void launch_cg(const hpx_plan_s* P, cudaStream_t s);
 template <class T> void launch_rot(const hpx_plan_s* P, T* alm, cudaStream_t s);
 int fused_tile_rows(int B);
-template <class T> void launch_fused(const hpx_plan_s* P, T* alm, cudaStream_t s);
+// per-order operators on the FP32 pipes; Mrows: row-major operators of the
+// layout of fusedM's SIMT form (NULL = fusedM), e.g. the synthesis operators synM
+template <class T> void launch_fused(const hpx_plan_s* P, T* alm, cudaStream_t s, const void* Mrows = nullptr);
+// S^T of the spherical-harmonic synthesis times `scale` (maps -> alm) and the
+// Jacobi-refined equal-weight analysis of the HEALPix software (k_healpix.cu)
+template <class T> void launch_sh_adjoint(const hpx_plan_s* P, const T* maps, T* alm, cudaStream_t s, T scale);
+template <class T> void launch_healpix_jacobi(const hpx_plan_s* P, const T* maps, T* alm, int niter, cudaStream_t s);
 void launch_fused_tc(const hpx_plan_s* P, float* alm, cudaStream_t s);
 // after build_fused<float> of the tensor-core layout: converts M to the form
 // launch_fused_tc reads (and allocates its scale arrays); 0 on success

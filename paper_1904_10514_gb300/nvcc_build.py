@@ -12,7 +12,7 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhpx.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
-SOURCES = ["plan_math.cpp", "capi.cu", "k_ring.cu", "k_nufft.cu", "k_dense.cu", "k_rot.cu", "k_cl.cu", "k_adjoint.cu", "k_fused.cu", "k_fused_tc.cu", "group.cu", "k_cg.cu", "noalloc.cu", "k_nufft2.cu"]
+SOURCES = ["plan_math.cpp", "capi.cu", "k_ring.cu", "k_nufft.cu", "k_dense.cu", "k_rot.cu", "k_cl.cu", "k_adjoint.cu", "k_fused.cu", "k_fused_tc.cu", "group.cu", "k_cg.cu", "noalloc.cu", "k_nufft2.cu", "k_healpix.cu"]
 
 
 def _compile(src, extra):

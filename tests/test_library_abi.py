@@ -63,7 +63,7 @@ def test_invalid_arguments_rejected_before_any_cuda_call(hp):
 
 
 def test_descriptor_fields_rejected_before_any_cuda_call(hp):
-    assert not hp.hpx_plan_ex(8, -1, 1, hp.HPX_FP32, 128)                 # unknown flag
+    assert not hp.hpx_plan_ex(8, -1, 1, hp.HPX_FP32, 1 << 10)             # unknown flag
     assert hp.hpx_last_error() == hp.HPX_ERR_ARG
     assert not hp.hpx_plan_ex(8, -1, 2, hp.HPX_FP32, 0, None, [16, 17])   # lmax_1 > 2 nside
     assert hp.hpx_last_error() == hp.HPX_ERR_LMAX
