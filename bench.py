@@ -548,7 +548,7 @@ def main():
 
     # spherical-harmonic synthesis of the same batch (the inverse direction): alm -> maps
     t_syn0 = time.perf_counter()
-    plan_syn = hp.Plan(NSIDE, LMAX, nb, "fp32", synthesis=True)
+    plan_syn = hp.Plan(NSIDE, LMAX, nb, "fp32", jacobi=True)   # synthesis + the Jacobi workspace
     torch.cuda.synchronize()
     syn_build_s = time.perf_counter() - t_syn0
     maps_syn = torch.empty_like(maps)
@@ -570,8 +570,23 @@ def main():
                                           for k, n in enumerate(hp.STAGES_SYNTH) if n != "unused"},
                  "plan_build_s": syn_build_s,
                  "path": "per-order synthesis operators" if plan_syn.flags & hp.HPX_FLAG_SWEEPS == 0 else "sweeps"}
+    # the HEALPix software's analysis (Sec. 2.2), the paper's comparison method: equal-weight
+    # quadrature (niter = 0) and with the default 3 Jacobi iterations, same batch
+    healpix_sw = {}
+    alm_hs = torch.empty_like(alm)
+    for niter in (0, 3):
+        plan_syn.healpix_analysis(maps, niter=niter, out=alm_hs)
+        torch.cuda.synchronize()
+        nh = 3
+        e0.record(stream)
+        for _ in range(nh):
+            plan_syn.healpix_analysis(maps, niter=niter, out=alm_hs)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        th = e0.elapsed_time(e1) / nh / 1e3
+        healpix_sw["niter_%d" % niter] = {"value": npix_step / th / 1e9, "unit": "Gpix/s", "ms_per_step": th * 1e3}
     plan_syn.close()
-    del maps_syn
+    del maps_syn, alm_hs
 
     # ablation: the paper's form of the latitude solve (CG on the normal equations per
     # column) with the run-time sweeps, same batch
@@ -696,6 +711,7 @@ def main():
             "config": config_dict(), "roofline": roof, "roofline_stages": per_stage, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": (hp.lib().hpx_plan_launches(plan.handle) + 1) * args.steps, "clocks": clk, "fp64_single_map": fp64, "sh_synthesis_fp32": synthesis, "ablation_cg_latitude_solve": cg,
             "sweeps_path": sweeps, "uneven_batch_200": uneven, "differentiation_nside2048x8": diffw,
+            "healpix_software_analysis": healpix_sw,
             "fp32_batched_over_fp64_single": value / world / fp64["value"],
             "stages_ms_per_launch": per_launch, "plan_build_s": plan_build_s, "plan_gb": plan.nbytes / 1e9,
             "plan_path": "sweeps" if plan.flags & hp.HPX_FLAG_SWEEPS else "per-order operators"}

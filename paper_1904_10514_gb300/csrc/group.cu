@@ -34,10 +34,30 @@ __global__ void segment_copy_kernel(const unsigned char* __restrict__ src, unsig
 
 namespace {
 
-void seg_copy(const hpx_plan_s* P, int s, const void* src, void* dst, const int64_t* off, int64_t seg, bool gather) {
+void seg_copy(const hpx_plan_s* P, int s, const void* src, void* dst, const int64_t* off, int64_t seg, bool gather,
+              cudaStream_t st) {
     dim3 grid((unsigned)std::min<int64_t>((seg / 8 + 255) / 256, 1024), P->sub_count[s]);
-    segment_copy_kernel<<<grid, 256, 0, P->stream>>>((const unsigned char*)src, (unsigned char*)dst,
-                                                     P->d_idx + P->sub_first[s], off, seg, gather);
+    segment_copy_kernel<<<grid, 256, 0, st>>>((const unsigned char*)src, (unsigned char*)dst,
+                                              P->d_idx + P->sub_first[s], off, seg, gather);
+}
+void seg_copy(const hpx_plan_s* P, int s, const void* src, void* dst, const int64_t* off, int64_t seg, bool gather) {
+    seg_copy(P, s, src, dst, off, seg, gather, P->stream);
+}
+
+// The sub-plans of an analysis run concurrently: each on a stream of its own
+// that waits for the group's stream (fork), and the group's stream waits for all
+// of them (join).  Under stream capture (HPX_FLAG_GRAPH) this becomes one graph
+// with a branch per sub-plan.
+void fork(hpx_plan_s* G) { cudaEventRecord(G->sfork, G->stream); }
+cudaStream_t branch(hpx_plan_s* G, size_t s) {
+    cudaStreamWaitEvent(G->sstreams[s], G->sfork, 0);
+    return G->sstreams[s];
+}
+void join(hpx_plan_s* G) {
+    for (size_t s = 0; s < G->subs.size(); ++s) {
+        cudaEventRecord(G->sjoin[s], G->sstreams[s]);
+        cudaStreamWaitEvent(G->stream, G->sjoin[s], 0);
+    }
 }
 
 int64_t nalm_of(int L) { return (int64_t)(L + 1) * (L + 2) / 2; }
@@ -90,6 +110,11 @@ hpx_plan_s* group_create(const hpx_plan_desc* d, int* err) {
         byNside[{ns, L}].push_back(i);
     }
     G->total_npix = om;
+    if (cudaEventCreateWithFlags(&G->sfork, cudaEventDisableTiming) != cudaSuccess) {
+        *err = HPX_ERR_CUDA;
+        delete G;
+        return nullptr;
+    }
     G->total_nalm = oa;
     G->total_ncl = oc;
     G->g = Geometry{};
@@ -113,6 +138,16 @@ hpx_plan_s* group_create(const hpx_plan_desc* d, int* err) {
         hpx_plan_s* S = hpx_plan_ex(&sd);
         if (!S) { *err = hpx_last_error(); ok = false; break; }
         G->subs.push_back(S);
+        cudaStream_t st = nullptr;
+        cudaEvent_t ev = nullptr;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+            *err = HPX_ERR_CUDA;
+            ok = false;
+        }
+        G->sstreams.push_back(st);
+        G->sjoin.push_back(ev);
+        if (!ok) break;
         G->bytes += S->bytes;
         G->sub_count.push_back((int)maps.size());
         G->sub_first.push_back((int)idx.size());
@@ -168,7 +203,14 @@ hpx_plan_s* group_create(const hpx_plan_desc* d, int* err) {
 }
 
 void group_free(hpx_plan_s* G) {
+    for (cudaStream_t st : G->sstreams)
+        if (st) cudaStreamSynchronize(st);
     for (hpx_plan_s* S : G->subs) hpx_destroy(S);
+    for (cudaStream_t st : G->sstreams)
+        if (st) cudaStreamDestroy(st);
+    for (cudaEvent_t ev : G->sjoin)
+        if (ev) cudaEventDestroy(ev);
+    if (G->sfork) cudaEventDestroy(G->sfork);
     for (void* q : G->stage_maps) if (q) cudaFree(q);
     for (void* q : G->stage_alm) if (q) cudaFree(q);
     for (void* q : G->stage_cl) if (q) cudaFree(q);
@@ -182,21 +224,24 @@ void group_free(hpx_plan_s* G) {
 }
 
 int group_analyze(hpx_plan_s* G, const void* maps, void* alm) {
-    for (size_t s = 0; s < G->subs.size(); ++s) {
+    fork(G);
+    int rc = HPX_OK;
+    for (size_t s = 0; s < G->subs.size() && rc == HPX_OK; ++s) {
         hpx_plan_s* S = G->subs[s];
-        hpx_set_stream(S, G->stream);
+        const cudaStream_t st = branch(G, s);
+        hpx_set_stream(S, st);
         const size_t es = G->precision == HPX_FP64 ? 8 : 4;
         if (G->sub_inplace[s]) {
-            const int rc = hpx_analyze(S, (const unsigned char*)maps + G->sub_mapoff[s],
-                                       (unsigned char*)alm + G->sub_almoff[s]);
-            if (rc != HPX_OK) return rc;
+            rc = hpx_analyze(S, (const unsigned char*)maps + G->sub_mapoff[s], (unsigned char*)alm + G->sub_almoff[s]);
         } else {
-            seg_copy(G, (int)s, maps, G->stage_maps[s], G->d_mapoff, S->g.npix * (int64_t)es, true);
-            const int rc = hpx_analyze(S, G->stage_maps[s], G->stage_alm[s]);
-            if (rc != HPX_OK) return rc;
-            seg_copy(G, (int)s, G->stage_alm[s], alm, G->d_almoff, S->g.nalm * (int64_t)es * 2, false);
+            seg_copy(G, (int)s, maps, G->stage_maps[s], G->d_mapoff, S->g.npix * (int64_t)es, true, st);
+            rc = hpx_analyze(S, G->stage_maps[s], G->stage_alm[s]);
+            if (rc == HPX_OK)
+                seg_copy(G, (int)s, G->stage_alm[s], alm, G->d_almoff, S->g.nalm * (int64_t)es * 2, false, st);
         }
     }
+    join(G);   // also after an error: every branch rejoins the group's stream
+    if (rc != HPX_OK) return rc;
     return cudaGetLastError() == cudaSuccess ? HPX_OK : HPX_ERR_CUDA;
 }
 

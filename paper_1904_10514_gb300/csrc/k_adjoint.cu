@@ -233,10 +233,11 @@ __global__ void __launch_bounds__(256) ring_adj_kernel(
     const int* __restrict__ logn_t, const int* __restrict__ fftL_t, const int* __restrict__ logL_t,
     const int64_t* __restrict__ shOff_t, const int64_t* __restrict__ chOff_t, const int64_t* __restrict__ bhOff_t,
     const cplx<T>* __restrict__ shift, const cplx<T>* __restrict__ chirp, const cplx<T>* __restrict__ bhat,
-    const cplx<T>* __restrict__ tw, int twlen, int p, int Q, int64_t npix, int npairs) {
+    const cplx<T>* __restrict__ tw, int twlen, int p, int Q, int64_t npix, int npairs,
+    const int* __restrict__ ringlist) {
     extern __shared__ unsigned char smem_raw[];
     cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw);
-    const int i = npairs - 1 - (int)blockIdx.x;
+    const int i = ringlist ? ringlist[blockIdx.x] : npairs - 1 - (int)blockIdx.x;
     const int b = blockIdx.y;
     const int n = nphi_t[i], h = n >> 1;
     const int sN = startN_t[i], sS = startS_t[i];
@@ -305,6 +306,103 @@ __global__ void pole_adj_kernel(const cplx<T>* __restrict__ Y, T* __restrict__ m
     }
 }
 
+// ring_adj_kernel for the ring classes of 4096 points and more, with the
+// compile-time FFT: the first pass reads the Hermitian extension X of each ring
+// pair straight from the rows of Y.
+template <class T, int LOGN, int NT, bool BLUE>
+__global__ void __launch_bounds__(NT, (LOGN <= 13 ? 1024 / NT : 1)) ring_adj_ct_kernel(
+    const cplx<T>* __restrict__ Y, T* __restrict__ maps, const int* __restrict__ nphi_t,
+    const int* __restrict__ startN_t, const int* __restrict__ startS_t, const int64_t* __restrict__ shOff_t,
+    const int64_t* __restrict__ chOff_t, const int64_t* __restrict__ bhOff_t, const cplx<T>* __restrict__ shift,
+    const cplx<T>* __restrict__ chirp, const cplx<T>* __restrict__ bhat, const cplx<T>* __restrict__ tw, int twlen,
+    int p, int Q, int64_t npix, const int* __restrict__ ringlist) {
+    extern __shared__ unsigned char smem_raw[];
+    cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw);
+    const int i = ringlist[blockIdx.y];
+    const int b = blockIdx.x;
+    const int n = nphi_t[i], h = n >> 1;
+    const int sN = startN_t[i], sS = startS_t[i];
+    const bool equator = (sN == sS);
+    const int tid = threadIdx.x;
+    const int twstep = twlen >> LOGN;
+    const cplx<T>* ph = shift + shOff_t[i];
+    const cplx<T>* rowN = Y + ((int64_t)b * Q + (i + 1)) * (p + 1);
+    const cplx<T>* rowS = Y + ((int64_t)b * Q + (Q - 2 - i)) * (p + 1);
+    // X_k = H_N + i H_S, H the Hermitian extension of z_m = conj(ph_m) y_m (k < n)
+    auto X = [&](int k) {
+        const int m = k <= h ? k : n - k;
+        const cplx<T> w = conjg(ph[m]);
+        const cplx<T> zn = mul(w, rowN[m]);
+        const cplx<T> zs = equator ? mk<T>(T(0), T(0)) : mul(w, rowS[m]);
+        if (m == 0 || m == h) return mk<T>(zn.r, zs.r);
+        if (k <= h) return mk<T>(T(0.5) * (zn.r - zs.i), T(0.5) * (zn.i + zs.r));   // zn/2 + i zs/2
+        return mk<T>(T(0.5) * (zn.r + zs.i), T(0.5) * (-zn.i + zs.r));              // conj(zn)/2 + i conj(zs)/2
+    };
+    auto to_smem = [&](int, int pi, cplx<T> v) { buf[pi] = v; };
+    if constexpr (!BLUE) {
+        ct::fft<T, LOGN, NT, true, false>(buf, tw, twstep, [&](int k, int) { return X(k); }, to_smem);
+    } else {
+        // inverse DFT of length n via Bluestein: transform conj(X) forward with the chirp
+        const cplx<T>* ch = chirp + chOff_t[i];
+        const cplx<T>* bh = bhat + bhOff_t[i];
+        ct::fft<T, LOGN, NT, false, false>(
+            buf, tw, twstep, [&](int k, int) { return k < n ? mul(conjg(X(k)), ch[k]) : mk<T>(T(0), T(0)); },
+            [&](int j, int pi, cplx<T> v) { buf[pi] = mul(v, bh[j]); });
+        ct::fft<T, LOGN, NT, true, true>(
+            buf, tw, twstep, [&](int, int pi) { return buf[pi]; },
+            [&](int j, int pi, cplx<T> v) { buf[pi] = j < n ? conjg(mul(v, ch[j])) : v; });
+    }
+    T* f = maps + (int64_t)b * npix;
+    for (int k = tid; k < n; k += NT) {
+        const cplx<T> v = buf[ct::padc(k)];
+        f[sN + k] = v.r;
+        if (!equator) f[sS + k] = v.i;
+    }
+}
+
+template <class T>
+void launch_ring_adj(const hpx_plan_s* P, T* maps, cudaStream_t s) {
+    const auto& g = P->g;
+    const auto& t = P->t;
+    auto old = [&](int blocks, size_t smem, const int* list) {
+        cudaFuncSetAttribute(ring_adj_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        dim3 grid(blocks, g.B);
+        ring_adj_kernel<T><<<grid, 256, smem, s>>>(
+            (const cplx<T>*)P->Y, maps, t.nphi, t.startN, t.startS, t.pow2, t.logn, t.fftL, t.logL, t.shOff,
+            t.chOff, t.bhOff, (const cplx<T>*)t.shift, (const cplx<T>*)t.chirp, (const cplx<T>*)t.bhat,
+            (const cplx<T>*)t.twid, g.Lmax, g.p, g.Q, g.npix, g.npairs, list);
+    };
+    if (!P->ringList) {
+        old(g.npairs, (size_t)g.smem_ring * sizeof(cplx<T>), nullptr);
+        return;
+    }
+    for (const auto& c : P->ringClasses) {
+        if (c.N < kRingCtMin) {
+            old(c.count, (size_t)c.N * sizeof(cplx<T>), P->ringList + c.first);
+            continue;
+        }
+        const size_t smem = (size_t)(c.N + c.N / 16) * sizeof(cplx<T>);
+        dim3 grid(g.B, c.count);
+        auto run = [&](auto kern, int threads) {
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            kern<<<grid, threads, smem, s>>>((const cplx<T>*)P->Y, maps, t.nphi, t.startN, t.startS, t.shOff,
+                                             t.chOff, t.bhOff, (const cplx<T>*)t.shift, (const cplx<T>*)t.chirp,
+                                             (const cplx<T>*)t.bhat, (const cplx<T>*)t.twid, g.Lmax, g.p, g.Q,
+                                             g.npix, P->ringList + c.first);
+        };
+        if (c.N == 4096) {
+            if (c.blue) run(ring_adj_ct_kernel<T, 12, 256, true>, 256);
+            else run(ring_adj_ct_kernel<T, 12, 256, false>, 256);
+        } else if (c.N == 8192) {
+            if (c.blue) run(ring_adj_ct_kernel<T, 13, 512, true>, 512);
+            else run(ring_adj_ct_kernel<T, 13, 512, false>, 512);
+        } else {
+            if (c.blue) run(ring_adj_ct_kernel<T, 14, 512, true>, 512);
+            else run(ring_adj_ct_kernel<T, 14, 512, false>, 512);
+        }
+    }
+}
+
 template <class T>
 void launch_adjoint(const hpx_plan_s* P, const T* alm, T* maps, cudaStream_t s, T wpos) {
     const auto& g = P->g;
@@ -337,13 +435,7 @@ void launch_adjoint(const hpx_plan_s* P, const T* alm, T* maps, cudaStream_t s, 
                                                     g.Lmax, g.M, logM, g.p, g.Q, g.P2);
     }
     {
-        const size_t smem = (size_t)g.smem_ring * sizeof(cplx<T>);
-        cudaFuncSetAttribute(ring_adj_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        dim3 grid(g.npairs, g.B);
-        ring_adj_kernel<T><<<grid, 256, smem, s>>>(
-            (const cplx<T>*)P->Y, maps, t.nphi, t.startN, t.startS, t.pow2, t.logn, t.fftL, t.logL, t.shOff,
-            t.chOff, t.bhOff, (const cplx<T>*)t.shift, (const cplx<T>*)t.chirp, (const cplx<T>*)t.bhat,
-            (const cplx<T>*)t.twid, g.Lmax, g.p, g.Q, g.npix, g.npairs);
+        launch_ring_adj<T>(P, maps, s);
         pole_adj_kernel<T><<<g.B, 128, 0, s>>>((const cplx<T>*)P->Y, maps, t.poleN, t.poleS, t.polew, t.npole,
                                                g.p, g.Q, g.npix);
     }

@@ -120,6 +120,9 @@ struct hpx_plan_s {
     int64_t* d_clel = nullptr;
     int* d_lmax = nullptr;                   // lmax of map i
     std::vector<void*> stage_maps, stage_alm, stage_cl;   // per sub-plan staging (gathered runs)
+    std::vector<cudaStream_t> sstreams;      // per sub-plan stream (concurrent branches of an analysis)
+    std::vector<cudaEvent_t> sjoin;          // per sub-plan join event
+    cudaEvent_t sfork = nullptr;             // fork event on the group's stream
     int64_t total_npix = 0, total_nalm = 0, total_ncl = 0;
 
     // CUDA graphs of hpx_analyze (HPX_FLAG_GRAPH)
