@@ -81,12 +81,12 @@ void free_plan(hpx_plan_s* P) {
 }
 
 template <class T>
-int analyze_impl(hpx_plan_s* P, const void* maps, void* alm) {
+int analyze_impl(hpx_plan_s* P, const void* maps, void* alm, bool rings = true) {
     cudaStream_t s = P->stream;
     cudaEvent_t* ev = nullptr;
     if (P->prof && P->nprof < hpx_plan_s::kMaxProf) ev = P->ev + (size_t)P->nprof++ * (hpx_plan_s::kStages + 1);
     if (ev) cudaEventRecord(ev[0], s);
-    hpx::launch_ring_fft<T>(P, (const T*)maps, s);
+    if (rings) hpx::launch_ring_fft<T>(P, (const T*)maps, s);
     if (ev) cudaEventRecord(ev[1], s);
     hpx::launch_poles<T>(P, (const T*)maps, s);
     if (ev) cudaEventRecord(ev[2], s);
@@ -120,6 +120,13 @@ int analyze_impl(hpx_plan_s* P, const void* maps, void* alm) {
 }  // namespace
 
 int hpx_internal_set_error(int code) { return set_err(code); }
+
+namespace hpx {
+int analyze_after_rings(hpx_plan_s* P, const void* maps, void* alm) {
+    return P->precision == HPX_FP64 ? analyze_impl<double>(P, maps, alm, false)
+                                    : analyze_impl<float>(P, maps, alm, false);
+}
+}  // namespace hpx
 
 namespace {
 int autotune(hpx_plan_s* P);
@@ -159,6 +166,12 @@ hpx_plan_s* hpx_plan_ex(const hpx_plan_desc* d) {
         int err = HPX_OK;
         hpx_plan_s* G = hpx::group_create(d, &err);
         if (!G) { set_err(err); return nullptr; }
+        if (!hpx::group_build_ring_list(G)) {
+            cudaGetLastError();
+            free_plan(G);
+            set_err(HPX_ERR_OOM);
+            return nullptr;
+        }
         if (cudaMalloc(&G->d_status, sizeof(int)) != cudaSuccess) {
             free_plan(G);
             set_err(HPX_ERR_OOM);
@@ -676,9 +689,9 @@ int hpx_plan_flags(const hpx_plan_s* P) { return P ? (int)P->flags : -1; }
 
 int hpx_plan_launches(const hpx_plan_s* P) {
     if (!P) return -1;
-    if (P->group) {
-        int n = 0;
-        for (const hpx_plan_s* S : P->subs) n += hpx_plan_launches(S);
+    if (P->group) {   // one persistent ring launch, then each sub-plan's other stages
+        int n = 1;
+        for (const hpx_plan_s* S : P->subs) n += hpx_plan_launches(S) - (S->ringList ? (int)S->ringClasses.size() : 1);
         for (size_t s = 0; s < P->subs.size(); ++s) n += P->sub_inplace[s] ? 0 : 2;   // gather + scatter
         return n;
     }

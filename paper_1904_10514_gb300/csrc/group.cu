@@ -211,6 +211,8 @@ void group_free(hpx_plan_s* G) {
     for (cudaEvent_t ev : G->sjoin)
         if (ev) cudaEventDestroy(ev);
     if (G->sfork) cudaEventDestroy(G->sfork);
+    if (G->ringJobs) cudaFree(G->ringJobs);
+    if (G->ringItems) cudaFree(G->ringItems);
     for (void* q : G->stage_maps) if (q) cudaFree(q);
     for (void* q : G->stage_alm) if (q) cudaFree(q);
     for (void* q : G->stage_cl) if (q) cudaFree(q);
@@ -223,19 +225,32 @@ void group_free(hpx_plan_s* G) {
     if (G->d_lmax) cudaFree(G->d_lmax);
 }
 
+// An uneven analysis: the gathers of the sub-plans whose maps are not adjacent,
+// then the ring stage of every map of every Nside in one persistent launch (the
+// work list of build_ring_list), then the remaining stages of each sub-plan as
+// concurrent branches, each ending with its scatter.
 int group_analyze(hpx_plan_s* G, const void* maps, void* alm) {
+    const size_t es = G->precision == HPX_FP64 ? 8 : 4;
+    for (size_t s = 0; s < G->subs.size(); ++s)
+        if (!G->sub_inplace[s])
+            seg_copy(G, (int)s, maps, G->stage_maps[s], G->d_mapoff, G->subs[s]->g.npix * (int64_t)es, true);
+    if (G->precision == HPX_FP64)
+        launch_ring_list<double>((const RingJob<double>*)G->ringJobs, G->ringItems, G->nRingItems, G->ringMaxN,
+                                 G->ringBlocks, (const double*)maps, G->stream);
+    else
+        launch_ring_list<float>((const RingJob<float>*)G->ringJobs, G->ringItems, G->nRingItems, G->ringMaxN,
+                                G->ringBlocks, (const float*)maps, G->stream);
     fork(G);
     int rc = HPX_OK;
     for (size_t s = 0; s < G->subs.size() && rc == HPX_OK; ++s) {
         hpx_plan_s* S = G->subs[s];
         const cudaStream_t st = branch(G, s);
         hpx_set_stream(S, st);
-        const size_t es = G->precision == HPX_FP64 ? 8 : 4;
         if (G->sub_inplace[s]) {
-            rc = hpx_analyze(S, (const unsigned char*)maps + G->sub_mapoff[s], (unsigned char*)alm + G->sub_almoff[s]);
+            rc = analyze_after_rings(S, (const unsigned char*)maps + G->sub_mapoff[s],
+                                     (unsigned char*)alm + G->sub_almoff[s]);
         } else {
-            seg_copy(G, (int)s, maps, G->stage_maps[s], G->d_mapoff, S->g.npix * (int64_t)es, true, st);
-            rc = hpx_analyze(S, G->stage_maps[s], G->stage_alm[s]);
+            rc = analyze_after_rings(S, G->stage_maps[s], G->stage_alm[s]);
             if (rc == HPX_OK)
                 seg_copy(G, (int)s, G->stage_alm[s], alm, G->d_almoff, S->g.nalm * (int64_t)es * 2, false, st);
         }
@@ -276,23 +291,75 @@ int group_sh_synthesis(hpx_plan_s* G, const void* alm, void* maps) {
     return group_alm_to_maps(G, alm, maps, hpx_sh_synthesis);
 }
 
+// every map of the batch in one launch, located through the per-map tables
 int group_cl(hpx_plan_s* G, const void* alm, double* cl) {
+    if (G->precision == HPX_FP64) launch_cl<double>(G, (const double*)alm, cl, G->stream);
+    else launch_cl<float>(G, (const float*)alm, cl, G->stream);
+    return cudaGetLastError() == cudaSuccess ? HPX_OK : HPX_ERR_CUDA;
+}
+
+namespace {
+// The work list of the persistent ring kernel: (sub-plan, ring pair, map) for
+// every map of the batch, longest transforms first, and the job table of the
+// sub-plans (their tables, Y workspaces and where their maps are).
+template <class T>
+bool build_ring_list(hpx_plan_s* G) {
+    const size_t es = sizeof(T);
+    std::vector<RingJob<T>> jobs;
+    struct Item {
+        int len, s, i, b;
+    };
+    std::vector<Item> items;
+    int maxN = 0;
     for (size_t s = 0; s < G->subs.size(); ++s) {
-        hpx_plan_s* S = G->subs[s];
-        hpx_set_stream(S, G->stream);
-        const size_t es = G->precision == HPX_FP64 ? 8 : 4;
-        if (G->sub_inplace[s]) {
-            const int rc = hpx_cl(S, (const unsigned char*)alm + G->sub_almoff[s],
-                                  (double*)((unsigned char*)cl + G->sub_cloff[s]));
-            if (rc != HPX_OK) return rc;
-        } else {
-            seg_copy(G, (int)s, alm, G->stage_alm[s], G->d_almoff, S->g.nalm * (int64_t)es * 2, true);
-            const int rc = hpx_cl(S, G->stage_alm[s], (double*)G->stage_cl[s]);
-            if (rc != HPX_OK) return rc;
-            seg_copy(G, (int)s, G->stage_cl[s], cl, G->d_cloff, (S->g.L + 1) * 8, false);
+        const hpx_plan_s* S = G->subs[s];
+        const auto& t = S->t;
+        RingJob<T> J;
+        J.staged = G->sub_inplace[s] ? nullptr : (const T*)G->stage_maps[s];
+        J.mapoff = G->sub_mapoff[s] / (int64_t)es;
+        J.Y = (cplx<T>*)S->Y;
+        J.nphi = t.nphi; J.startN = t.startN; J.startS = t.startS; J.pow2 = t.pow2; J.logn = t.logn;
+        J.fftL = t.fftL; J.logL = t.logL; J.shifted = t.shifted;
+        J.shOff = t.shOff; J.chOff = t.chOff; J.bhOff = t.bhOff;
+        J.shift = (const cplx<T>*)t.shift; J.chirp = (const cplx<T>*)t.chirp; J.bhat = (const cplx<T>*)t.bhat;
+        J.tw = (const cplx<T>*)t.twid;
+        J.twlen = S->g.Lmax; J.p = S->g.p; J.Q = S->g.Q; J.L = S->g.L; J.npix = S->g.npix;
+        jobs.push_back(J);
+        // transform length of every ring pair, from the host copy of the geometry
+        const int ns = S->g.ns;
+        for (int i = 0; i < S->g.npairs; ++i) {
+            const int j = i + 1;
+            const int n = (j < ns) ? 4 * j : 4 * ns;
+            int len = n;
+            if (n & (n - 1)) {   // Bluestein: the power of two >= 2 n - 1
+                len = 1;
+                while (len < 2 * n - 1) len <<= 1;
+            }
+            maxN = std::max(maxN, len);
+            for (int b = 0; b < G->sub_count[s]; ++b) items.push_back({len, (int)s, i, b});
         }
     }
-    return cudaGetLastError() == cudaSuccess ? HPX_OK : HPX_ERR_CUDA;
+    std::stable_sort(items.begin(), items.end(), [](const Item& a, const Item& b) { return a.len > b.len; });
+    std::vector<int4> packed(items.size());
+    for (size_t k = 0; k < items.size(); ++k) packed[k] = make_int4(items[k].s, items[k].i, items[k].b, items[k].len);
+    if (cudaMalloc(&G->ringJobs, jobs.size() * sizeof(RingJob<T>)) != cudaSuccess ||
+        cudaMalloc(&G->ringItems, packed.size() * sizeof(int4)) != cudaSuccess)
+        return false;
+    cudaMemcpy(G->ringJobs, jobs.data(), jobs.size() * sizeof(RingJob<T>), cudaMemcpyHostToDevice);
+    cudaMemcpy(G->ringItems, packed.data(), packed.size() * sizeof(int4), cudaMemcpyHostToDevice);
+    G->nRingItems = (int)packed.size();
+    G->ringMaxN = maxN;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    // resident blocks of 512 threads: two per SM (registers), one above 8192 points (shared memory)
+    G->ringBlocks = sms * (maxN > 8192 ? 1 : 2);
+    return true;
+}
+}  // namespace
+
+bool group_build_ring_list(hpx_plan_s* G) {
+    return G->precision == HPX_FP64 ? build_ring_list<double>(G) : build_ring_list<float>(G);
 }
 
 }  // namespace hpx

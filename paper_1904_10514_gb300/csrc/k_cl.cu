@@ -26,14 +26,20 @@ __device__ __forceinline__ void neumaier(double& s, double& comp, double v) {
 constexpr int kSlices = 8;
 }  // namespace
 
+// almoff / cloff / lmax: per-map element offsets and degrees of a concatenated
+// uneven batch (one launch for all its maps), or NULL for a uniform batch.
 template <class T>
 __global__ void __launch_bounds__(32 * kSlices) cl_kernel(const cplx<T>* __restrict__ alm, double* __restrict__ cl,
-                                                          int L, int64_t nalm) {
+                                                          int Lu, int64_t nalm, const int64_t* __restrict__ almoff,
+                                                          const int64_t* __restrict__ cloff,
+                                                          const int* __restrict__ lmax) {
     __shared__ double part[kSlices][32][2];
     const int lane = threadIdx.x & 31, slice = threadIdx.x >> 5;
     const int l = blockIdx.x * 32 + lane;
     const int b = blockIdx.y;
-    const cplx<T>* a = alm + (int64_t)b * nalm;
+    const int L = lmax ? lmax[b] : Lu;
+    if (blockIdx.x * 32 > L) return;   // the whole block is past this map's degrees
+    const cplx<T>* a = alm + (almoff ? almoff[b] : (int64_t)b * nalm);
     double s = 0.0;
     if (l <= L) {
         auto sq = [&](int m) {
@@ -60,7 +66,7 @@ __global__ void __launch_bounds__(32 * kSlices) cl_kernel(const cplx<T>* __restr
             neumaier(S, C, part[k][lane][0]);
             C += part[k][lane][1];
         }
-        cl[(int64_t)b * (L + 1) + l] = (S + C) / (2.0 * l + 1.0);
+        cl[(cloff ? cloff[b] : (int64_t)b * (L + 1)) + l] = (S + C) / (2.0 * l + 1.0);
     }
 }
 
@@ -68,7 +74,11 @@ template <class T>
 void launch_cl(const hpx_plan_s* P, const T* alm, double* cl, cudaStream_t s) {
     const auto& g = P->g;
     dim3 grid((g.L + 1 + 31) / 32, g.B);
-    cl_kernel<T><<<grid, 32 * kSlices, 0, s>>>((const cplx<T>*)alm, cl, g.L, g.nalm);
+    if (P->group)   // every map of an uneven batch in one launch, from the per-map tables
+        cl_kernel<T><<<grid, 32 * kSlices, 0, s>>>((const cplx<T>*)alm, cl, g.L, g.nalm, P->d_almel, P->d_clel,
+                                                   P->d_lmax);
+    else
+        cl_kernel<T><<<grid, 32 * kSlices, 0, s>>>((const cplx<T>*)alm, cl, g.L, g.nalm, nullptr, nullptr, nullptr);
 }
 
 // Vector-Jacobian product of Eq. (APS): for a loss L(C) with g_l = dL/dC_l, the

@@ -32,8 +32,11 @@ constexpr int kRingThreads = 512;
 //   ew != 0 (the transpose of the synthesis' ring stage, used by the equal-weight
 //     quadrature of Sec. 2.2): for every m <= L the ring's Fourier sum
 //     D_m = sum_k f_k e^{-i m lambda_k} (m taken mod n, so the polar rings alias),
-//     weighted like the synthesis folds the orders (1/2 at m = 0, 1 for even m,
-//     2 for odd m) and scaled by ew; 0 for L < m <= p.
+//     times ew and the weight of order m: the synthesis folds Y_m / 2 (even m) or
+//     Y_m (odd m) at +-m, so the plain transpose carries 1 (even m > 0), 2 (odd m)
+//     and 1/2 (m = 0); the transpose for the coefficient inner product with
+//     weight 2 for m > 0 halves the m > 0 ones: 1/2 for even m, 1 for odd m.
+//     0 for L < m <= p.
 template <class T, class BUF>
 __device__ __forceinline__ void ring_rows_out(BUF zat, int n, int p, int L, const cplx<T>* __restrict__ ph, bool sh,
                                               T ew, cplx<T>* rowN, cplx<T>* rowS, bool equator, int tid, int nt) {
@@ -51,7 +54,7 @@ __device__ __forceinline__ void ring_rows_out(BUF zat, int n, int p, int L, cons
             if (ew == T(0)) {
                 w = ph[m];
             } else {
-                const T wm = ew * (m == 0 ? T(0.5) : (m & 1) ? T(2) : T(1));
+                const T wm = ew * ((m & 1) ? T(1) : T(0.5));
                 if (sh) {   // e^{-i m pi / n}
                     T sn, cs;
                     if constexpr (sizeof(T) == 4) sincospif(-(float)(m % (2 * n)) / (float)n, &sn, &cs);
@@ -114,21 +117,17 @@ __global__ void __launch_bounds__(NT, (LOGN <= 13 ? 1024 / NT : 1)) ring_ct_kern
                      rowN, rowS, equator, tid, NT);
 }
 
+// The step for ring pair i of map b by the whole block (runtime transform
+// length; the generic form behind ring_fft_kernel and ring_list_kernel).
 template <class T, int E>
-__global__ void __launch_bounds__(kRingThreads, (E <= 16 ? 2 : 1)) ring_fft_kernel(
-    const T* __restrict__ maps, cplx<T>* __restrict__ Y, const int* __restrict__ nphi_t,
-    const int* __restrict__ startN_t, const int* __restrict__ startS_t,
-    const int* __restrict__ pow2_t, const int* __restrict__ logn_t, const int* __restrict__ fftL_t,
-    const int* __restrict__ logL_t, const int64_t* __restrict__ shOff_t,
-    const int64_t* __restrict__ chOff_t, const int64_t* __restrict__ bhOff_t,
-    const cplx<T>* __restrict__ shift, const cplx<T>* __restrict__ chirp,
-    const cplx<T>* __restrict__ bhat, const cplx<T>* __restrict__ tw, int twlen, int p, int Q,
-    int64_t npix, int npairs, const int* __restrict__ ringlist, T ew, const int* __restrict__ shifted_t, int L) {
-    extern __shared__ unsigned char smem_raw[];
-    cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw);
-    // largest rings first: blockIdx.y = 0 is the equator
-    const int i = ringlist ? ringlist[blockIdx.y] : npairs - 1 - (int)blockIdx.y;
-    const int b = blockIdx.x;
+__device__ __forceinline__ void ring_pair(
+    cplx<T>* buf, int i, int b, const T* __restrict__ maps, cplx<T>* __restrict__ Y, const int* __restrict__ nphi_t,
+    const int* __restrict__ startN_t, const int* __restrict__ startS_t, const int* __restrict__ pow2_t,
+    const int* __restrict__ logn_t, const int* __restrict__ fftL_t, const int* __restrict__ logL_t,
+    const int64_t* __restrict__ shOff_t, const int64_t* __restrict__ chOff_t, const int64_t* __restrict__ bhOff_t,
+    const cplx<T>* __restrict__ shift, const cplx<T>* __restrict__ chirp, const cplx<T>* __restrict__ bhat,
+    const cplx<T>* __restrict__ tw, int twlen, int p, int Q, int64_t npix, T ew, const int* __restrict__ shifted_t,
+    int L) {
     const int n = nphi_t[i];
     const int sN = startN_t[i], sS = startS_t[i];
     const bool equator = (sN == sS);
@@ -181,6 +180,62 @@ __global__ void __launch_bounds__(kRingThreads, (E <= 16 ? 2 : 1)) ring_fft_kern
     ring_rows_out<T>([&](int k) { return buf[pad(k)]; }, n, p, L, shift + shOff_t[i], shifted_t[i] != 0, ew, rowN,
                      rowS, equator, tid, nt);
 }
+
+
+template <class T, int E>
+__global__ void __launch_bounds__(kRingThreads, (E <= 16 ? 2 : 1)) ring_fft_kernel(
+    const T* __restrict__ maps, cplx<T>* __restrict__ Y, const int* __restrict__ nphi_t,
+    const int* __restrict__ startN_t, const int* __restrict__ startS_t,
+    const int* __restrict__ pow2_t, const int* __restrict__ logn_t, const int* __restrict__ fftL_t,
+    const int* __restrict__ logL_t, const int64_t* __restrict__ shOff_t,
+    const int64_t* __restrict__ chOff_t, const int64_t* __restrict__ bhOff_t,
+    const cplx<T>* __restrict__ shift, const cplx<T>* __restrict__ chirp,
+    const cplx<T>* __restrict__ bhat, const cplx<T>* __restrict__ tw, int twlen, int p, int Q,
+    int64_t npix, int npairs, const int* __restrict__ ringlist, T ew, const int* __restrict__ shifted_t, int L) {
+    extern __shared__ unsigned char smem_raw[];
+    cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw);
+    // largest rings first: blockIdx.y = 0 is the equator
+    const int i = ringlist ? ringlist[blockIdx.y] : npairs - 1 - (int)blockIdx.y;
+    ring_pair<T, E>(buf, i, blockIdx.x, maps, Y, nphi_t, startN_t, startS_t, pow2_t, logn_t, fftL_t, logL_t, shOff_t,
+                    chOff_t, bhOff_t, shift, chirp, bhat, tw, twlen, p, Q, npix, ew, shifted_t, L);
+}
+
+// The ring stage of every sub-plan of an uneven batch in one persistent launch:
+// the blocks walk a work list of (sub-plan, ring pair, map) items, built at
+// plan time with the longest transforms first, in strides of the grid size; the
+// sub-plans' tables and workspaces come from the job table.  Maps of a
+// sub-plan used in place are read from the caller's array (maps_base plus the
+// job's element offset), gathered ones from the sub-plan's staging buffer.
+template <class T, int E>
+__global__ void __launch_bounds__(kRingThreads, 1) ring_list_kernel(const RingJob<T>* __restrict__ jobs,
+                                                                     const int4* __restrict__ items, int nitems,
+                                                                     const T* __restrict__ maps_base) {
+    extern __shared__ unsigned char smem_raw[];
+    cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw);
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const int4 w = items[it];
+        const RingJob<T>& J = jobs[w.x];
+        const T* maps = J.staged ? J.staged : maps_base + J.mapoff;
+        ring_pair<T, E>(buf, w.y, w.z, maps, J.Y, J.nphi, J.startN, J.startS, J.pow2, J.logn, J.fftL, J.logL,
+                        J.shOff, J.chOff, J.bhOff, J.shift, J.chirp, J.bhat, J.tw, J.twlen, J.p, J.Q, J.npix, T(0),
+                        J.shifted, J.L);
+        __syncthreads();   // the next item overwrites the shared buffer
+    }
+}
+
+template <class T>
+void launch_ring_list(const RingJob<T>* jobs, const int4* items, int nitems, int maxN, int blocks, const T* maps_base,
+                      cudaStream_t s) {
+    const bool big = maxN > 16 * kRingThreads;
+    const size_t smem = (size_t)(maxN + maxN / 16) * sizeof(cplx<T>);
+    auto kern = big ? ring_list_kernel<T, 32> : ring_list_kernel<T, 16>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    kern<<<blocks, kRingThreads, smem, s>>>(jobs, items, nitems, maps_base);
+}
+
+template void launch_ring_list<float>(const RingJob<float>*, const int4*, int, int, int, const float*, cudaStream_t);
+template void launch_ring_list<double>(const RingJob<double>*, const int4*, int, int, int, const double*,
+                                       cudaStream_t);
 
 // Pole values (Sec. 3.2.1): a fixed linear functional of the samples of the
 // three rings nearest each pole (unit-weight quadratic least squares in the

@@ -123,6 +123,9 @@ struct hpx_plan_s {
     std::vector<cudaStream_t> sstreams;      // per sub-plan stream (concurrent branches of an analysis)
     std::vector<cudaEvent_t> sjoin;          // per sub-plan join event
     cudaEvent_t sfork = nullptr;             // fork event on the group's stream
+    void* ringJobs = nullptr;                // RingJob<T> per sub-plan (persistent ring kernel)
+    int4* ringItems = nullptr;               // (sub-plan, ring pair, map, length), longest first
+    int nRingItems = 0, ringMaxN = 0, ringBlocks = 0;
     int64_t total_npix = 0, total_nalm = 0, total_ncl = 0;
 
     // CUDA graphs of hpx_analyze (HPX_FLAG_GRAPH)
@@ -136,6 +139,24 @@ struct hpx_plan_s {
 };
 
 namespace hpx {
+
+// One sub-plan of an uneven batch as seen by the persistent ring kernel: its
+// tables and Y workspace, and where its maps are (staged: a plan-owned staging
+// buffer; else the caller's array plus mapoff elements).
+template <class T>
+struct RingJob {
+    const T* staged;
+    int64_t mapoff;
+    cplx<T>* Y;
+    const int *nphi, *startN, *startS, *pow2, *logn, *fftL, *logL, *shifted;
+    const int64_t *shOff, *chOff, *bhOff;
+    const cplx<T> *shift, *chirp, *bhat, *tw;
+    int twlen, p, Q, L;
+    int64_t npix;
+};
+template <class T>
+void launch_ring_list(const RingJob<T>* jobs, const int4* items, int nitems, int maxN, int blocks, const T* maps_base,
+                      cudaStream_t s);
 
 // ring transforms of this many points or more run in launches of one length and
 // one kind (plain or Bluestein) with the compile-time FFT of fft_ct.cuh
@@ -192,6 +213,10 @@ int group_analyze(hpx_plan_s* P, const void* maps, void* alm);
 int group_synthesize(hpx_plan_s* P, const void* alm, void* maps);
 int group_cl(hpx_plan_s* P, const void* alm, double* cl);
 int group_analyze_vjp(hpx_plan_s* P, const void* galm, void* gmaps);
+bool group_build_ring_list(hpx_plan_s* G);
+// the analysis of a uniform plan without its ring stage (Y already holds the
+// ring coefficients): poles onward (capi.cu)
+int analyze_after_rings(hpx_plan_s* P, const void* maps, void* alm);
 void group_free(hpx_plan_s* P);
 template <class T> void launch_cl(const hpx_plan_s* P, const T* alm, double* cl, cudaStream_t s);
 // dL/da of Eq. (APS) for gcl = dL/dC (k_cl.cu); almoff / cloff / lmax: per-map
