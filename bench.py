@@ -390,6 +390,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle leg")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default launch shapes (e.g. under a profiler, whose serialised timings "
+                         "would steer the tuning)")
     ap.add_argument("--kernels-only", action="store_true",
                     help="time only the device-resident step (for profiler runs): no e2e, FP64 or CPU legs")
     ap.add_argument("--nside", type=int, default=NSIDE, help="smaller cases for profiler captures")
@@ -427,7 +430,8 @@ def main():
     else:
         maps_np = skies.small_powerlaw_maps(ns, nb, seed=6000 + rank, alpha=2.0, noise=1e-3)[0].astype(np.float32)
     t_plan0 = time.perf_counter()
-    plan = hp.Plan(ns, 2 * ns, nb, "fp32", sweeps=args.sweeps and args.kernels_only)
+    # autotune: launch shapes of the FFT stages, and the operators against the sweeps
+    plan = hp.Plan(ns, 2 * ns, nb, "fp32", sweeps=args.sweeps and args.kernels_only, autotune=not args.no_autotune)
     torch.cuda.synchronize()
     plan_build_s = time.perf_counter() - t_plan0
     maps = torch.from_numpy(maps_np).cuda()
@@ -467,7 +471,8 @@ def main():
             per_launch = {n: stage_ms[k] / max(ncalls, 1) for k, n in enumerate(plan.stages)}
             print(json.dumps({"nside": ns, "batch": nb, "value": value, "unit": "Gpix/s",
                               "ms_per_step": t_step * 1e3, "stages_ms_per_launch": per_launch,
-                              "plan_build_s": plan_build_s, "plan_gb": plan.nbytes / 1e9}), flush=True)
+                              "plan_build_s": plan_build_s, "plan_gb": plan.nbytes / 1e9,
+                              "launch_shapes": list(plan.tuning)}), flush=True)
         if world > 1:
             dist.destroy_process_group()
         return
@@ -714,7 +719,8 @@ def main():
             "healpix_software_analysis": healpix_sw,
             "fp32_batched_over_fp64_single": value / world / fp64["value"],
             "stages_ms_per_launch": per_launch, "plan_build_s": plan_build_s, "plan_gb": plan.nbytes / 1e9,
-            "plan_path": "sweeps" if plan.flags & hp.HPX_FLAG_SWEEPS else "per-order operators"}
+            "plan_path": "sweeps" if plan.flags & hp.HPX_FLAG_SWEEPS else "per-order operators",
+            "launch_shapes": {"ring_fft_elems_per_thread": plan.tuning[0], "grid_fft_elems_per_thread": plan.tuning[1]}}
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

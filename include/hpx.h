@@ -61,7 +61,10 @@ extern "C" {
  *   n_alm x (nside + 1) entries, 8.6 GB in FP32 at nside 1024) and the analysis
  *   applies those as one batched contraction; if that memory is not available,
  *   or the operators would exceed 24 GB (nside 2048 needs 69 GB and minutes of
- *   FP64 build), the plan uses the sweeps and sets this flag (hpx_plan_flags). */
+ *   FP64 build), the plan uses the sweeps and sets this flag (hpx_plan_flags).
+ *   With the sweeps, FP32 plans of 4 maps or more and nside <= 1024 apply D on
+ *   the tensor cores (the FP16-pair arithmetic of the operators, D resident in
+ *   L2), unless HPX_FLAG_SIMT or HPX_FLAG_CG is given. */
 #define HPX_FLAG_SWEEPS 1u
 /* HPX_FLAG_GRAPH: the first hpx_analyze call with a given (maps, alm) pair
  *   captures the plan's whole launch sequence into a CUDA graph (on a stream of
@@ -82,11 +85,15 @@ extern "C" {
  *   status word and reported by the next hpx_sync; the outputs are then
  *   undefined).  Costs one extra read of the input. */
 #define HPX_FLAG_CHECKED 8u
-/* HPX_FLAG_AUTOTUNE: at plan creation, when the per-order operators were built,
- *   time one analysis of a batch through them and through the run-time sweeps
- *   (on scratch buffers allocated and freed inside hpx_plan_ex) and keep the
- *   faster path; if that is the sweeps the operators are freed and
- *   HPX_FLAG_SWEEPS is set (hpx_plan_flags). */
+/* HPX_FLAG_AUTOTUNE: at plan creation, on scratch buffers allocated and freed
+ *   inside hpx_plan_ex: (1) time the ring-FFT and grid-FFT stages of the plan's
+ *   batch with 16 and with 32 elements per thread (launch shapes of the
+ *   compile-time FFT kernels) and keep the faster of each (hpx_plan_tuning;
+ *   remembered per nside, lmax, batch and precision for the process's later
+ *   plans); (2) when the per-order operators were built, time one analysis
+ *   through them and through the run-time sweeps and keep the faster path; if
+ *   that is the sweeps the operators are freed and HPX_FLAG_SWEEPS is set
+ *   (hpx_plan_flags). */
 #define HPX_FLAG_AUTOTUNE 16u
 /* HPX_FLAG_SYNTHESIS: also build the table of hpx_sh_synthesis (the expansion
  *   of the order-0/1 Legendre functions in the latitude Fourier basis, FP64 on
@@ -231,6 +238,16 @@ int64_t hpx_plan_bytes(const hpx_plan_s* plan);
 int hpx_plan_flags(const hpx_plan_s* plan);
 /* Kernel launches of one hpx_analyze call (ring FFTs: one per transform length). */
 int hpx_plan_launches(const hpx_plan_s* plan);
+/* Launch shapes in effect (HPX_FLAG_AUTOTUNE, else 16 and 16): elements per
+ * thread of the ring-FFT and of the grid-FFT kernels.  HPX_ERR_ARG for NULL
+ * arguments or an uneven-batch plan. */
+int hpx_plan_tuning(const hpx_plan_s* plan, int* ring_elems, int* fft_elems);
+/* Sets those launch shapes (16 or 32 each; e.g. the values an earlier process's
+ * HPX_FLAG_AUTOTUNE chose) and drops the plan's captured graphs, which are
+ * captured again by the next call.  Results do not depend on the shapes: every
+ * transform runs the same radix passes in the same order, only their split over
+ * the threads differs.  HPX_ERR_ARG for other values or an uneven-batch plan. */
+int hpx_plan_set_tuning(hpx_plan_s* plan, int ring_elems, int fft_elems);
 
 /* Stage timing for profiling.  With profiling enabled (enable = 1) every
  * hpx_analyze records CUDA events on the plan's stream around each of its

@@ -33,7 +33,8 @@ EXPORTS = ["hpx_plan", "hpx_plan_ex", "hpx_set_stream", "hpx_analyze", "hpx_synt
            "hpx_sync", "hpx_destroy", "hpx_npix", "hpx_nalm", "hpx_plan_lmax", "hpx_plan_bytes",
            "hpx_last_error", "hpx_strerror", "hpx_set_profiling", "hpx_stage_times",
            "hpx_analyze_noalloc", "hpx_plan_flags", "hpx_selftest_timeout", "hpx_sh_synthesis", "hpx_plan_launches",
-           "hpx_analyze_vjp", "hpx_cl_vjp", "hpx_sh_synthesis_adjoint", "hpx_healpix_analysis"]
+           "hpx_analyze_vjp", "hpx_cl_vjp", "hpx_sh_synthesis_adjoint", "hpx_healpix_analysis", "hpx_plan_tuning",
+           "hpx_plan_set_tuning"]
 HPX_FLAG_SWEEPS = 1
 HPX_FLAG_GRAPH = 2
 HPX_FLAG_SIMT = 4
@@ -110,6 +111,8 @@ def lib():
             "hpx_analyze_vjp": (i32, [vp, vp, vp]),
             "hpx_sh_synthesis_adjoint": (i32, [vp, vp, vp]),
             "hpx_healpix_analysis": (i32, [vp, vp, vp, i32]),
+            "hpx_plan_tuning": (i32, [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+            "hpx_plan_set_tuning": (i32, [vp, i32, i32]),
             "hpx_cl_vjp": (i32, [vp, vp, vp, vp]),
             "hpx_stage_times": (i32, [vp, ctypes.POINTER(ctypes.c_float), i32, ctypes.POINTER(ctypes.c_int)]),
         }
@@ -247,6 +250,18 @@ class Plan:
         self.nalm = lib().hpx_nalm(h)
         self.rdtype = torch.float64 if self.precision == HPX_FP64 else torch.float32
         self.cdtype = torch.complex128 if self.precision == HPX_FP64 else torch.complex64
+
+    @property
+    def tuning(self):
+        """(ring-FFT, grid-FFT) elements per thread in effect (HPX_FLAG_AUTOTUNE)."""
+        r, f = ctypes.c_int(0), ctypes.c_int(0)
+        self._check(lib().hpx_plan_tuning(self.handle, ctypes.byref(r), ctypes.byref(f)), "hpx_plan_tuning")
+        return r.value, f.value
+
+    @tuning.setter
+    def tuning(self, shapes):
+        r, f = shapes
+        self._check(lib().hpx_plan_set_tuning(self.handle, int(r), int(f)), "hpx_plan_set_tuning")
 
     @property
     def nbytes(self):

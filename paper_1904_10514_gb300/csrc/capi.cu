@@ -4,7 +4,10 @@
 
 #include <algorithm>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
+#include <tuple>
 #include <string>
 #include <vector>
 
@@ -70,7 +73,7 @@ void free_plan(hpx_plan_s* P) {
                     t.bhOff, t.shift, t.chirp, t.bhat, t.twid, t.poleN, t.poleS, t.polew, t.rowptr,
                     t.ent, t.entw, t.dec, t.D, t.tstart, t.hwn, t.angOff, t.ang, t.skOff, t.skew, t.skewT, t.nrowptr, t.nent, t.nentw, t.nstart, t.swts, t.hstart, t.hwts, t.Es, t.shifted, t.C, t.cgH, P->Y, P->U, P->bvec,
                     P->fusedM, P->fusedOff, P->fusedTiles, P->tcOff, P->tcFirst, P->tcRinv, P->bscale, P->d_status, P->synM, P->ringList,
-                    P->jres, P->jalm};
+                    P->jres, P->jalm, P->dTC, P->dRinv, P->dTiles, P->dTcOff, P->mapIdx};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     if (P->ev) {
@@ -106,6 +109,8 @@ int analyze_impl(hpx_plan_s* P, const void* maps, void* alm, bool rings = true) 
         if (P->flags & HPX_FLAG_CG) {
             hpx::launch_cg<T>(P, s);                  // bvec <- T^{-1} bvec, column by column
             hpx::launch_dense<T>(P, s, P->t.C);       // change of basis alone
+        } else if (sizeof(T) == 4 && P->dTC) {
+            hpx::launch_dense_tc(P, s);               // D on the tensor cores
         } else {
             hpx::launch_dense<T>(P, s);
         }
@@ -378,9 +383,20 @@ hpx_plan_s* hpx_plan_ex(const hpx_plan_desc* d) {
         }
     }
     if (cudaDeviceSynchronize() != cudaSuccess) { free_plan(P); set_err(HPX_ERR_CUDA); return nullptr; }
-    if ((d->flags & HPX_FLAG_AUTOTUNE) && P->fusedM) {
+    if (d->flags & HPX_FLAG_AUTOTUNE) {
         const int rc = autotune(P);
         if (rc != HPX_OK) { free_plan(P); set_err(rc); return nullptr; }
+    }
+    // the sweeps path of FP32 plans of 4 maps or more: D on the tensor cores (its
+    // tiles are 32 maps wide; below 4 maps the FP32-pipe kernel is as fast).  Up
+    // to nside 1024: at nside 2048 (K = 2049 terms per row) the FP16 pairs' 2^-22
+    // representation error of both operands left a flat-spectrum map at 1.2e-5
+    // per degree, above the 1e-5 of FP32 plans, so the FP32 pipes apply D there
+    if (!P->fusedM && !fp64 && g.B >= 4 && ns <= 1024 && !(d->flags & (HPX_FLAG_SIMT | HPX_FLAG_CG)) &&
+        hpx::prepare_dense_tc(P) != 0) {
+        free_plan(P);
+        set_err(HPX_ERR_CUDA);
+        return nullptr;
     }
     set_err(HPX_OK);
     return P;
@@ -415,8 +431,65 @@ int analyze_direct(hpx_plan_s* P, const void* maps, void* alm) {
     return P->precision == HPX_FP64 ? analyze_impl<double>(P, maps, alm) : analyze_impl<float>(P, maps, alm);
 }
 
-// HPX_FLAG_AUTOTUNE: time the operator path and the run-time sweeps on scratch
-// buffers (3 analyses each after one warm-up) and keep the faster.
+// Launch shapes chosen by HPX_FLAG_AUTOTUNE, per (nside, lmax, batch,
+// precision): later plans of the same shape reuse them without timing.
+struct TuneKey {
+    int ns, L, B, prec;
+    bool operator<(const TuneKey& o) const {
+        return std::tie(ns, L, B, prec) < std::tie(o.ns, o.L, o.B, o.prec);
+    }
+};
+std::mutex g_tune_mutex;
+std::map<TuneKey, std::pair<int, int>> g_tune_cache;   // (ring elements per thread, grid-FFT elements per thread)
+
+// Times one stage (ring FFT: stage 0, grid FFT: stage 1) of the analysis for
+// every launch shape and keeps the fastest.
+float time_stage(hpx_plan_s* P, const void* maps, int stage, cudaEvent_t e0, cudaEvent_t e1) {
+    float best = 0.f;
+    for (int r = 0; r < 4; ++r) {   // one warm-up, then the best of three
+        cudaEventRecord(e0, P->stream);
+        if (P->precision == HPX_FP64) {
+            if (stage == 0) hpx::launch_ring_fft<double>(P, (const double*)maps, P->stream);
+            else hpx::launch_lat_fft<double>(P, P->stream);
+        } else {
+            if (stage == 0) hpx::launch_ring_fft<float>(P, (const float*)maps, P->stream);
+            else hpx::launch_lat_fft<float>(P, P->stream);
+        }
+        cudaEventRecord(e1, P->stream);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (r == 1 || (r > 1 && ms < best)) best = ms;
+    }
+    return best;
+}
+
+void tune_shapes(hpx_plan_s* P, const void* maps, cudaEvent_t e0, cudaEvent_t e1) {
+    const TuneKey key{P->g.ns, P->g.L, P->g.B, P->precision};
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            P->ringE = it->second.first;
+            P->latE = it->second.second;
+            return;
+        }
+    }
+    float t[2][2];
+    for (int e = 0; e < 2; ++e) {
+        P->ringE = P->latE = e ? 32 : 16;
+        t[0][e] = time_stage(P, maps, 0, e0, e1);
+        t[1][e] = time_stage(P, maps, 1, e0, e1);
+    }
+    P->ringE = t[0][1] < t[0][0] ? 32 : 16;
+    P->latE = t[1][1] < t[1][0] ? 32 : 16;
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    g_tune_cache[key] = {P->ringE, P->latE};
+}
+
+// HPX_FLAG_AUTOTUNE: choose the launch shapes of the FFT stages (tune_shapes),
+// then time the operator path and the run-time sweeps on scratch buffers (3
+// analyses each after one warm-up) and keep the faster.
 int autotune(hpx_plan_s* P) {
     const size_t es = P->precision == HPX_FP64 ? 8 : 4;
     void *maps = nullptr, *alm = nullptr;
@@ -429,6 +502,14 @@ int autotune(hpx_plan_s* P) {
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
+    tune_shapes(P, maps, e0, e1);
+    if (!P->fusedM) {   // only the sweeps: nothing else to choose
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        cudaFree(maps);
+        cudaFree(alm);
+        return cudaGetLastError() == cudaSuccess ? HPX_OK : HPX_ERR_CUDA;
+    }
     float ms[2] = {0.f, 0.f};
     void* M = P->fusedM;
     for (int path = 0; path < 2; ++path) {   // 0: operators, 1: sweeps
@@ -687,11 +768,33 @@ int hpx_plan_lmax(const hpx_plan_s* P) { return P ? P->g.L : -1; }
 int64_t hpx_plan_bytes(const hpx_plan_s* P) { return P ? P->bytes : 0; }
 int hpx_plan_flags(const hpx_plan_s* P) { return P ? (int)P->flags : -1; }
 
+int hpx_plan_tuning(const hpx_plan_s* P, int* ring_elems, int* fft_elems) {
+    if (!P || P->group || !ring_elems || !fft_elems) return set_err(HPX_ERR_ARG);
+    *ring_elems = P->ringE;
+    *fft_elems = P->latE;
+    return set_err(HPX_OK);
+}
+
+int hpx_plan_set_tuning(hpx_plan_s* P, int ring_elems, int fft_elems) {
+    if (!P || P->group) return set_err(HPX_ERR_ARG);
+    auto ok = [](int e) { return e == 16 || e == 32; };
+    if (!ok(ring_elems) || !ok(fft_elems)) return set_err(HPX_ERR_ARG);
+    P->ringE = ring_elems;
+    P->latE = fft_elems;
+    // captured graphs hold the old launch shapes: capture again on the next call
+    for (auto& e : P->graphs) cudaGraphExecDestroy(e.exec);
+    P->graphs.clear();
+    return set_err(HPX_OK);
+}
+
 int hpx_plan_launches(const hpx_plan_s* P) {
     if (!P) return -1;
-    if (P->group) {   // one persistent ring launch, then each sub-plan's other stages
-        int n = 1;
-        for (const hpx_plan_s* S : P->subs) n += hpx_plan_launches(S) - (S->ringList ? (int)S->ringClasses.size() : 1);
+    if (P->group) {   // the persistent short-ring launches, then each sub-plan's other stages
+        int n = (P->nRingLong > 0) + (P->nRingItems > P->nRingLong);
+        for (const hpx_plan_s* S : P->subs) {
+            n += hpx_plan_launches(S);
+            for (const auto& c : S->ringClasses) n -= c.N < hpx::kRingCtMin;   // in the persistent launches
+        }
         for (size_t s = 0; s < P->subs.size(); ++s) n += P->sub_inplace[s] ? 0 : 2;   // gather + scatter
         return n;
     }

@@ -2,11 +2,13 @@
 //
 // A group plan holds one uniform sub-plan per distinct (nside, lmax).  The caller's
 // maps, coefficients and spectra are concatenated in batch order; a sub-plan
-// whose maps are adjacent in the batch works on the caller's arrays in place,
-// otherwise its maps are gathered into a plan-owned staging buffer before the
-// launch and its results scattered back after it (segment_copy_kernel).  All
-// launches go to the group's stream, so HPX_FLAG_GRAPH captures the whole
-// batch -- every nside -- as one CUDA graph.
+// whose maps are adjacent in the batch works on the caller's arrays in place.
+// The others read their maps in place too, through a table of per-map offsets
+// (the ring and pole stages), and write their coefficients into a plan-owned
+// staging buffer that is scattered back after the launch (segment_copy_kernel);
+// the directions that write maps (adjoint, synthesis) stage the maps the same
+// way.  The launches start and end on the group's stream, so HPX_FLAG_GRAPH
+// captures the whole batch -- every nside -- as one CUDA graph.
 #include <algorithm>
 #include <map>
 #include <new>
@@ -194,6 +196,17 @@ hpx_plan_s* group_create(const hpx_plan_desc* d, int* err) {
             *err = HPX_ERR_OOM;
         }
     }
+    // per-map element offsets of the sub-plans whose maps are not adjacent: the
+    // analysis reads their maps in place through them
+    for (size_t s = 0; ok && s < G->subs.size(); ++s) {
+        if (G->sub_inplace[s]) continue;
+        std::vector<int64_t> offs(G->sub_count[s]);
+        for (int k = 0; k < G->sub_count[s]; ++k) offs[k] = mapoff[idx[G->sub_first[s] + k]] / (int64_t)es;
+        hpx_plan_s* S = G->subs[s];
+        ok = cudaMalloc(&S->mapIdx, offs.size() * sizeof(int64_t)) == cudaSuccess &&
+             cudaMemcpy(S->mapIdx, offs.data(), offs.size() * sizeof(int64_t), cudaMemcpyHostToDevice) == cudaSuccess;
+        if (!ok) *err = HPX_ERR_OOM;
+    }
     if (!ok) {
         group_free(G);
         return nullptr;
@@ -213,6 +226,7 @@ void group_free(hpx_plan_s* G) {
     if (G->sfork) cudaEventDestroy(G->sfork);
     if (G->ringJobs) cudaFree(G->ringJobs);
     if (G->ringItems) cudaFree(G->ringItems);
+    if (G->ringEv) cudaEventDestroy(G->ringEv);
     for (void* q : G->stage_maps) if (q) cudaFree(q);
     for (void* q : G->stage_alm) if (q) cudaFree(q);
     for (void* q : G->stage_cl) if (q) cudaFree(q);
@@ -231,26 +245,32 @@ void group_free(hpx_plan_s* G) {
 // concurrent branches, each ending with its scatter.
 int group_analyze(hpx_plan_s* G, const void* maps, void* alm) {
     const size_t es = G->precision == HPX_FP64 ? 8 : 4;
-    for (size_t s = 0; s < G->subs.size(); ++s)
-        if (!G->sub_inplace[s])
-            seg_copy(G, (int)s, maps, G->stage_maps[s], G->d_mapoff, G->subs[s]->g.npix * (int64_t)es, true);
-    if (G->precision == HPX_FP64)
-        launch_ring_list<double>((const RingJob<double>*)G->ringJobs, G->ringItems, G->nRingItems, G->ringMaxN,
-                                 G->ringBlocks, (const double*)maps, G->stream);
-    else
-        launch_ring_list<float>((const RingJob<float>*)G->ringJobs, G->ringItems, G->nRingItems, G->ringMaxN,
-                                G->ringBlocks, (const float*)maps, G->stream);
     fork(G);
+    // the short rings of every sub-plan on the group's stream, meanwhile each
+    // branch runs its sub-plan's compile-time ring classes
+    if (G->precision == HPX_FP64)
+        launch_ring_list<double>((const RingJob<double>*)G->ringJobs, G->ringItems, G->nRingItems, G->nRingLong,
+                                 (const double*)maps, G->stream);
+    else
+        launch_ring_list<float>((const RingJob<float>*)G->ringJobs, G->ringItems, G->nRingItems, G->nRingLong,
+                                (const float*)maps, G->stream);
+    cudaEventRecord(G->ringEv, G->stream);
     int rc = HPX_OK;
     for (size_t s = 0; s < G->subs.size() && rc == HPX_OK; ++s) {
         hpx_plan_s* S = G->subs[s];
         const cudaStream_t st = branch(G, s);
         hpx_set_stream(S, st);
+        // maps read in place: adjacent ones from the sub-plan's first map, the
+        // others through the sub-plan's per-map offsets from the caller's base
+        const void* smaps = G->sub_inplace[s] ? (const void*)((const unsigned char*)maps + G->sub_mapoff[s]) : maps;
+        if (G->precision == HPX_FP64) launch_ring_fft<double>(S, (const double*)smaps, st, 0.0, kRingCtMin);
+        else launch_ring_fft<float>(S, (const float*)smaps, st, 0.f, kRingCtMin);
+        cudaStreamWaitEvent(st, G->ringEv, 0);
         if (G->sub_inplace[s]) {
             rc = analyze_after_rings(S, (const unsigned char*)maps + G->sub_mapoff[s],
                                      (unsigned char*)alm + G->sub_almoff[s]);
         } else {
-            rc = analyze_after_rings(S, G->stage_maps[s], G->stage_alm[s]);
+            rc = analyze_after_rings(S, maps, G->stage_alm[s]);
             if (rc == HPX_OK)
                 seg_copy(G, (int)s, G->stage_alm[s], alm, G->d_almoff, S->g.nalm * (int64_t)es * 2, false, st);
         }
@@ -310,13 +330,12 @@ bool build_ring_list(hpx_plan_s* G) {
         int len, s, i, b;
     };
     std::vector<Item> items;
-    int maxN = 0;
     for (size_t s = 0; s < G->subs.size(); ++s) {
         const hpx_plan_s* S = G->subs[s];
         const auto& t = S->t;
         RingJob<T> J;
-        J.staged = G->sub_inplace[s] ? nullptr : (const T*)G->stage_maps[s];
-        J.mapoff = G->sub_mapoff[s] / (int64_t)es;
+        J.mapoff = G->sub_inplace[s] ? G->sub_mapoff[s] / (int64_t)es : 0;
+        J.mapIdx = S->mapIdx;
         J.Y = (cplx<T>*)S->Y;
         J.nphi = t.nphi; J.startN = t.startN; J.startS = t.startS; J.pow2 = t.pow2; J.logn = t.logn;
         J.fftL = t.fftL; J.logL = t.logL; J.shifted = t.shifted;
@@ -335,7 +354,7 @@ bool build_ring_list(hpx_plan_s* G) {
                 len = 1;
                 while (len < 2 * n - 1) len <<= 1;
             }
-            maxN = std::max(maxN, len);
+            if (len >= kRingCtMin) continue;   // the sub-plan's compile-time kernels
             for (int b = 0; b < G->sub_count[s]; ++b) items.push_back({len, (int)s, i, b});
         }
     }
@@ -348,13 +367,9 @@ bool build_ring_list(hpx_plan_s* G) {
     cudaMemcpy(G->ringJobs, jobs.data(), jobs.size() * sizeof(RingJob<T>), cudaMemcpyHostToDevice);
     cudaMemcpy(G->ringItems, packed.data(), packed.size() * sizeof(int4), cudaMemcpyHostToDevice);
     G->nRingItems = (int)packed.size();
-    G->ringMaxN = maxN;
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    // resident blocks of 512 threads: two per SM (registers), one above 8192 points (shared memory)
-    G->ringBlocks = sms * (maxN > 8192 ? 1 : 2);
-    return true;
+    G->nRingLong = 0;
+    while (G->nRingLong < (int)items.size() && items[G->nRingLong].len > 512) ++G->nRingLong;
+    return cudaEventCreateWithFlags(&G->ringEv, cudaEventDisableTiming) == cudaSuccess;
 }
 }  // namespace
 

@@ -28,6 +28,7 @@
 // and returns after releasing its tensor memory.
 #include <cuda_fp16.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "plan.h"
@@ -464,6 +465,14 @@ __device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
 }
 
+// DENSE = false: the per-order operators M_{m,c}, tile (m, c, i0), output into
+// alm.  DENSE = true: the latitude operator D of the sweeps path (Sec. 3.2.2 and
+// the first half of Sec. 3.3, shared by all orders of one parity), tile
+// (m, par, i0) = rows q = i0.. of D[m & 1][par] applied to the columns
+// b[map][m][par], output into beta[m][par][q][map] for the Givens sweeps; the
+// tiles of all orders of one parity point at the same operator data, which
+// stays resident in L2.
+template <bool DENSE>
 __global__ void __launch_bounds__(NTW, 2) fused_tc_ws_kernel(
     const unsigned char* __restrict__ Mh, const int64_t* __restrict__ tcOff, const float* __restrict__ tcRinv,
     const int* __restrict__ tiles, const cplx<float>* __restrict__ bvec, const float* __restrict__ bscale,
@@ -480,8 +489,8 @@ __global__ void __launch_bounds__(NTW, 2) fused_tc_ws_kernel(
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m = tiles[3 * blockIdx.x], c = tiles[3 * blockIdx.x + 1], i0 = tiles[3 * blockIdx.x + 2];
-    const int par = ((m & 1) + c) & 1;
-    const int nrows = chain_len(m, c, L);
+    const int par = DENSE ? c : ((m & 1) + c) & 1;
+    const int nrows = DENSE ? P2 : chain_len(m, c, L);
     const int rp = (min(TM, nrows - i0) + 7) & ~7;
     const int b0 = blockIdx.y * (TN / 2);
     const int nchunks = (P2 + KC - 1) / KC;
@@ -653,13 +662,23 @@ __global__ void __launch_bounds__(NTW, 2) fused_tc_ws_kernel(
             const int i = i0 + row;
             if (i < nrows) {
                 const float ri = tcRinv[tcOff[blockIdx.x] / (32 * nchunks) + row];
-                const int64_t base = (int64_t)m * (2 * L + 1 - m) / 2 + m + c + 2 * (int64_t)i;
+                if constexpr (DENSE) {   // beta[m][par][i][map]: the 32 maps side by side
+                    cplx<float>* out = alm + (((int64_t)m * 2 + par) * P2 + i) * B + b0;
 #pragma unroll
-                for (int q = 0; q < 32; ++q)
-                    if (b0 + q < B) {
-                        const float sc = ri * tinv[q];
-                        alm[(int64_t)(b0 + q) * nalm + base] = mk<float>(acc[q] * sc, acc[32 + q] * sc);
-                    }
+                    for (int q = 0; q < 32; ++q)
+                        if (b0 + q < B) {
+                            const float sc = ri * tinv[q];
+                            out[q] = mk<float>(acc[q] * sc, acc[32 + q] * sc);
+                        }
+                } else {
+                    const int64_t base = (int64_t)m * (2 * L + 1 - m) / 2 + m + c + 2 * (int64_t)i;
+#pragma unroll
+                    for (int q = 0; q < 32; ++q)
+                        if (b0 + q < B) {
+                            const float sc = ri * tinv[q];
+                            alm[(int64_t)(b0 + q) * nalm + base] = mk<float>(acc[q] * sc, acc[32 + q] * sc);
+                        }
+                }
             }
         }
     }
@@ -685,11 +704,13 @@ __global__ void __launch_bounds__(NTW, 2) fused_tc_ws_kernel(
 // tile, thread r = row r): the row's largest magnitude gives its scale s_r,
 // 1 / s_r goes to rinv, and every chunk (all of it read before any of it is
 // rewritten) becomes the hi block followed by the lo block of s_r M.
+// rowsAll > 0: every tile belongs to a matrix of rowsAll rows (D), else to the
+// chain (m, c) of the tile table.
 __global__ void __launch_bounds__(TM) tc_to_f16_kernel(float* __restrict__ Mt, const int64_t* __restrict__ tcOff,
                                                        const int* __restrict__ tiles, int P2, int L,
-                                                       float* __restrict__ rinv) {
+                                                       float* __restrict__ rinv, int rowsAll) {
     const int m = tiles[3 * blockIdx.x], c = tiles[3 * blockIdx.x + 1], i0 = tiles[3 * blockIdx.x + 2];
-    const int rp = (min(TM, chain_len(m, c, L) - i0) + 7) & ~7;
+    const int rp = (min(TM, (rowsAll > 0 ? rowsAll : chain_len(m, c, L)) - i0) + 7) & ~7;
     const int nchunks = (P2 + KC - 1) / KC;
     float* At = Mt + tcOff[blockIdx.x];
     const int r = threadIdx.x;
@@ -759,7 +780,7 @@ int prepare_fused_tc(hpx_plan_s* P) {
     if (cudaMalloc(&P->tcRinv, rb) != cudaSuccess || cudaMalloc(&P->bscale, bb) != cudaSuccess) return -1;
     P->bytes += (int64_t)(rb + bb);
     P->fused_bytes += (int64_t)(rb + bb);
-    tc_to_f16_kernel<<<P->fused_ntiles, TM>>>((float*)P->fusedM, P->tcOff, P->fusedTiles, g.P2, g.L, P->tcRinv);
+    tc_to_f16_kernel<<<P->fused_ntiles, TM>>>((float*)P->fusedM, P->tcOff, P->fusedTiles, g.P2, g.L, P->tcRinv, 0);
     return cudaDeviceSynchronize() == cudaSuccess ? 0 : -1;
 #else
     (void)P;
@@ -772,8 +793,8 @@ void launch_fused_tc(const hpx_plan_s* P, float* alm, cudaStream_t s) {
     dim3 grid(P->fused_ntiles, (g.B + 31) / 32);
 #if HPX_TC_F16
     const size_t smem_h = NSH * TILE_A + NB * 2 * TILE_H + NBR * TILE_R;
-    cudaFuncSetAttribute(fused_tc_ws_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_h);
-    fused_tc_ws_kernel<<<grid, NTW, smem_h, s>>>((const unsigned char*)P->fusedM, P->tcOff, P->tcRinv, P->fusedTiles,
+    cudaFuncSetAttribute(fused_tc_ws_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_h);
+    fused_tc_ws_kernel<false><<<grid, NTW, smem_h, s>>>((const unsigned char*)P->fusedM, P->tcOff, P->tcRinv, P->fusedTiles,
                                                  (const cplx<float>*)P->bvec, P->bscale, (cplx<float>*)alm, g.P2,
                                                  g.p, g.L, g.B, g.nalm, P->d_status);
 #else
@@ -782,6 +803,103 @@ void launch_fused_tc(const hpx_plan_s* P, float* alm, cudaStream_t s) {
     fused_tc_tmem_kernel<<<grid, NT, smem_t, s>>>((const float*)P->fusedM, P->tcOff, P->fusedTiles,
                                                   (const cplx<float>*)P->bvec, (cplx<float>*)alm, g.P2, g.p, g.L,
                                                   g.B, g.nalm, P->d_status);
+#endif
+}
+
+// D (FP32, [mpar][par][q][k], P2 x P2 per block) -> tile u of rows i0.. of
+// block blk in the FP32 core-matrix layout of the operator tiles (K-chunks of
+// rp x 32; rows and k past P2 zero).  One block of 128 threads per tile,
+// thread = row.
+__global__ void __launch_bounds__(TM) dense_tiles_kernel(const float* __restrict__ D, float* __restrict__ Mt,
+                                                         const int64_t* __restrict__ tcOff,
+                                                         const int* __restrict__ tiles, int P2) {
+    const int blk = tiles[3 * blockIdx.x], i0 = tiles[3 * blockIdx.x + 2];
+    const int rp = (min(TM, P2 - i0) + 7) & ~7;
+    const int nchunks = (P2 + KC - 1) / KC;
+    const int r = threadIdx.x;
+    if (r >= rp) return;
+    const int q = i0 + r;
+    const float* src = D + ((size_t)blk * P2 + min(q, P2 - 1)) * P2;
+    float* At = Mt + tcOff[blockIdx.x];
+    for (int ch = 0; ch < nchunks; ++ch)
+        for (int kk = 0; kk < KC; ++kk) {
+            const int k = ch * KC + kk;
+            const float v = (q < P2 && k < P2) ? src[k] : 0.f;
+            At[(int64_t)ch * rp * 32 + (r >> 3) * 256 + (kk >> 2) * 32 + (r & 7) * 4 + (kk & 3)] = v;
+        }
+}
+
+int prepare_dense_tc(hpx_plan_s* P) {
+#if HPX_TC_F16
+    const auto& g = P->g;
+    const int nch = (g.P2 + KC - 1) / KC;
+    const int nti = (g.P2 + TM - 1) / TM;
+    // the 4 x nti distinct tiles of D, then one CTA tile per (m, par, row tile)
+    std::vector<int> utiles;
+    std::vector<int64_t> uoff;
+    int64_t o = 0, rows = 0;
+    for (int blk = 0; blk < 4; ++blk)
+        for (int ti = 0; ti < nti; ++ti) {
+            const int i0 = ti * TM, rp = (std::min(TM, g.P2 - i0) + 7) & ~7;
+            utiles.insert(utiles.end(), {blk, 0, i0});
+            uoff.push_back(o);
+            o += (int64_t)nch * rp * 32;
+            rows += rp;
+        }
+    std::vector<int> tiles;
+    std::vector<int64_t> off;
+    for (int m = 0; m <= g.L; ++m)
+        for (int par = 0; par < 2; ++par)
+            for (int ti = 0; ti < nti; ++ti) {
+                tiles.insert(tiles.end(), {m, par, ti * TM});
+                off.push_back(uoff[(size_t)((m & 1) * 2 + par) * nti + ti]);
+            }
+    int *du = nullptr, *dt = nullptr;
+    int64_t *duo = nullptr, *dto = nullptr;
+    const size_t bb = (size_t)g.B * (g.L + 1) * sizeof(float);
+    bool ok = cudaMalloc(&P->dTC, (size_t)o * 4) == cudaSuccess &&
+              cudaMalloc(&P->dRinv, (size_t)rows * 4) == cudaSuccess &&
+              cudaMalloc(&du, utiles.size() * sizeof(int)) == cudaSuccess &&
+              cudaMalloc(&duo, uoff.size() * sizeof(int64_t)) == cudaSuccess &&
+              cudaMalloc(&dt, tiles.size() * sizeof(int)) == cudaSuccess &&
+              cudaMalloc(&dto, off.size() * sizeof(int64_t)) == cudaSuccess &&
+              (P->bscale || cudaMalloc(&P->bscale, bb) == cudaSuccess);
+    if (ok) {
+        cudaMemcpy(du, utiles.data(), utiles.size() * sizeof(int), cudaMemcpyHostToDevice);
+        cudaMemcpy(duo, uoff.data(), uoff.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
+        cudaMemcpy(dt, tiles.data(), tiles.size() * sizeof(int), cudaMemcpyHostToDevice);
+        cudaMemcpy(dto, off.data(), off.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
+        const int nu = (int)uoff.size();
+        dense_tiles_kernel<<<nu, TM>>>((const float*)P->t.D, (float*)P->dTC, duo, du, g.P2);
+        tc_to_f16_kernel<<<nu, TM>>>((float*)P->dTC, duo, du, g.P2, g.L, (float*)P->dRinv, g.P2);
+        ok = cudaDeviceSynchronize() == cudaSuccess;
+    }
+    if (du) cudaFree(du);
+    if (duo) cudaFree(duo);
+    P->dTiles = dt;
+    P->dTcOff = dto;
+    P->dNtiles = (int)off.size();
+    P->bytes += (int64_t)o * 4 + rows * 4 + (int64_t)bb + (int64_t)(tiles.size() * sizeof(int) + off.size() * 8);
+    return ok ? 0 : -1;
+#else
+    (void)P;
+    return 0;
+#endif
+}
+
+void launch_dense_tc(const hpx_plan_s* P, cudaStream_t s) {
+#if HPX_TC_F16
+    const auto& g = P->g;
+    dim3 grid(P->dNtiles, (g.B + 31) / 32);
+    const size_t smem_h = NSH * TILE_A + NB * 2 * TILE_H + NBR * TILE_R;
+    cudaFuncSetAttribute(fused_tc_ws_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_h);
+    fused_tc_ws_kernel<true><<<grid, NTW, smem_h, s>>>((const unsigned char*)P->dTC, P->dTcOff, (const float*)P->dRinv,
+                                                       P->dTiles, (const cplx<float>*)P->bvec, P->bscale,
+                                                       (cplx<float>*)P->beta, g.P2, g.p, g.L, g.B, g.nalm,
+                                                       P->d_status);
+#else
+    (void)P;
+    (void)s;
 #endif
 }
 

@@ -379,7 +379,7 @@ __device__ __forceinline__ cplx<float> prewhiten_inverse(int j) {
 }
 
 template <class T, int LOGM, int NT>
-__global__ void __launch_bounds__(NT, (LOGM <= 13 ? 1024 / NT : 1)) lat_fft_pair_ct_kernel(
+__global__ void __launch_bounds__(NT, ((1 << LOGM) / NT == 16 ? (LOGM <= 13 ? 1024 / NT : 1) : 512 / NT)) lat_fft_pair_ct_kernel(
     const cplx<T>* __restrict__ U, cplx<T>* __restrict__ bvec, const T* __restrict__ dec,
     const cplx<T>* __restrict__ tw, int twlen, int p, int L, int P2, int ldu, float* __restrict__ bscale) {
     constexpr int M = 1 << LOGM;
@@ -471,8 +471,9 @@ void launch_lat_fft(const hpx_plan_s* P, cudaStream_t s) {
                                                (const cplx<T>*)P->t.twid, g.Lmax, g.p, g.L, g.P2, P->ldu,
                                                P->bscale);
         };
-        if (logM == 12) run(lat_fft_pair_ct_kernel<T, 12, 256>, 256);
-        else if (logM == 13) run(lat_fft_pair_ct_kernel<T, 13, 512>, 512);
+        const bool e32 = P->latE == 32;   // elements per thread (the plan's tuning), else 16
+        if (logM == 12) { if (e32) run(lat_fft_pair_ct_kernel<T, 12, 128>, 128); else run(lat_fft_pair_ct_kernel<T, 12, 256>, 256); }
+        else if (logM == 13) { if (e32) run(lat_fft_pair_ct_kernel<T, 13, 256>, 256); else run(lat_fft_pair_ct_kernel<T, 13, 512>, 512); }
         else run(lat_fft_pair_ct_kernel<T, 14, 512>, 512);
         return;
     }

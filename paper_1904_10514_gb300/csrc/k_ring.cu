@@ -79,12 +79,13 @@ __device__ __forceinline__ void ring_rows_out(BUF zat, int n, int p, int L, cons
 // (fft_ct.cuh), and the kind of ring is known, so neither transform carries
 // the other's code.
 template <class T, int LOGN, int NT, bool BLUE>
-__global__ void __launch_bounds__(NT, (LOGN <= 13 ? 1024 / NT : 1)) ring_ct_kernel(
+__global__ void __launch_bounds__(NT, ((1 << LOGN) / NT == 16 ? (LOGN <= 13 ? 1024 / NT : 1) : 512 / NT)) ring_ct_kernel(
     const T* __restrict__ maps, cplx<T>* __restrict__ Y, const int* __restrict__ nphi_t,
     const int* __restrict__ startN_t, const int* __restrict__ startS_t, const int64_t* __restrict__ shOff_t,
     const int64_t* __restrict__ chOff_t, const int64_t* __restrict__ bhOff_t, const cplx<T>* __restrict__ shift,
     const cplx<T>* __restrict__ chirp, const cplx<T>* __restrict__ bhat, const cplx<T>* __restrict__ tw, int twlen,
-    int p, int Q, int64_t npix, const int* __restrict__ ringlist, T ew, const int* __restrict__ shifted_t, int L) {
+    int p, int Q, int64_t npix, const int* __restrict__ ringlist, T ew, const int* __restrict__ shifted_t, int L,
+    const int64_t* __restrict__ mapIdx) {
     extern __shared__ unsigned char smem_raw[];
     cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw);
     const int i = ringlist[blockIdx.y];
@@ -92,7 +93,7 @@ __global__ void __launch_bounds__(NT, (LOGN <= 13 ? 1024 / NT : 1)) ring_ct_kern
     const int n = nphi_t[i];
     const int sN = startN_t[i], sS = startS_t[i];
     const bool equator = (sN == sS);
-    const T* f = maps + (int64_t)b * npix;
+    const T* f = maps + (mapIdx ? mapIdx[b] : (int64_t)b * npix);
     const int tid = threadIdx.x;
     const int twstep = twlen >> LOGN;
     auto sample = [&](int k) { return mk<T>(f[sN + k], equator ? T(0) : f[sS + k]); };
@@ -127,11 +128,11 @@ __device__ __forceinline__ void ring_pair(
     const int64_t* __restrict__ shOff_t, const int64_t* __restrict__ chOff_t, const int64_t* __restrict__ bhOff_t,
     const cplx<T>* __restrict__ shift, const cplx<T>* __restrict__ chirp, const cplx<T>* __restrict__ bhat,
     const cplx<T>* __restrict__ tw, int twlen, int p, int Q, int64_t npix, T ew, const int* __restrict__ shifted_t,
-    int L) {
+    int L, const int64_t* __restrict__ mapIdx) {
     const int n = nphi_t[i];
     const int sN = startN_t[i], sS = startS_t[i];
     const bool equator = (sN == sS);
-    const T* f = maps + (int64_t)b * npix;
+    const T* f = maps + (mapIdx ? mapIdx[b] : (int64_t)b * npix);
     const int tid = threadIdx.x, nt = blockDim.x;
 
     auto sample = [&](int k) { return mk<T>(f[sN + k], equator ? T(0) : f[sS + k]); };
@@ -191,51 +192,62 @@ __global__ void __launch_bounds__(kRingThreads, (E <= 16 ? 2 : 1)) ring_fft_kern
     const int64_t* __restrict__ chOff_t, const int64_t* __restrict__ bhOff_t,
     const cplx<T>* __restrict__ shift, const cplx<T>* __restrict__ chirp,
     const cplx<T>* __restrict__ bhat, const cplx<T>* __restrict__ tw, int twlen, int p, int Q,
-    int64_t npix, int npairs, const int* __restrict__ ringlist, T ew, const int* __restrict__ shifted_t, int L) {
+    int64_t npix, int npairs, const int* __restrict__ ringlist, T ew, const int* __restrict__ shifted_t, int L,
+    const int64_t* __restrict__ mapIdx) {
     extern __shared__ unsigned char smem_raw[];
     cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw);
     // largest rings first: blockIdx.y = 0 is the equator
     const int i = ringlist ? ringlist[blockIdx.y] : npairs - 1 - (int)blockIdx.y;
     ring_pair<T, E>(buf, i, blockIdx.x, maps, Y, nphi_t, startN_t, startS_t, pow2_t, logn_t, fftL_t, logL_t, shOff_t,
-                    chOff_t, bhOff_t, shift, chirp, bhat, tw, twlen, p, Q, npix, ew, shifted_t, L);
+                    chOff_t, bhOff_t, shift, chirp, bhat, tw, twlen, p, Q, npix, ew, shifted_t, L, mapIdx);
 }
 
-// The ring stage of every sub-plan of an uneven batch in one persistent launch:
-// the blocks walk a work list of (sub-plan, ring pair, map) items, built at
-// plan time with the longest transforms first, in strides of the grid size; the
-// sub-plans' tables and workspaces come from the job table.  Maps of a
-// sub-plan used in place are read from the caller's array (maps_base plus the
-// job's element offset), gathered ones from the sub-plan's staging buffer.
-template <class T, int E>
-__global__ void __launch_bounds__(kRingThreads, 1) ring_list_kernel(const RingJob<T>* __restrict__ jobs,
-                                                                     const int4* __restrict__ items, int nitems,
-                                                                     const T* __restrict__ maps_base) {
+// The short-ring part of the ring stage of every sub-plan of an uneven batch
+// in persistent launches: the blocks walk a work list of (sub-plan, ring pair,
+// map) items with transforms shorter than kRingCtMin points, built at plan time
+// with the longest transforms first, in strides of the grid size; the
+// sub-plans' tables and workspaces come from the job table.  The maps are read
+// from the caller's array: those of a sub-plan whose maps are adjacent at the
+// job's element offset from maps_base, the others at their own offsets (the
+// job's mapIdx table).  NT
+// threads per block (16 elements per thread): 128 for the items of 1024 and
+// 2048 points, 32 for the shorter ones, each group its own launch.  The
+// longer transforms run in the sub-plans' compile-time kernels.
+template <class T, int NT>
+__global__ void __launch_bounds__(NT, (NT == 32 ? 16 : 8)) ring_list_kernel(const RingJob<T>* __restrict__ jobs,
+                                                                          const int4* __restrict__ items,
+                                                                          int nitems, const T* __restrict__ maps_base) {
     extern __shared__ unsigned char smem_raw[];
     cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw);
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
         const int4 w = items[it];
         const RingJob<T>& J = jobs[w.x];
-        const T* maps = J.staged ? J.staged : maps_base + J.mapoff;
-        ring_pair<T, E>(buf, w.y, w.z, maps, J.Y, J.nphi, J.startN, J.startS, J.pow2, J.logn, J.fftL, J.logL,
-                        J.shOff, J.chOff, J.bhOff, J.shift, J.chirp, J.bhat, J.tw, J.twlen, J.p, J.Q, J.npix, T(0),
-                        J.shifted, J.L);
+        ring_pair<T, 16>(buf, w.y, w.z, maps_base + J.mapoff, J.Y, J.nphi, J.startN, J.startS, J.pow2, J.logn,
+                         J.fftL, J.logL, J.shOff, J.chOff, J.bhOff, J.shift, J.chirp, J.bhat, J.tw, J.twlen, J.p, J.Q,
+                         J.npix, T(0), J.shifted, J.L, J.mapIdx);
         __syncthreads();   // the next item overwrites the shared buffer
     }
 }
 
 template <class T>
-void launch_ring_list(const RingJob<T>* jobs, const int4* items, int nitems, int maxN, int blocks, const T* maps_base,
+void launch_ring_list(const RingJob<T>* jobs, const int4* items, int nitems, int nlong, const T* maps_base,
                       cudaStream_t s) {
-    const bool big = maxN > 16 * kRingThreads;
-    const size_t smem = (size_t)(maxN + maxN / 16) * sizeof(cplx<T>);
-    auto kern = big ? ring_list_kernel<T, 32> : ring_list_kernel<T, 16>;
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    kern<<<blocks, kRingThreads, smem, s>>>(jobs, items, nitems, maps_base);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    auto run = [&](auto kern, int threads, int maxN, const int4* first, int n, int perSM) {
+        if (n <= 0) return;
+        const size_t smem = (size_t)(maxN + maxN / 16) * sizeof(cplx<T>);
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        kern<<<std::min(n, sms * perSM), threads, smem, s>>>(jobs, first, n, maps_base);
+    };
+    // items [0, nlong): 1024 or 2048 points; [nlong, nitems): 512 or fewer
+    run(ring_list_kernel<T, 128>, 128, 2048, items, nlong, 8);
+    run(ring_list_kernel<T, 32>, 32, 512, items + nlong, nitems - nlong, 16);
 }
 
-template void launch_ring_list<float>(const RingJob<float>*, const int4*, int, int, int, const float*, cudaStream_t);
-template void launch_ring_list<double>(const RingJob<double>*, const int4*, int, int, int, const double*,
-                                       cudaStream_t);
+template void launch_ring_list<float>(const RingJob<float>*, const int4*, int, int, const float*, cudaStream_t);
+template void launch_ring_list<double>(const RingJob<double>*, const int4*, int, int, const double*, cudaStream_t);
 
 // Pole values (Sec. 3.2.1): a fixed linear functional of the samples of the
 // three rings nearest each pole (unit-weight quadratic least squares in the
@@ -244,9 +256,10 @@ template void launch_ring_list<double>(const RingJob<double>*, const int4*, int,
 template <class T>
 __global__ void pole_kernel(const T* __restrict__ maps, cplx<T>* __restrict__ Y,
                             const int* __restrict__ poleN, const int* __restrict__ poleS,
-                            const double* __restrict__ w, int npole, int p, int Q, int64_t npix) {
+                            const double* __restrict__ w, int npole, int p, int Q, int64_t npix,
+                            const int64_t* __restrict__ mapIdx) {
     const int b = blockIdx.x;
-    const T* f = maps + (int64_t)b * npix;
+    const T* f = maps + (mapIdx ? mapIdx[b] : (int64_t)b * npix);
     __shared__ double red[2][32];
     double sn = 0.0, ss = 0.0;
     for (int k = threadIdx.x; k < npole; k += blockDim.x) {
@@ -276,7 +289,7 @@ __global__ void pole_kernel(const T* __restrict__ maps, cplx<T>* __restrict__ Y,
 }
 
 template <class T>
-void launch_ring_fft(const hpx_plan_s* P, const T* maps, cudaStream_t s, T ew) {
+void launch_ring_fft(const hpx_plan_s* P, const T* maps, cudaStream_t s, T ew, int minN) {
     const auto& g = P->g;
     const auto& t = P->t;
     auto launch = [&](int N, int nrings, const int* list) {
@@ -290,7 +303,7 @@ void launch_ring_fft(const hpx_plan_s* P, const T* maps, cudaStream_t s, T ew) {
         kern<<<grid, threads, smem, s>>>(
             maps, (cplx<T>*)P->Y, t.nphi, t.startN, t.startS, t.pow2, t.logn, t.fftL, t.logL, t.shOff,
             t.chOff, t.bhOff, (const cplx<T>*)t.shift, (const cplx<T>*)t.chirp, (const cplx<T>*)t.bhat,
-            (const cplx<T>*)t.twid, g.Lmax, g.p, g.Q, g.npix, g.npairs, list, ew, t.shifted, g.L);
+            (const cplx<T>*)t.twid, g.Lmax, g.p, g.Q, g.npix, g.npairs, list, ew, t.shifted, g.L, P->mapIdx);
     };
     if (!P->ringList) {   // one launch sized for the largest transform
         launch(g.smem_ring, g.npairs, nullptr);
@@ -299,6 +312,7 @@ void launch_ring_fft(const hpx_plan_s* P, const T* maps, cudaStream_t s, T ew) {
     // one launch per transform length (and kind, from 4096 points up), blocks
     // sized to it, longest first
     for (const auto& c : P->ringClasses) {
+        if (c.N < minN) continue;
         if (c.N < kRingCtMin) {
             launch(c.N, c.count, P->ringList + c.first);
             continue;
@@ -310,13 +324,18 @@ void launch_ring_fft(const hpx_plan_s* P, const T* maps, cudaStream_t s, T ew) {
             kern<<<grid, threads, smem, s>>>(maps, (cplx<T>*)P->Y, t.nphi, t.startN, t.startS, t.shOff, t.chOff,
                                              t.bhOff, (const cplx<T>*)t.shift, (const cplx<T>*)t.chirp,
                                              (const cplx<T>*)t.bhat, (const cplx<T>*)t.twid, g.Lmax, g.p, g.Q,
-                                             g.npix, P->ringList + c.first, ew, t.shifted, g.L);
+                                             g.npix, P->ringList + c.first, ew, t.shifted, g.L, P->mapIdx);
         };
+        // elements per thread: 16 (N / 16 threads) or, when the plan's tuning chose
+        // it, 32 (N / 32 threads, two groups per thread and pass)
+        const bool e32 = P->ringE == 32;
         if (c.N == 4096) {
-            if (c.blue) run(ring_ct_kernel<T, 12, 256, true>, 256);
+            if (e32) { if (c.blue) run(ring_ct_kernel<T, 12, 128, true>, 128); else run(ring_ct_kernel<T, 12, 128, false>, 128); }
+            else if (c.blue) run(ring_ct_kernel<T, 12, 256, true>, 256);
             else run(ring_ct_kernel<T, 12, 256, false>, 256);
         } else if (c.N == 8192) {
-            if (c.blue) run(ring_ct_kernel<T, 13, 512, true>, 512);
+            if (e32) { if (c.blue) run(ring_ct_kernel<T, 13, 256, true>, 256); else run(ring_ct_kernel<T, 13, 256, false>, 256); }
+            else if (c.blue) run(ring_ct_kernel<T, 13, 512, true>, 512);
             else run(ring_ct_kernel<T, 13, 512, false>, 512);
         } else {
             if (c.blue) run(ring_ct_kernel<T, 14, 512, true>, 512);
@@ -329,11 +348,11 @@ template <class T>
 void launch_poles(const hpx_plan_s* P, const T* maps, cudaStream_t s) {
     const auto& g = P->g;
     pole_kernel<T><<<g.B, 128, 0, s>>>(maps, (cplx<T>*)P->Y, P->t.poleN, P->t.poleS, P->t.polew,
-                                       P->t.npole, g.p, g.Q, g.npix);
+                                       P->t.npole, g.p, g.Q, g.npix, P->mapIdx);
 }
 
-template void launch_ring_fft<float>(const hpx_plan_s*, const float*, cudaStream_t, float);
-template void launch_ring_fft<double>(const hpx_plan_s*, const double*, cudaStream_t, double);
+template void launch_ring_fft<float>(const hpx_plan_s*, const float*, cudaStream_t, float, int);
+template void launch_ring_fft<double>(const hpx_plan_s*, const double*, cudaStream_t, double, int);
 template void launch_poles<float>(const hpx_plan_s*, const float*, cudaStream_t);
 template void launch_poles<double>(const hpx_plan_s*, const double*, cudaStream_t);
 

@@ -104,7 +104,22 @@ struct hpx_plan_s {
     void* synM = nullptr;          // T, n_alm x ldm row-major: synthesis operators R_{m,c} Es (HPX_FLAG_SYNTHESIS)
     void* jres = nullptr;          // T [B][npix]: Jacobi residual maps (HPX_FLAG_JACOBI)
     void* jalm = nullptr;          // cplx<T> [B][n_alm]: Jacobi update
+    // sub-plan of an uneven batch whose maps are not adjacent in the caller's
+    // array: element offset of each of its maps there (read by the ring and pole
+    // stages of the analysis, which then take the caller's base pointer)
+    int64_t* mapIdx = nullptr;
+    // sweeps path of FP32 plans of 4 maps or more, nside <= 1024: D on the tensor cores
+    // (prepare_dense_tc): its distinct tiles in the FP16-pair form, 1 / row scale,
+    // and the CTA tiles (m, par, first row) with their operator offsets
+    void* dTC = nullptr;
+    void* dRinv = nullptr;
+    int* dTiles = nullptr;
+    int64_t* dTcOff = nullptr;
+    int dNtiles = 0;
     float tuned_ms[2] = {0.f, 0.f};   // HPX_FLAG_AUTOTUNE: ms per analysis, operators / sweeps
+    // launch shapes of the compile-time FFT kernels: elements per thread (16 or 32)
+    // of the ring stage and of the grid FFT (HPX_FLAG_AUTOTUNE times both)
+    int ringE = 16, latE = 16;
 
     // uneven batches (group plans): one uniform sub-plan per distinct nside
     bool group = false;
@@ -125,7 +140,8 @@ struct hpx_plan_s {
     cudaEvent_t sfork = nullptr;             // fork event on the group's stream
     void* ringJobs = nullptr;                // RingJob<T> per sub-plan (persistent ring kernel)
     int4* ringItems = nullptr;               // (sub-plan, ring pair, map, length), longest first
-    int nRingItems = 0, ringMaxN = 0, ringBlocks = 0;
+    int nRingItems = 0, nRingLong = 0;   // items, of which the first nRingLong have 1024 or 2048 points
+    cudaEvent_t ringEv = nullptr;        // recorded after the short-ring launches
     int64_t total_npix = 0, total_nalm = 0, total_ncl = 0;
 
     // CUDA graphs of hpx_analyze (HPX_FLAG_GRAPH)
@@ -145,8 +161,8 @@ namespace hpx {
 // buffer; else the caller's array plus mapoff elements).
 template <class T>
 struct RingJob {
-    const T* staged;
-    int64_t mapoff;
+    int64_t mapoff;            // element offset of the sub-plan's first map (adjacent maps)
+    const int64_t* mapIdx;     // else: element offset of each of its maps
     cplx<T>* Y;
     const int *nphi, *startN, *startS, *pow2, *logn, *fftL, *logL, *shifted;
     const int64_t *shOff, *chOff, *bhOff;
@@ -155,7 +171,7 @@ struct RingJob {
     int64_t npix;
 };
 template <class T>
-void launch_ring_list(const RingJob<T>* jobs, const int4* items, int nitems, int maxN, int blocks, const T* maps_base,
+void launch_ring_list(const RingJob<T>* jobs, const int4* items, int nitems, int nlong, const T* maps_base,
                       cudaStream_t s);
 
 // ring transforms of this many points or more run in launches of one length and
@@ -164,7 +180,8 @@ constexpr int kRingCtMin = 4096;
 
 // ew != 0: the rows of the equal-weight quadrature's ring stage (every m <= lmax,
 // aliased mod nphi, synthesis fold weights, times ew) instead of the analysis'
-template <class T> void launch_ring_fft(const hpx_plan_s* P, const T* maps, cudaStream_t s, T ew = T(0));
+// ring classes of minN points or more only (minN > 0: the rest ran elsewhere)
+template <class T> void launch_ring_fft(const hpx_plan_s* P, const T* maps, cudaStream_t s, T ew = T(0), int minN = 0);
 template <class T> void launch_poles(const hpx_plan_s* P, const T* maps, cudaStream_t s);
 template <class T> void launch_nufft(const hpx_plan_s* P, cudaStream_t s);
 template <class T> void launch_spread(const hpx_plan_s* P, cudaStream_t s);
@@ -185,6 +202,10 @@ void launch_fused_tc(const hpx_plan_s* P, float* alm, cudaStream_t s);
 // after build_fused<float> of the tensor-core layout: converts M to the form
 // launch_fused_tc reads (and allocates its scale arrays); 0 on success
 int prepare_fused_tc(hpx_plan_s* P);
+// D of the sweeps path on the tensor cores: plan-time layout (0 on success) and
+// the launch (bvec -> beta, like launch_dense)
+int prepare_dense_tc(hpx_plan_s* P);
+void launch_dense_tc(const hpx_plan_s* P, cudaStream_t s);
 void launch_timeout_selftest(const hpx_plan_s* P, int spins, cudaStream_t s);
 // HPX_FLAG_CHECKED: records HPX_ERR_NONFINITE in *status if any of the n reals
 // (float or double) at x is NaN or infinite.

@@ -330,6 +330,30 @@ def test_autotune_keeps_a_correct_path(hp, prec, nside, B):
         assert per_l_error(a[b], ref[b], 2 * nside).max() < TOL[prec]
 
 
+def test_launch_shapes_give_identical_results(hp):
+    """The ring-FFT and grid-FFT kernels with 16 or 32 elements per thread run the
+    same radix passes in the same order, so every launch shape (and whatever
+    HPX_FLAG_AUTOTUNE picks) gives bit-identical coefficients; shapes outside
+    {16, 32} are refused."""
+    ns, B = 1024, 2
+    rng = np.random.default_rng(71)
+    x = torch.as_tensor(rng.standard_normal((B, 12 * ns * ns)).astype(np.float32), device="cuda")
+    plan = hp.Plan(ns, -1, B, "fp32", sweeps=True, autotune=True)
+    assert plan.tuning[0] in (16, 32) and plan.tuning[1] in (16, 32)
+    tuned = plan.analyze(x).clone()
+    outs = []
+    for shapes in ((16, 16), (32, 32), (16, 32)):
+        plan.tuning = shapes
+        assert plan.tuning == shapes
+        outs.append(plan.analyze(x).clone())
+    torch.cuda.synchronize()
+    for o in outs:
+        assert torch.equal(o, tuned)
+    for bad in ((8, 16), (16, 64), (0, 0)):
+        with pytest.raises(hp.HpxError):
+            plan.tuning = bad
+
+
 def test_graph_tensor_core_path_matches_eager(hp):
     """The tensor-core path overlaps grid FFTs and operators on two streams; a
     graph capture of it replays to the same coefficients as eager calls."""
@@ -372,17 +396,22 @@ def _damped_maps(nside, lmax, seeds):
     return skies.synthesize(alms, nside, lmax), alms
 
 
-def test_tensor_core_damped_spectrum_nside256(hp):
-    """The FP16-pair tensor-core kernel (FP32 plan, 10 maps) on noise-free skies
-    whose spectrum falls by exp(-(l/400)^2): every degree of every map within
-    1e-5 of the oracle, like the FP32-pipe kernel."""
+@pytest.mark.parametrize("sweeps", [False, True], ids=["operators", "sweeps"])
+def test_tensor_core_damped_spectrum_nside256(hp, sweeps):
+    """The FP16-pair tensor-core kernels (FP32 plan, 10 maps: the per-order
+    operators, or D ahead of the run-time sweeps) on noise-free skies whose
+    spectrum falls by exp(-(l/400)^2): every degree of every map within 1e-5 of
+    the oracle, like the FP32-pipe kernels (which give other bits)."""
     ns, L, B = 256, 512, 10
     maps, _ = _damped_maps(ns, L, range(9100, 9100 + B))
     maps = maps.astype(np.float32).astype(np.float64)
-    plan = hp.Plan(ns, L, B, "fp32")
-    assert not plan.flags & hp.HPX_FLAG_SWEEPS
-    a = plan.analyze(torch.as_tensor(maps, dtype=torch.float32, device="cuda"))
+    x = torch.as_tensor(maps, dtype=torch.float32, device="cuda")
+    plan = hp.Plan(ns, L, B, "fp32", sweeps=sweeps)
+    assert bool(plan.flags & hp.HPX_FLAG_SWEEPS) == sweeps
+    a = plan.analyze(x)
+    a_simt = hp.Plan(ns, L, B, "fp32", sweeps=sweeps, simt=True).analyze(x)
     plan.sync()
+    assert not torch.equal(a, a_simt)
     a = a.cpu().numpy().astype(np.complex128)
     ref = hp2sph.analyze(maps, ns, L)
     for b in range(B):
