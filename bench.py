@@ -31,8 +31,9 @@ METRIC = "HEALPix analysis Gpix/s at Nside=1024 (batched FP32 vs plain FP64, err
 NSIDE, LMAX, BATCH = 1024, 2048, 32
 WORKLOAD = "bench_nside1024x32"
 MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
-# measured DRAM traffic / algorithmic bytes of a kernel (ncu capture, Nside 512, 32 maps)
-TRAFFIC_OVER_ALGORITHMIC = {"fused_fsht": 1.5552 / 1.4829}
+# measured DRAM traffic / algorithmic bytes of a kernel (ncu capture, Nside 512, 32 maps:
+# fused_tc_ws_kernel with the packed FP16-pair right-hand sides, 1.4479 GB read + 0.1249 GB written)
+TRAFFIC_OVER_ALGORITHMIC = {"fused_fsht": (1.4479 + 0.1249) / 1.4828}
 # FP32 SIMT peak: 152 SMs x 128 FP32 lanes x 2 flop/FMA x 2.070 GHz (maximum SM clock)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 

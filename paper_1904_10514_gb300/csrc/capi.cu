@@ -73,7 +73,7 @@ void free_plan(hpx_plan_s* P) {
                     t.bhOff, t.shift, t.chirp, t.bhat, t.twid, t.poleN, t.poleS, t.polew, t.rowptr,
                     t.ent, t.entw, t.dec, t.D, t.tstart, t.hwn, t.angOff, t.ang, t.skOff, t.skew, t.skewT, t.nrowptr, t.nent, t.nentw, t.nstart, t.swts, t.hstart, t.hwts, t.Es, t.shifted, t.C, t.cgH, P->Y, P->U, P->bvec,
                     P->fusedM, P->fusedOff, P->fusedTiles, P->tcOff, P->tcFirst, P->tcRinv, P->bscale, P->d_status, P->synM, P->ringList,
-                    P->jres, P->jalm, P->dTC, P->dRinv, P->dTiles, P->dTcOff, P->mapIdx};
+                    P->jres, P->jalm, P->dTC, P->dRinv, P->dTiles, P->dTcOff, P->mapIdx, P->bpk};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     if (P->ev) {
@@ -95,7 +95,7 @@ int analyze_impl(hpx_plan_s* P, const void* maps, void* alm, bool rings = true) 
     if (ev) cudaEventRecord(ev[2], s);
     hpx::launch_spread<T>(P, s);
     if (ev) cudaEventRecord(ev[3], s);
-    hpx::launch_lat_fft<T>(P, s);
+    hpx::launch_lat_fft<T>(P, s, hpx::packs_b(P));
     if (ev) cudaEventRecord(ev[4], s);
     if (P->fusedM) {
         if constexpr (sizeof(T) == 4) {
@@ -453,7 +453,7 @@ float time_stage(hpx_plan_s* P, const void* maps, int stage, cudaEvent_t e0, cud
             else hpx::launch_lat_fft<double>(P, P->stream);
         } else {
             if (stage == 0) hpx::launch_ring_fft<float>(P, (const float*)maps, P->stream);
-            else hpx::launch_lat_fft<float>(P, P->stream);
+            else hpx::launch_lat_fft<float>(P, P->stream, hpx::packs_b(P));
         }
         cudaEventRecord(e1, P->stream);
         cudaEventSynchronize(e1);
@@ -531,7 +531,7 @@ int autotune(hpx_plan_s* P) {
     P->tuned_ms[1] = ms[1] / 3;
     if (ms[1] < ms[0]) {   // keep the sweeps: release the operators
         void* ptrs[] = {P->fusedM, P->synM ? nullptr : P->fusedOff, P->fusedTiles, P->tcOff, P->tcFirst,
-                        P->tcRinv, P->bscale};
+                        P->tcRinv, P->bscale, P->bpk};
         for (void* q : ptrs)
             if (q) cudaFree(q);
         P->fusedM = nullptr;
@@ -541,6 +541,7 @@ int autotune(hpx_plan_s* P) {
         P->tcFirst = nullptr;
         P->tcRinv = nullptr;
         P->bscale = nullptr;
+        P->bpk = nullptr;
         P->bytes -= P->fused_bytes;
         P->fused_bytes = 0;
         P->use_tc = false;

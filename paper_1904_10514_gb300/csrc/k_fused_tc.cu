@@ -31,6 +31,7 @@
 #include <algorithm>
 #include <cstdint>
 
+#include "fp16pair.cuh"
 #include "plan.h"
 #include "plan_math.h"
 
@@ -384,37 +385,38 @@ __global__ void __launch_bounds__(NT, 2) fused_tc_tmem_kernel(
 // column) maximum lose relative precision, with an absolute error below 2^-39
 // of that maximum.  The scales are undone in the epilogue.
 //
+// The right-hand sides arrive already split: the grid-FFT kernel that
+// produces b scales every column and writes its FP16 pairs in the MMA's B
+// layout (bpk: per map tile of 32, order m, parity and K-chunk one 8 KB block,
+// the hi copy then the lo copy, each 64 columns x 32 k in K-major core matrices
+// of 8 columns x 8 halves: 8-column groups 512 bytes apart, core matrices
+// adjacent in K 128 bytes apart; columns 0-31 the real parts of the 32 maps,
+// 32-63 the imaginary parts), so the kernel converts nothing.
+//
 // The kernel is warp-specialised; its roles meet only at mbarriers, so each
 // stream runs ahead by its own ring of stages:
-//   * warp 4 copies: one lane the operator chunks (hi block, then lo block,
-//     rp x 64 bytes each, K-major core matrices of 8 rows x 8 halves: 8-row
-//     groups 512 bytes apart, core matrices adjacent in K 128 bytes apart) by
-//     bulk copy into NSH shared-memory stages (fullA / emptyA), and all lanes
-//     the chunk's FP32 b values (32 maps x 32 k, 8-byte cp.async, rows padded
-//     to 272 bytes) into NBR raw stages (brawFull / brawEmpty);
+//   * warp 4 (one lane) copies each K-chunk's operator block (hi then lo,
+//     rp x 64 bytes each) and its 8 KB b block into one of NSH shared-memory
+//     stages by two bulk copies that complete on the stage's mbarrier (fullA /
+//     emptyA);
 //   * warp 5 (one lane) issues, per chunk, 2 K-steps x 3 kind::f16 MMAs
 //     (M = 128, N = 64, K = 16) into a fresh accumulator of NACC TMEM stages
-//     (64 columns each) and commits them to emptyA, emptyB and accFull;
-//   * warps 0-3 (128 workers) split the raw b of a chunk into the FP16 pair of
-//     B stages (NB stages; fullB / emptyB), and drain the
-//     accumulator of chunk c - LAG into FP32 registers (thread = TMEM lane =
-//     row; 32 real and 32 imaginary columns), then release it (accEmpty).
-// The operator tile needs no conversion in the kernel.  Every wait is bounded
-// and watches an abort flag: a role that gives up sets it, the others stop at
-// their next wait, and one thread then waits (bounded) for the bulk copies and
-// MMAs still in flight before the CTA releases its tensor memory.
+//     (64 columns each) and commits them to emptyA and accFull;
+//   * warps 0-3 (128 workers) drain each accumulator into FP32 registers
+//     (thread = TMEM lane = row; 32 real and 32 imaginary columns), release it
+//     (accEmpty), and write the tile's results.
+// Every wait is bounded and watches an abort flag: a role that gives up sets
+// it, the others stop at their next wait, and one thread then waits (bounded)
+// for the bulk copies and MMAs still in flight before the CTA releases its
+// tensor memory.
 
 constexpr int TILE_H = TN * KC * 2;   // bytes of one FP16 copy of a b chunk (4 KB)
-constexpr int NSH = 4;                // operator stages of the FP16 form
-constexpr int NB = 2;                 // b stages (hi, lo)
-constexpr int NBR = 3;                // raw FP32 b stages
-constexpr int BRS = 272;              // bytes per map in a raw b stage (32 complex + padding)
-constexpr int TILE_R = 32 * BRS;      // one raw b stage
+constexpr int TILE_BP = kBpkChunk;    // a b chunk's pair (hi, lo): 8 KB
+static_assert(TILE_BP == 2 * TILE_H, "packed b chunk: hi and lo copies");
+constexpr int NSH = 4;                // stages (operator chunk + b chunk)
 constexpr int NACC = 4;               // accumulator stages (TMEM, 64 columns each)
-constexpr int LAG = 2;                // workers drain chunk c - LAG after preparing chunk c
 constexpr int NW = 128;               // worker threads (warps 0-3)
 constexpr int NTW = NW + 64;          // + the copy warp and the MMA warp
-static_assert(LAG < NACC, "the MMA of chunk c must not wait for the drain of chunk c - NACC");
 
 // Instruction descriptor: kind::f16, D = F32, A = B = F16, both K-major,
 // M = 128, N = 64.
@@ -429,19 +431,12 @@ __device__ __forceinline__ void mma_f16(uint32_t dtmem, uint64_t adesc, uint64_t
         : "r"(dtmem), "l"(adesc), "l"(bdesc), "r"(kIdescH), "r"(acc));
 }
 
-// The FP16 pair of x (already scaled), packed two values per 32-bit word
-// (the first one in the low half, i.e. at the lower address).
-struct HalfPair {
-    __half hi, lo;
-};
-__device__ __forceinline__ HalfPair split_h(float x) {
-    const __half h = __float2half_rn(x);
-    return HalfPair{h, __float2half_rn(x - __half2float(h))};
+// Bulk copy with the default L2 policy (data that other CTAs read again).
+__device__ __forceinline__ void bulk_g2s_keep(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(mbar)
+                 : "memory");
 }
-__device__ __forceinline__ uint32_t pack_h(__half a, __half b) {
-    return (uint32_t)__half_as_ushort(a) | ((uint32_t)__half_as_ushort(b) << 16);
-}
-
 
 // Bounded wait that also gives up when another role has set *abort.
 __device__ __forceinline__ bool ws_wait(uint32_t mbar, uint32_t parity, volatile int* abort) {
@@ -471,18 +466,17 @@ __device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
 // (m, par, i0) = rows q = i0.. of D[m & 1][par] applied to the columns
 // b[map][m][par], output into beta[m][par][q][map] for the Givens sweeps; the
 // tiles of all orders of one parity point at the same operator data, which
-// stays resident in L2.
+// stays resident in L2 (default copy policy; the per-order operators are
+// streamed once per call and copied evict-first).
 template <bool DENSE>
 __global__ void __launch_bounds__(NTW, 2) fused_tc_ws_kernel(
     const unsigned char* __restrict__ Mh, const int64_t* __restrict__ tcOff, const float* __restrict__ tcRinv,
-    const int* __restrict__ tiles, const cplx<float>* __restrict__ bvec, const float* __restrict__ bscale,
+    const int* __restrict__ tiles, const unsigned char* __restrict__ bpk, const float* __restrict__ bscale,
     cplx<float>* __restrict__ alm, int P2, int p, int L, int B, int64_t nalm, int* __restrict__ status) {
     extern __shared__ __align__(1024) unsigned char smem_w[];
     unsigned char* const sA = smem_w;                  // NSH x TILE_A: operator chunks (hi, lo)
-    unsigned char* const sB = smem_w + NSH * TILE_A;   // NB x (Bhi, Blo), TILE_H each
-    unsigned char* const sR = sB + NB * 2 * TILE_H;     // NBR x TILE_R: raw b
-    __shared__ __align__(8) uint64_t fullA[NSH], emptyA[NSH], fullB[NB], emptyB[NB], accFull[NACC],
-        accEmpty[NACC], brawFull[NBR], brawEmpty[NBR];
+    unsigned char* const sB = smem_w + NSH * TILE_A;   // NSH x TILE_BP: b chunks (hi, lo)
+    __shared__ __align__(8) uint64_t fullA[NSH], emptyA[NSH], accFull[NACC], accEmpty[NACC];
     __shared__ uint32_t tmem_base;
     __shared__ int abort_, issuedA, seenA, committed;
     __shared__ float tinv[TN / 2];   // 1 / column scale of each map of the tile
@@ -508,17 +502,9 @@ __global__ void __launch_bounds__(NTW, 2) fused_tc_ws_kernel(
             mbar_init(smem_u32(&fullA[q]), 1);
             mbar_init(smem_u32(&emptyA[q]), 1);
         }
-        for (int q = 0; q < NB; ++q) {
-            mbar_init(smem_u32(&fullB[q]), NW);
-            mbar_init(smem_u32(&emptyB[q]), 1);
-        }
         for (int q = 0; q < NACC; ++q) {
             mbar_init(smem_u32(&accFull[q]), 1);
             mbar_init(smem_u32(&accEmpty[q]), NW);
-        }
-        for (int q = 0; q < NBR; ++q) {
-            mbar_init(smem_u32(&brawFull[q]), 32);   // one asynchronous arrival per copying lane
-            mbar_init(smem_u32(&brawEmpty[q]), NW);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         abort_ = 0;
@@ -537,43 +523,31 @@ __global__ void __launch_bounds__(NTW, 2) fused_tc_ws_kernel(
 
     if (warp == 4) {
         // ---------------------------------------------------------- copies
-        const unsigned char* At = Mh + tcOff[blockIdx.x] * 4;
-        for (int ch = 0; ch < nchunks; ++ch) {
-            const int s = ch % NSH, r = ch % NBR;
-            if (ch >= NSH && !ws_wait(smem_u32(&emptyA[s]), (uint32_t)((ch / NSH + 1) & 1), abort)) break;
-            if (lane == 0) {
+        if (lane == 0) {
+            const unsigned char* At = Mh + tcOff[blockIdx.x] * 4;
+            const unsigned char* Bt = bpk + (((int64_t)blockIdx.y * (L + 1) + m) * 2 + par) * nchunks * TILE_BP;
+            for (int ch = 0; ch < nchunks; ++ch) {
+                const int s = ch % NSH;
+                if (ch >= NSH && !ws_wait(smem_u32(&emptyA[s]), (uint32_t)((ch / NSH + 1) & 1), abort)) break;
                 const uint32_t fb = smem_u32(&fullA[s]);
-                mbar_expect_tx(fb, chunkBytes);
-                bulk_g2s(smem_u32(sA + s * TILE_A), At + (int64_t)ch * chunkBytes, chunkBytes, fb);
+                mbar_expect_tx(fb, chunkBytes + TILE_BP);
+                if (DENSE) bulk_g2s_keep(smem_u32(sA + s * TILE_A), At + (int64_t)ch * chunkBytes, chunkBytes, fb);
+                else bulk_g2s(smem_u32(sA + s * TILE_A), At + (int64_t)ch * chunkBytes, chunkBytes, fb);
+                bulk_g2s_keep(smem_u32(sB + s * TILE_BP), Bt + (int64_t)ch * TILE_BP, TILE_BP, fb);
                 issuedA = ch + 1;
             }
-            if (ch >= NBR && !ws_wait(smem_u32(&brawEmpty[r]), (uint32_t)((ch / NBR + 1) & 1), abort)) break;
-            // lane = k within the chunk; zero fill past P2 and past the last map
-            const int k = ch * KC + lane;
-            unsigned char* dst = sR + r * TILE_R + lane * 8;
-#pragma unroll 8
-            for (int q = 0; q < TN / 2; ++q) {
-                const int bm = b0 + q;
-                const bool okb = bm < B && k < P2;
-                const cplx<float>* src = bvec + (((int64_t)min(bm, B - 1) * (p + 1) + m) * 2 + par) * P2 + min(k, P2 - 1);
-                cp_async8(dst + q * BRS, src, okb ? 8 : 0);
-            }
-            asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(&brawFull[r]))
-                         : "memory");
         }
-        asm volatile("cp.async.wait_all;" ::: "memory");
     } else if (warp == 5) {
         // ---------------------------------------------------------- MMAs
         if (lane == 0) {
             for (int ch = 0; ch < nchunks; ++ch) {
-                const int s = ch % NSH, t = ch % NB, a = ch % NACC;
+                const int s = ch % NSH, a = ch % NACC;
                 if (!ws_wait(smem_u32(&fullA[s]), (uint32_t)((ch / NSH) & 1), abort)) break;
                 seenA = ch + 1;
-                if (!ws_wait(smem_u32(&fullB[t]), (uint32_t)((ch / NB) & 1), abort)) break;
                 if (ch >= NACC && !ws_wait(smem_u32(&accEmpty[a]), (uint32_t)((ch / NACC + 1) & 1), abort)) break;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t aH = smem_u32(sA + s * TILE_A), aL = aH + (uint32_t)rp * 64;
-                const uint32_t bH = smem_u32(sB + t * (2 * TILE_H)), bL = bH + TILE_H;
+                const uint32_t bH = smem_u32(sB + s * TILE_BP), bL = bH + TILE_H;
                 const uint32_t d = dtmem + (uint32_t)(a * TN);
 #pragma unroll
                 for (int ks = 0; ks < KC / 16; ++ks) {
@@ -587,29 +561,23 @@ __global__ void __launch_bounds__(NTW, 2) fused_tc_ws_kernel(
                     mma_f16(d, make_desc(aH + o, 128, 512), make_desc(bH + o, 128, 512), 1u);
                 }
                 mma_commit(smem_u32(&emptyA[s]));
-                mma_commit(smem_u32(&emptyB[t]));
                 mma_commit(smem_u32(&accFull[a]));
                 committed = ch + 1;
             }
         }
     } else {
         // ---------------------------------------------------------- workers
-        // b: thread -> map (tid & 31) and the 8 consecutive k = 8 (tid >> 5) ..;
-        // real parts to B row (tid & 31), imaginary parts to row 32 + (tid & 31):
-        // one 16-byte core-matrix row each
-        const int bm = tid & 31, kg = tid >> 5;
-        const int bmap = b0 + bm;
-        const float tb = bmap < B ? pow2_scale(bscale[(int64_t)bmap * (L + 1) + m], 13) : 1.f;
-        const uint32_t offr = (uint32_t)((bm >> 3) * 512 + kg * 128 + (bm & 7) * 16);
-        const uint32_t offi = offr + 4 * 512;
         float acc[64];
 #pragma unroll
         for (int q = 0; q < 64; ++q) acc[q] = 0.f;
         const uint32_t trow = dtmem + ((uint32_t)(32 * warp) << 16);
         bool ok = true;
-        auto drain = [&](int dch) {
-            const int a = dch % NACC;
-            if (!ws_wait(smem_u32(&accFull[a]), (uint32_t)((dch / NACC) & 1), abort)) return false;
+        for (int ch = 0; ch < nchunks && ok; ++ch) {
+            const int a = ch % NACC;
+            if (!ws_wait(smem_u32(&accFull[a]), (uint32_t)((ch / NACC) & 1), abort)) {
+                ok = false;
+                break;
+            }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
             for (int h = 0; h < 4; ++h) {
@@ -620,43 +588,7 @@ __global__ void __launch_bounds__(NTW, 2) fused_tc_ws_kernel(
             }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             mbar_arrive(smem_u32(&accEmpty[a]));
-            return true;
-        };
-        auto work = [&](int ch) {
-            const int t = ch % NB, r = ch % NBR;
-            // this thread's 8 complex b values of the chunk from the raw stage
-            if (!ws_wait(smem_u32(&brawFull[r]), (uint32_t)((ch / NBR) & 1), abort)) return false;
-            float2 rb[8];
-            const float4* raw = reinterpret_cast<const float4*>(sR + r * TILE_R + bm * BRS + kg * 64);
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const float4 v = raw[e];
-                rb[2 * e] = make_float2(v.x, v.y);
-                rb[2 * e + 1] = make_float2(v.z, v.w);
-            }
-            mbar_arrive(smem_u32(&brawEmpty[r]));
-            if (ch >= NB && !ws_wait(smem_u32(&emptyB[t]), (uint32_t)((ch / NB + 1) & 1), abort)) return false;
-            unsigned char* Bhi = sB + t * (2 * TILE_H);
-            uint32_t rh[4], rl[4], qh[4], ql[4];
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const HalfPair x0 = split_h(tb * rb[2 * e].x), x1 = split_h(tb * rb[2 * e + 1].x);
-                const HalfPair y0 = split_h(tb * rb[2 * e].y), y1 = split_h(tb * rb[2 * e + 1].y);
-                rh[e] = pack_h(x0.hi, x1.hi);
-                rl[e] = pack_h(x0.lo, x1.lo);
-                qh[e] = pack_h(y0.hi, y1.hi);
-                ql[e] = pack_h(y0.lo, y1.lo);
-            }
-            *reinterpret_cast<uint4*>(Bhi + offr) = make_uint4(rh[0], rh[1], rh[2], rh[3]);
-            *reinterpret_cast<uint4*>(Bhi + TILE_H + offr) = make_uint4(rl[0], rl[1], rl[2], rl[3]);
-            *reinterpret_cast<uint4*>(Bhi + offi) = make_uint4(qh[0], qh[1], qh[2], qh[3]);
-            *reinterpret_cast<uint4*>(Bhi + TILE_H + offi) = make_uint4(ql[0], ql[1], ql[2], ql[3]);
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            mbar_arrive(smem_u32(&fullB[t]));
-            return ch < LAG || drain(ch - LAG);
-        };
-        for (int ch = 0; ch < nchunks && ok; ++ch) ok = work(ch);
-        for (int dch = max(0, nchunks - LAG); ok && dch < nchunks; ++dch) ok = drain(dch);
+        }
         if (ok) {
             const int row = 32 * warp + lane;
             const int i = i0 + row;
@@ -687,7 +619,7 @@ __global__ void __launch_bounds__(NTW, 2) fused_tc_ws_kernel(
     if (abort_) {
         if (tid == 0) {
             atomicExch(status, HPX_ERR_TIMEOUT);
-            // operator copies issued but not seen by the MMA warp, and the last MMAs
+            // copies issued but not seen by the MMA warp, and the last MMAs
             for (int q = seenA; q < issuedA; ++q)
                 mbar_wait(smem_u32(&fullA[q % NSH]), (uint32_t)((q / NSH) & 1));
             if (committed > 0)
@@ -777,9 +709,13 @@ int prepare_fused_tc(hpx_plan_s* P) {
     const int64_t nch = (g.P2 + KC - 1) / KC;
     const int64_t rows = P->fused_bytes / 4 / (32 * nch);   // stored rows of all tiles
     const size_t rb = (size_t)rows * sizeof(float), bb = (size_t)g.B * (g.L + 1) * sizeof(float);
-    if (cudaMalloc(&P->tcRinv, rb) != cudaSuccess || cudaMalloc(&P->bscale, bb) != cudaSuccess) return -1;
-    P->bytes += (int64_t)(rb + bb);
-    P->fused_bytes += (int64_t)(rb + bb);
+    const size_t pb = bpk_bytes(g.B, g.L, g.P2);
+    if (cudaMalloc(&P->tcRinv, rb) != cudaSuccess || cudaMalloc(&P->bscale, bb) != cudaSuccess ||
+        cudaMalloc(&P->bpk, pb) != cudaSuccess)
+        return -1;
+    cudaMemset(P->bpk, 0, pb);   // columns of maps past the batch stay zero
+    P->bytes += (int64_t)(rb + bb + pb);
+    P->fused_bytes += (int64_t)(rb + bb + pb);
     tc_to_f16_kernel<<<P->fused_ntiles, TM>>>((float*)P->fusedM, P->tcOff, P->fusedTiles, g.P2, g.L, P->tcRinv, 0);
     return cudaDeviceSynchronize() == cudaSuccess ? 0 : -1;
 #else
@@ -792,11 +728,11 @@ void launch_fused_tc(const hpx_plan_s* P, float* alm, cudaStream_t s) {
     const auto& g = P->g;
     dim3 grid(P->fused_ntiles, (g.B + 31) / 32);
 #if HPX_TC_F16
-    const size_t smem_h = NSH * TILE_A + NB * 2 * TILE_H + NBR * TILE_R;
+    const size_t smem_h = NSH * (TILE_A + TILE_BP);
     cudaFuncSetAttribute(fused_tc_ws_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_h);
-    fused_tc_ws_kernel<false><<<grid, NTW, smem_h, s>>>((const unsigned char*)P->fusedM, P->tcOff, P->tcRinv, P->fusedTiles,
-                                                 (const cplx<float>*)P->bvec, P->bscale, (cplx<float>*)alm, g.P2,
-                                                 g.p, g.L, g.B, g.nalm, P->d_status);
+    fused_tc_ws_kernel<false><<<grid, NTW, smem_h, s>>>((const unsigned char*)P->fusedM, P->tcOff, P->tcRinv,
+                                                        P->fusedTiles, (const unsigned char*)P->bpk, P->bscale,
+                                                        (cplx<float>*)alm, g.P2, g.p, g.L, g.B, g.nalm, P->d_status);
 #else
     const size_t smem_t = NSA * TILE_A + 4 * TILE_B;
     cudaFuncSetAttribute(fused_tc_tmem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_t);
@@ -863,7 +799,9 @@ int prepare_dense_tc(hpx_plan_s* P) {
               cudaMalloc(&duo, uoff.size() * sizeof(int64_t)) == cudaSuccess &&
               cudaMalloc(&dt, tiles.size() * sizeof(int)) == cudaSuccess &&
               cudaMalloc(&dto, off.size() * sizeof(int64_t)) == cudaSuccess &&
-              (P->bscale || cudaMalloc(&P->bscale, bb) == cudaSuccess);
+              (P->bscale || cudaMalloc(&P->bscale, bb) == cudaSuccess) &&
+              (P->bpk || (cudaMalloc(&P->bpk, bpk_bytes(g.B, g.L, g.P2)) == cudaSuccess &&
+                          cudaMemset(P->bpk, 0, bpk_bytes(g.B, g.L, g.P2)) == cudaSuccess));
     if (ok) {
         cudaMemcpy(du, utiles.data(), utiles.size() * sizeof(int), cudaMemcpyHostToDevice);
         cudaMemcpy(duo, uoff.data(), uoff.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
@@ -879,7 +817,8 @@ int prepare_dense_tc(hpx_plan_s* P) {
     P->dTiles = dt;
     P->dTcOff = dto;
     P->dNtiles = (int)off.size();
-    P->bytes += (int64_t)o * 4 + rows * 4 + (int64_t)bb + (int64_t)(tiles.size() * sizeof(int) + off.size() * 8);
+    P->bytes += (int64_t)o * 4 + rows * 4 + (int64_t)bb + (int64_t)bpk_bytes(g.B, g.L, g.P2) +
+                (int64_t)(tiles.size() * sizeof(int) + off.size() * 8);
     return ok ? 0 : -1;
 #else
     (void)P;
@@ -891,10 +830,10 @@ void launch_dense_tc(const hpx_plan_s* P, cudaStream_t s) {
 #if HPX_TC_F16
     const auto& g = P->g;
     dim3 grid(P->dNtiles, (g.B + 31) / 32);
-    const size_t smem_h = NSH * TILE_A + NB * 2 * TILE_H + NBR * TILE_R;
+    const size_t smem_h = NSH * (TILE_A + TILE_BP);
     cudaFuncSetAttribute(fused_tc_ws_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_h);
     fused_tc_ws_kernel<true><<<grid, NTW, smem_h, s>>>((const unsigned char*)P->dTC, P->dTcOff, (const float*)P->dRinv,
-                                                       P->dTiles, (const cplx<float>*)P->bvec, P->bscale,
+                                                       P->dTiles, (const unsigned char*)P->bpk, P->bscale,
                                                        (cplx<float>*)P->beta, g.P2, g.p, g.L, g.B, g.nalm,
                                                        P->d_status);
 #else

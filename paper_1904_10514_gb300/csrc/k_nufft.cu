@@ -20,6 +20,7 @@
 // nufft_kernel does the whole step per column (used by the allocation-free
 // entry point); plans run it as spread_kernel + lat_fft_kernel below.
 #include "fft_ct.cuh"
+#include "fp16pair.cuh"
 #include "plan.h"
 
 namespace hpx {
@@ -381,15 +382,19 @@ __device__ __forceinline__ cplx<float> prewhiten_inverse(int j) {
 template <class T, int LOGM, int NT>
 __global__ void __launch_bounds__(NT, ((1 << LOGM) / NT == 16 ? (LOGM <= 13 ? 1024 / NT : 1) : 512 / NT)) lat_fft_pair_ct_kernel(
     const cplx<T>* __restrict__ U, cplx<T>* __restrict__ bvec, const T* __restrict__ dec,
-    const cplx<T>* __restrict__ tw, int twlen, int p, int L, int P2, int ldu, float* __restrict__ bscale) {
+    const cplx<T>* __restrict__ tw, int twlen, int p, int L, int P2, int ldu, float* __restrict__ bscale,
+    unsigned char* __restrict__ bpk) {
     constexpr int M = 1 << LOGM;
     constexpr int H = M >> 1;
     extern __shared__ unsigned char smem_raw[];
     cplx<T>* u = reinterpret_cast<cplx<T>*>(smem_raw);   // M (padded)
     cplx<T>* zlo = u + M + M / 16;                         // Z_j, j = 0..p
     cplx<T>* zhi = zlo + (p + 1);                          // Z_{M-j}, j = 0..p
-    const int m0 = 2 * blockIdx.x, m1 = m0 + 1;
-    const int b = blockIdx.y;
+    // blocks of one pair of orders and consecutive maps run together (map
+    // index fastest), so the packed b of a pair's 32 maps, which share every
+    // 128-byte line of the B layout, is written while its lines are in L2
+    const int b = blockIdx.x;
+    const int m0 = 2 * blockIdx.y, m1 = m0 + 1;
     const int tid = threadIdx.x;
     const bool has1 = m1 <= L;
     const cplx<T>* s0 = U + ((int64_t)b * (L + 1) + m0) * ldu;
@@ -422,6 +427,48 @@ __global__ void __launch_bounds__(NT, ((1 << LOGM) / NT == 16 ? (LOGM <= 13 ? 10
         };
         ct::fft<T, LOGM, NT, false, false>(u, tw, twlen >> LOGM, ld, st);
     }
+    if constexpr (sizeof(T) == 4) {
+        if (bpk) {   // FP16 pairs for the tensor cores, scaled per column by its largest magnitude
+            __shared__ float2 red32[32];
+            // B_m(j) and i/2 B_{m+1}(j) (the values of the bvec form below) by
+            // (column, parity of j, k = j >> 1) into the FFT buffer, which is free
+            // now; one spare slot every 8 k, so that the packing below, where
+            // lane g reads k = 8 g + e, spreads over the banks
+            cplx<float>* vb = u;
+            const int LD = P2 + (P2 >> 3) + 1;
+            auto vidx = [&](int col, int par, int k) { return (col * 2 + par) * LD + k + (k >> 3); };
+            float mx0 = 0.f, mx1 = 0.f;
+            for (int j = tid; j <= p; j += NT) {
+                const cplx<float> a = zlo[j], c = (j == 0) ? zlo[0] : zhi[j];
+                const float dj = dec[j];
+                const cplx<float> v0 = scale(add(a, c), 0.5f * dj);
+                vb[vidx(0, j & 1, j >> 1)] = v0;
+                mx0 = fmaxf(mx0, fmaxf(fabsf(v0.r), fabsf(v0.i)));
+                if (has1) {
+                    const cplx<float> v = scale(sub(a, c), 0.5f * dj);
+                    const cplx<float> v1 = mk<float>(-0.5f * v.i, 0.5f * v.r);
+                    vb[vidx(1, j & 1, j >> 1)] = v1;
+                    mx1 = fmaxf(mx1, fmaxf(fabsf(v1.r), fabsf(v1.i)));
+                }
+            }
+            const float2 mx = block_max2(make_float2(mx0, mx1), red32);   // (its barrier also publishes vb)
+            mx0 = mx.x;
+            mx1 = mx.y;
+            if (tid == 0) {
+                bscale[(int64_t)b * (L + 1) + m0] = mx0;
+                if (has1) bscale[(int64_t)b * (L + 1) + m1] = mx1;
+            }
+            auto val = [&](int col, int par, int k) {   // zero past the column
+                return (k < P2 && 2 * k + par <= p) ? vb[vidx(col, par, k)] : mk<float>(0.f, 0.f);
+            };
+            pack_column(bpk, b, m0, L, P2, pow2_scale(mx0, 13), [&](int par, int k) { return val(0, par, k); },
+                        tid, NT);
+            if (has1)
+                pack_column(bpk, b, m1, L, P2, pow2_scale(mx1, 13), [&](int par, int k) { return val(1, par, k); },
+                            tid, NT);
+            return;
+        }
+    }
     cplx<T>* out0 = bvec + ((int64_t)b * (p + 1) + m0) * 2 * P2;
     cplx<T>* out1 = out0 + 2 * P2;
     float mx0 = 0.f, mx1 = 0.f;   // largest magnitudes stored (for bscale)
@@ -453,23 +500,44 @@ __global__ void __launch_bounds__(NT, ((1 << LOGM) / NT == 16 ? (LOGM <= 13 ? 10
     }
 }
 
+// The packed form of b (fp16pair.cuh) from bvec, one block per (order, map):
+// for the grid-FFT kernels that write bvec only.
+__global__ void __launch_bounds__(256) pack_b_kernel(const cplx<float>* __restrict__ bvec,
+                                                     unsigned char* __restrict__ bpk, float* __restrict__ bscale,
+                                                     int p, int L, int P2) {
+    __shared__ float red32[32];
+    const int b = blockIdx.x, m = blockIdx.y;   // maps fastest, like the grid-FFT kernel
+    const cplx<float>* col = bvec + ((int64_t)b * (p + 1) + m) * 2 * P2;
+    auto val = [&](int par, int k) { return k < P2 ? col[par * P2 + k] : mk<float>(0.f, 0.f); };
+    float mx = 0.f;
+    for (int e = threadIdx.x; e < 2 * P2; e += blockDim.x) {
+        const cplx<float> v = col[e];
+        mx = fmaxf(mx, fmaxf(fabsf(v.r), fabsf(v.i)));
+    }
+    mx = block_max(mx, red32);
+    if (threadIdx.x == 0) bscale[(int64_t)b * (L + 1) + m] = mx;
+    pack_column(bpk, b, m, L, P2, pow2_scale(mx, 13), val, threadIdx.x, blockDim.x);
+}
+
+bool packs_b(const hpx_plan_s* P) {
+    return P->bpk && P->precision == HPX_FP32 && ((P->fusedM && P->use_tc) || (!P->fusedM && P->dTC));
+}
+
 template <class T>
-void launch_lat_fft(const hpx_plan_s* P, cudaStream_t s) {
+void launch_lat_fft(const hpx_plan_s* P, cudaStream_t s, bool packed) {
     const auto& g = P->g;
-    // bscale (FP16 operator form): per column the largest magnitude of b, as
-    // the atomic maximum of the float bits over the warps that write it
-    if (P->bscale) cudaMemsetAsync(P->bscale, 0, (size_t)g.B * (g.L + 1) * sizeof(float), s);
+    packed = packed && sizeof(T) == 4 && P->bpk && P->bscale;
     int logM = 0;
     while ((1 << logM) < g.M) ++logM;
     const size_t smem = (size_t)(g.M + g.M / 16) * sizeof(cplx<T>);
     if (logM >= 12 && logM <= 14) {   // two orders per block, compile-time grid length
         const size_t smem2 = (size_t)(g.M + g.M / 16 + 2 * (g.p + 1)) * sizeof(cplx<T>);
-        dim3 grid2((g.L + 2) / 2, g.B);
+        dim3 grid2(g.B, (g.L + 2) / 2);
         auto run = [&](auto kern, int threads) {
             cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
             kern<<<grid2, threads, smem2, s>>>((const cplx<T>*)P->U, (cplx<T>*)P->bvec, (const T*)P->t.dec,
                                                (const cplx<T>*)P->t.twid, g.Lmax, g.p, g.L, g.P2, P->ldu,
-                                               P->bscale);
+                                               packed ? P->bscale : nullptr, packed ? P->bpk : nullptr);
         };
         const bool e32 = P->latE == 32;   // elements per thread (the plan's tuning), else 16
         if (logM == 12) { if (e32) run(lat_fft_pair_ct_kernel<T, 12, 128>, 128); else run(lat_fft_pair_ct_kernel<T, 12, 256>, 256); }
@@ -484,20 +552,24 @@ void launch_lat_fft(const hpx_plan_s* P, cudaStream_t s) {
         dim3 grid2((g.L + 2) / 2, g.B);
         kern2<<<grid2, 512, smem2, s>>>((const cplx<T>*)P->U, (cplx<T>*)P->bvec, (const T*)P->t.dec,
                                         (const cplx<T>*)P->t.twid, g.Lmax, g.M, logM, g.p, g.L, g.P2, P->ldu,
-                                        P->bscale);
-        return;
+                                        nullptr);
+    } else {
+        auto kern = g.M > 16 * 512 ? lat_fft_kernel<T, 32> : lat_fft_kernel<T, 16>;
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        dim3 grid(g.L + 1, g.B);
+        kern<<<grid, 512, smem, s>>>((const cplx<T>*)P->U, (cplx<T>*)P->bvec, (const T*)P->t.dec,
+                                     (const cplx<T>*)P->t.twid, g.Lmax, g.M, logM, g.p, g.L, g.P2, P->ldu, nullptr);
     }
-    auto kern = g.M > 16 * 512 ? lat_fft_kernel<T, 32> : lat_fft_kernel<T, 16>;
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    dim3 grid(g.L + 1, g.B);
-    kern<<<grid, 512, smem, s>>>((const cplx<T>*)P->U, (cplx<T>*)P->bvec, (const T*)P->t.dec,
-                                 (const cplx<T>*)P->t.twid, g.Lmax, g.M, logM, g.p, g.L, g.P2, P->ldu, P->bscale);
+    if (packed) {
+        dim3 gp(g.B, g.L + 1);
+        pack_b_kernel<<<gp, 256, 0, s>>>((const cplx<float>*)P->bvec, P->bpk, P->bscale, g.p, g.L, g.P2);
+    }
 }
 
 template void launch_spread<float>(const hpx_plan_s*, cudaStream_t);
 template void launch_spread<double>(const hpx_plan_s*, cudaStream_t);
-template void launch_lat_fft<float>(const hpx_plan_s*, cudaStream_t);
-template void launch_lat_fft<double>(const hpx_plan_s*, cudaStream_t);
+template void launch_lat_fft<float>(const hpx_plan_s*, cudaStream_t, bool);
+template void launch_lat_fft<double>(const hpx_plan_s*, cudaStream_t, bool);
 
 template <class T>
 void launch_nufft(const hpx_plan_s* P, cudaStream_t s) {

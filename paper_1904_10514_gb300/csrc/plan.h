@@ -99,6 +99,7 @@ struct hpx_plan_s {
     int* tcFirst = nullptr;        // first tile of (m, c)
     float* tcRinv = nullptr;       // FP16 form: 1 / row scale, per stored row of the tiles
     float* bscale = nullptr;       // FP16 form: [B][L+1] largest magnitude of each b column
+    unsigned char* bpk = nullptr;  // FP16 form: b as scaled FP16 pairs in the MMA layout (fp16pair.cuh)
     int* d_status = nullptr;       // device status word (timed-out waits, non-finite inputs)
     int64_t fused_bytes = 0;       // bytes of M
     void* synM = nullptr;          // T, n_alm x ldm row-major: synthesis operators R_{m,c} Es (HPX_FLAG_SYNTHESIS)
@@ -185,7 +186,11 @@ template <class T> void launch_ring_fft(const hpx_plan_s* P, const T* maps, cuda
 template <class T> void launch_poles(const hpx_plan_s* P, const T* maps, cudaStream_t s);
 template <class T> void launch_nufft(const hpx_plan_s* P, cudaStream_t s);
 template <class T> void launch_spread(const hpx_plan_s* P, cudaStream_t s);
-template <class T> void launch_lat_fft(const hpx_plan_s* P, cudaStream_t s);
+// packed: also (FP32 tensor-core plans) write b as the FP16 pairs of bpk, with
+// each column's largest magnitude in bscale, instead of bvec
+template <class T> void launch_lat_fft(const hpx_plan_s* P, cudaStream_t s, bool packed = false);
+// whether the analysis' contraction reads the packed b (bpk) of this plan
+bool packs_b(const hpx_plan_s* P);
 
 template <class T> void launch_dense(const hpx_plan_s* P, cudaStream_t s, const void* Dmat = nullptr);
 template <class T> void launch_cg(const hpx_plan_s* P, cudaStream_t s);
