@@ -31,9 +31,15 @@ METRIC = "HEALPix analysis Gpix/s at Nside=1024 (batched FP32 vs plain FP64, err
 NSIDE, LMAX, BATCH = 1024, 2048, 32
 WORKLOAD = "bench_nside1024x32"
 MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
-# measured DRAM traffic / algorithmic bytes of a kernel (ncu capture, Nside 512, 32 maps:
-# fused_tc_ws_kernel with the packed FP16-pair right-hand sides, 1.4479 GB read + 0.1249 GB written)
-TRAFFIC_OVER_ALGORITHMIC = {"fused_fsht": (1.4479 + 0.1249) / 1.4828}
+# measured DRAM traffic (read + written, GB) / algorithmic bytes of each stage at Nside 512, 32 maps
+# (ncu --set full captures of the stage's launches; the summaries are in profiles/).  Dirty lines
+# still in L2 when a kernel ends are not counted, so a ratio can fall below 1.
+TRAFFIC_OVER_ALGORITHMIC = {
+    "fused_fsht": (1.4479 + 0.1249) / 1.4828,                      # fused_tc_ws_kernel, packed b
+    "ring_fft": (0.11342 + 0.08983 + 0.31140 + 0.34239) / 0.94031,  # ring_ct_kernel + ring_fft_kernel
+    "lat_fft": (0.53804 + 0.24894) / 0.80688,                      # lat_fft_pair_ct_kernel, packed b
+    "spread": (0.54846 + 0.49414) / 1.07532,                       # spread_rb_kernel
+}
 # FP32 SIMT peak: 152 SMs x 128 FP32 lanes x 2 flop/FMA x 2.070 GHz (maximum SM clock)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 
@@ -163,7 +169,7 @@ def roofline_report(work, per_launch, peaks):
     else:
         roof = stage_roofline(kind, amount, per_launch[dom], peaks)
         roof["traffic"] = amount * ratio if (ratio and kind == "hbm") else None
-    roof["traffic_source"] = ("ncu at Nside 512, 32 maps: %.4f x the operator stream bytes, scaled" % ratio
+    roof["traffic_source"] = ("ncu at Nside 512, 32 maps: %.4f x the stage's algorithmic bytes, scaled" % ratio
                               if roof.get("traffic") else None)
     roof["kernel"] = dom
     roof["per_launch_ms"] = per_launch[dom]
@@ -172,6 +178,8 @@ def roofline_report(work, per_launch, peaks):
         r = stage_roofline(work[n][0], work[n][1], per_launch[n], peaks)
         per_stage[n] = {"bound": r["bound"], "ms": per_launch[n], "achieved": r["achieved"], "unit": r["unit"],
                         "frac": r["frac"]}
+        if n in TRAFFIC_OVER_ALGORITHMIC and work[n][0] == "hbm":
+            per_stage[n]["traffic"] = work[n][1] * TRAFFIC_OVER_ALGORITHMIC[n]
     return roof, per_stage
 
 

@@ -32,7 +32,8 @@ def test_dominant_stage_and_rates():
     amount = work["ring_fft"][1]
     assert roof["achieved"] == pytest.approx(amount / 2.51e-3 / 1e9)
     assert roof["frac"] == pytest.approx(roof["achieved"] / 6790.3)
-    assert roof["traffic"] is None            # no capture of the ring stage
+    # traffic: the ring stage's DRAM bytes per algorithmic byte (ncu at Nside 512), scaled
+    assert roof["traffic"] == pytest.approx(amount * bench.TRAFFIC_OVER_ALGORITHMIC["ring_fft"])
     assert "unused" not in stages and set(stages) == {"ring_fft", "poles", "spread", "lat_fft", "fused_fsht"}
     op = stages["fused_fsht"]
     assert op["frac"] == pytest.approx(work["fused_fsht"][1] / 2.43e-3 / 1e9 / 6790.3)
