@@ -73,7 +73,8 @@ void free_plan(hpx_plan_s* P) {
                     t.bhOff, t.shift, t.chirp, t.bhat, t.twid, t.poleN, t.poleS, t.polew, t.rowptr,
                     t.ent, t.entw, t.dec, t.D, t.tstart, t.hwn, t.angOff, t.ang, t.skOff, t.skew, t.skewT, t.nrowptr, t.nent, t.nentw, t.nstart, t.swts, t.hstart, t.hwts, t.Es, t.shifted, t.C, t.cgH, P->Y, P->U, P->bvec,
                     P->fusedM, P->fusedOff, P->fusedTiles, P->tcOff, P->tcFirst, P->tcRinv, P->bscale, P->d_status, P->synM, P->ringList,
-                    P->jres, P->jalm, P->dTC, P->dRinv, P->dTiles, P->dTcOff, P->mapIdx, P->bpk};
+                    P->jres, P->jalm, P->dTC, P->dRinv, P->dTiles, P->dTcOff, P->mapIdx, P->bpk, P->synT,
+                    P->synRinv, P->synTiles, P->synNch, P->synOff, P->synRowBase, P->synScale, P->synBpk};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     if (P->ev) {
@@ -368,6 +369,8 @@ hpx_plan_s* hpx_plan_ex(const hpx_plan_desc* d) {
                                    : hpx::build_fused<float>(P, Es64, sk64, nullptr, P->synM, false))
                            : -1;
                 if (!fp64 && Es64) { cudaFree(Es64); P->bytes -= (int64_t)(EsHost.size() * 8); }
+                // FP32 plans on the tensor cores apply them there too
+                if (rc == 0 && P->use_tc) rc = hpx::prepare_synth_tc(P);
             } else {
                 cudaGetLastError();
             }

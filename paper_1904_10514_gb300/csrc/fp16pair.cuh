@@ -42,40 +42,60 @@ inline size_t bpk_bytes(int B, int L, int P2) {
     return (size_t)((B + 31) / 32) * (size_t)(L + 1) * 2 * (size_t)((P2 + 31) / 32) * kBpkChunk;
 }
 
-// Writes the packed blocks of column (map b, order m) by the nt threads tid:
-// val(par, k) is the complex b value (zero past the column), scaled by sc
-// before the split.  Each step takes 8 consecutive k of one parity: four 16-byte
-// stores (hi and lo of the real and of the imaginary parts).
+// One step of the packing: 8 consecutive k = 8 g8 .. 8 g8 + 7 of one half
+// (parity or chain) of a column, val(k) the complex value (zero past the half's
+// length), scaled by sc before the split; four 16-byte stores (hi and lo of the
+// real and of the imaginary parts) into the half's blocks at `half`, column
+// offset offr.
+template <class V>
+__device__ __forceinline__ void pack_group(unsigned char* __restrict__ half, int offr, int g8, float sc, V val) {
+    uint32_t hr[4], lr[4], hm[4], lm[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const int k = 8 * g8 + 2 * e;
+        const cplx<float> v0 = val(k), v1 = val(k + 1);
+        // the pairs of two consecutive k at once (the same roundings as split_h)
+        const float2 xr = make_float2(sc * v0.r, sc * v1.r), xi = make_float2(sc * v0.i, sc * v1.i);
+        const __half2 hR = __float22half2_rn(xr), hI = __float22half2_rn(xi);
+        const float2 fR = __half22float2(hR), fI = __half22float2(hI);
+        const __half2 lR = __float22half2_rn(make_float2(xr.x - fR.x, xr.y - fR.y));
+        const __half2 lI = __float22half2_rn(make_float2(xi.x - fI.x, xi.y - fI.y));
+        hr[e] = *reinterpret_cast<const uint32_t*>(&hR);
+        lr[e] = *reinterpret_cast<const uint32_t*>(&lR);
+        hm[e] = *reinterpret_cast<const uint32_t*>(&hI);
+        lm[e] = *reinterpret_cast<const uint32_t*>(&lI);
+    }
+    unsigned char* blk = half + (int64_t)(g8 >> 2) * kBpkChunk + (g8 & 3) * 128 + offr;
+    *reinterpret_cast<uint4*>(blk) = make_uint4(hr[0], hr[1], hr[2], hr[3]);
+    *reinterpret_cast<uint4*>(blk + 4096) = make_uint4(lr[0], lr[1], lr[2], lr[3]);
+    *reinterpret_cast<uint4*>(blk + 2048) = make_uint4(hm[0], hm[1], hm[2], hm[3]);
+    *reinterpret_cast<uint4*>(blk + 4096 + 2048) = make_uint4(lm[0], lm[1], lm[2], lm[3]);
+}
+
+// First byte of half h (0 or 1) of column (map b, order m); nch K-chunks per half.
+__device__ __forceinline__ unsigned char* packed_half(unsigned char* bpk, int b, int m, int h, int L, int nch) {
+    return bpk + ((((int64_t)(b >> 5) * (L + 1) + m) * 2 + h) * nch) * kBpkChunk;
+}
+__device__ __forceinline__ int packed_col_offset(int b) { return ((b & 31) >> 3) * 512 + (b & 7) * 16; }
+
+// Half h of column (map b, order m) by the nt threads tid, with its own scale.
+template <class V>
+__device__ __forceinline__ void pack_half(unsigned char* __restrict__ bpk, int b, int m, int h, int L, int nch,
+                                          float sc, V val, int tid, int nt) {
+    unsigned char* half = packed_half(bpk, b, m, h, L, nch);
+    const int offr = packed_col_offset(b);
+    for (int g8 = tid; g8 < nch * 4; g8 += nt) pack_group(half, offr, g8, sc, val);
+}
+
+// Both parities of column (map b, order m) with one scale: val(par, k).
 template <class V>
 __device__ __forceinline__ void pack_column(unsigned char* __restrict__ bpk, int b, int m, int L, int P2, float sc,
                                             V val, int tid, int nt) {
     const int nch = (P2 + 31) >> 5;
-    const int n = b & 31;
-    unsigned char* col = bpk + (((int64_t)(b >> 5) * (L + 1) + m) * 2) * nch * kBpkChunk;
-    const int offr = (n >> 3) * 512 + (n & 7) * 16;
-    for (int gi = tid; gi < 2 * nch * 4; gi += nt) {
-        const int par = gi / (nch * 4), g8 = gi - par * (nch * 4);
-        uint32_t hr[4], lr[4], hm[4], lm[4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const int k = 8 * g8 + 2 * e;
-            const cplx<float> v0 = val(par, k), v1 = val(par, k + 1);
-            // the pairs of two consecutive k at once (the same roundings as split_h)
-            const float2 xr = make_float2(sc * v0.r, sc * v1.r), xi = make_float2(sc * v0.i, sc * v1.i);
-            const __half2 hR = __float22half2_rn(xr), hI = __float22half2_rn(xi);
-            const float2 fR = __half22float2(hR), fI = __half22float2(hI);
-            const __half2 lR = __float22half2_rn(make_float2(xr.x - fR.x, xr.y - fR.y));
-            const __half2 lI = __float22half2_rn(make_float2(xi.x - fI.x, xi.y - fI.y));
-            hr[e] = *reinterpret_cast<const uint32_t*>(&hR);
-            lr[e] = *reinterpret_cast<const uint32_t*>(&lR);
-            hm[e] = *reinterpret_cast<const uint32_t*>(&hI);
-            lm[e] = *reinterpret_cast<const uint32_t*>(&lI);
-        }
-        unsigned char* blk = col + ((int64_t)par * nch + (g8 >> 2)) * kBpkChunk + (g8 & 3) * 128 + offr;
-        *reinterpret_cast<uint4*>(blk) = make_uint4(hr[0], hr[1], hr[2], hr[3]);
-        *reinterpret_cast<uint4*>(blk + 4096) = make_uint4(lr[0], lr[1], lr[2], lr[3]);
-        *reinterpret_cast<uint4*>(blk + 2048) = make_uint4(hm[0], hm[1], hm[2], hm[3]);
-        *reinterpret_cast<uint4*>(blk + 4096 + 2048) = make_uint4(lm[0], lm[1], lm[2], lm[3]);
+    const int offr = packed_col_offset(b);
+    for (int gi = tid; gi < 8 * nch; gi += nt) {
+        const int par = gi / (4 * nch), g8 = gi - par * (4 * nch);
+        pack_group(packed_half(bpk, b, m, par, L, nch), offr, g8, sc, [&](int k) { return val(par, k); });
     }
 }
 

@@ -655,7 +655,9 @@ void launch_sh_synthesis(const hpx_plan_s* P, const T* alm, T* maps, cudaStream_
     const auto& g = P->g;
     const auto& t = P->t;
     if (ev) cudaEventRecord(ev[0], s);
-    if (P->synM) {
+    if (sizeof(T) == 4 && P->synT) {
+        launch_synth_tc(P, (const float*)alm, s);   // the same operators on the tensor cores
+    } else if (P->synM) {
         launch_synth_apply<T>(P, alm, s);   // the sweeps and Es composed per (m, c)
     } else {
         const int ngroups = (2 * g.B + 31) / 32;

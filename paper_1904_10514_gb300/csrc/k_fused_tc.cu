@@ -460,19 +460,26 @@ __device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
 }
 
-// DENSE = false: the per-order operators M_{m,c}, tile (m, c, i0), output into
-// alm.  DENSE = true: the latitude operator D of the sweeps path (Sec. 3.2.2 and
-// the first half of Sec. 3.3, shared by all orders of one parity), tile
-// (m, par, i0) = rows q = i0.. of D[m & 1][par] applied to the columns
-// b[map][m][par], output into beta[m][par][q][map] for the Givens sweeps; the
-// tiles of all orders of one parity point at the same operator data, which
-// stays resident in L2 (default copy policy; the per-order operators are
-// streamed once per call and copied evict-first).
-template <bool DENSE>
+// MODE 0: the per-order operators M_{m,c}, tile (m, c, i0), output into alm.
+// MODE 1: the latitude operator D of the sweeps path (Sec. 3.2.2 and the first
+// half of Sec. 3.3, shared by all orders of one parity), tile (m, par, i0) =
+// rows q = i0.. of D[m & 1][par] applied to the columns b[map][m][par], output
+// into beta[m][par][q][map] for the Givens sweeps; the tiles of all orders of
+// one parity point at the same operator data, which stays resident in L2
+// (default copy policy; the per-order operators are streamed once per call and
+// copied evict-first).
+// MODE 2: the synthesis' order-m conversion, the transposed contraction
+// X[map][m][par][k] = sum_i S_{m,c}[i][k] a_{m+c+2i}^m[map]: tile (m, c, k0) =
+// rows k = k0.. of S_{m,c}^T (P2 rows), K = the chain's degrees (its own
+// chunk count), B = the packed coefficients of chain c (scaled per (map, m, c)),
+// output into bvec[map][m][par][k]; 1 / row scale at rowBase[tile] + row.
+template <int MODE>
 __global__ void __launch_bounds__(NTW, 2) fused_tc_ws_kernel(
     const unsigned char* __restrict__ Mh, const int64_t* __restrict__ tcOff, const float* __restrict__ tcRinv,
     const int* __restrict__ tiles, const unsigned char* __restrict__ bpk, const float* __restrict__ bscale,
-    cplx<float>* __restrict__ alm, int P2, int p, int L, int B, int64_t nalm, int* __restrict__ status) {
+    cplx<float>* __restrict__ alm, int P2, int p, int L, int B, int64_t nalm, int* __restrict__ status,
+    const int64_t* __restrict__ rowBase) {
+    constexpr bool DENSE = MODE == 1, SYNTH = MODE == 2;
     extern __shared__ __align__(1024) unsigned char smem_w[];
     unsigned char* const sA = smem_w;                  // NSH x TILE_A: operator chunks (hi, lo)
     unsigned char* const sB = smem_w + NSH * TILE_A;   // NSH x TILE_BP: b chunks (hi, lo)
@@ -484,10 +491,11 @@ __global__ void __launch_bounds__(NTW, 2) fused_tc_ws_kernel(
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m = tiles[3 * blockIdx.x], c = tiles[3 * blockIdx.x + 1], i0 = tiles[3 * blockIdx.x + 2];
     const int par = DENSE ? c : ((m & 1) + c) & 1;
-    const int nrows = DENSE ? P2 : chain_len(m, c, L);
+    const int nrows = (DENSE || SYNTH) ? P2 : chain_len(m, c, L);
     const int rp = (min(TM, nrows - i0) + 7) & ~7;
     const int b0 = blockIdx.y * (TN / 2);
-    const int nchunks = (P2 + KC - 1) / KC;
+    const int nchB = (P2 + KC - 1) / KC;                                       // K-chunks of a packed half
+    const int nchunks = SYNTH ? (chain_len(m, c, L) + KC - 1) / KC : nchB;    // K-chunks of this tile
     const uint32_t chunkBytes = (uint32_t)rp * 128u;
     volatile int* abort = &abort_;
 
@@ -514,7 +522,8 @@ __global__ void __launch_bounds__(NTW, 2) fused_tc_ws_kernel(
     }
     if (tid < TN / 2) {
         const int bm = b0 + tid;
-        tinv[tid] = bm < B ? 1.f / pow2_scale(bscale[(int64_t)bm * (L + 1) + m], 13) : 0.f;
+        const int64_t col = SYNTH ? ((int64_t)bm * (L + 1) + m) * 2 + c : (int64_t)bm * (L + 1) + m;
+        tinv[tid] = bm < B ? 1.f / pow2_scale(bscale[col], 13) : 0.f;
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -525,7 +534,8 @@ __global__ void __launch_bounds__(NTW, 2) fused_tc_ws_kernel(
         // ---------------------------------------------------------- copies
         if (lane == 0) {
             const unsigned char* At = Mh + tcOff[blockIdx.x] * 4;
-            const unsigned char* Bt = bpk + (((int64_t)blockIdx.y * (L + 1) + m) * 2 + par) * nchunks * TILE_BP;
+            const unsigned char* Bt =
+                bpk + (((int64_t)blockIdx.y * (L + 1) + m) * 2 + (SYNTH ? c : par)) * nchB * TILE_BP;
             for (int ch = 0; ch < nchunks; ++ch) {
                 const int s = ch % NSH;
                 if (ch >= NSH && !ws_wait(smem_u32(&emptyA[s]), (uint32_t)((ch / NSH + 1) & 1), abort)) break;
@@ -593,8 +603,16 @@ __global__ void __launch_bounds__(NTW, 2) fused_tc_ws_kernel(
             const int row = 32 * warp + lane;
             const int i = i0 + row;
             if (i < nrows) {
-                const float ri = tcRinv[tcOff[blockIdx.x] / (32 * nchunks) + row];
-                if constexpr (DENSE) {   // beta[m][par][i][map]: the 32 maps side by side
+                const float ri = tcRinv[SYNTH ? rowBase[blockIdx.x] + row : tcOff[blockIdx.x] / (32 * nchunks) + row];
+                if constexpr (SYNTH) {   // bvec[map][m][par][k], k = i
+#pragma unroll
+                    for (int q = 0; q < 32; ++q)
+                        if (b0 + q < B) {
+                            const float sc = ri * tinv[q];
+                            alm[(((int64_t)(b0 + q) * (p + 1) + m) * 2 + par) * P2 + i] =
+                                mk<float>(acc[q] * sc, acc[32 + q] * sc);
+                        }
+                } else if constexpr (DENSE) {   // beta[m][par][i][map]: the 32 maps side by side
                     cplx<float>* out = alm + (((int64_t)m * 2 + par) * P2 + i) * B + b0;
 #pragma unroll
                     for (int q = 0; q < 32; ++q)
@@ -636,14 +654,18 @@ __global__ void __launch_bounds__(NTW, 2) fused_tc_ws_kernel(
 // tile, thread r = row r): the row's largest magnitude gives its scale s_r,
 // 1 / s_r goes to rinv, and every chunk (all of it read before any of it is
 // rewritten) becomes the hi block followed by the lo block of s_r M.
-// rowsAll > 0: every tile belongs to a matrix of rowsAll rows (D), else to the
-// chain (m, c) of the tile table.
+// rowsAll > 0: every tile belongs to a matrix of rowsAll rows (D, S^T), else to
+// the chain (m, c) of the tile table.  tileNch / rowBase (both or neither):
+// the tile's K-chunk count and the index of its first row scale, else
+// ceil(P2 / 32) chunks and rows stored consecutively.
 __global__ void __launch_bounds__(TM) tc_to_f16_kernel(float* __restrict__ Mt, const int64_t* __restrict__ tcOff,
                                                        const int* __restrict__ tiles, int P2, int L,
-                                                       float* __restrict__ rinv, int rowsAll) {
+                                                       float* __restrict__ rinv, int rowsAll,
+                                                       const int* __restrict__ tileNch,
+                                                       const int64_t* __restrict__ rowBase) {
     const int m = tiles[3 * blockIdx.x], c = tiles[3 * blockIdx.x + 1], i0 = tiles[3 * blockIdx.x + 2];
     const int rp = (min(TM, (rowsAll > 0 ? rowsAll : chain_len(m, c, L)) - i0) + 7) & ~7;
-    const int nchunks = (P2 + KC - 1) / KC;
+    const int nchunks = tileNch ? tileNch[blockIdx.x] : (P2 + KC - 1) / KC;
     float* At = Mt + tcOff[blockIdx.x];
     const int r = threadIdx.x;
     const bool mine = r < rp;
@@ -657,7 +679,7 @@ __global__ void __launch_bounds__(TM) tc_to_f16_kernel(float* __restrict__ Mt, c
             }
         }
     const float sr = pow2_scale(mx, 14);
-    if (mine) rinv[tcOff[blockIdx.x] / (32 * nchunks) + r] = 1.f / sr;
+    if (mine) rinv[rowBase ? rowBase[blockIdx.x] + r : tcOff[blockIdx.x] / (32 * nchunks) + r] = 1.f / sr;
     for (int ch = 0; ch < nchunks; ++ch) {
         float* base = At + (int64_t)ch * rp * 32;
         float v[32];
@@ -716,7 +738,8 @@ int prepare_fused_tc(hpx_plan_s* P) {
     cudaMemset(P->bpk, 0, pb);   // columns of maps past the batch stay zero
     P->bytes += (int64_t)(rb + bb + pb);
     P->fused_bytes += (int64_t)(rb + bb + pb);
-    tc_to_f16_kernel<<<P->fused_ntiles, TM>>>((float*)P->fusedM, P->tcOff, P->fusedTiles, g.P2, g.L, P->tcRinv, 0);
+    tc_to_f16_kernel<<<P->fused_ntiles, TM>>>((float*)P->fusedM, P->tcOff, P->fusedTiles, g.P2, g.L, P->tcRinv, 0,
+                                              nullptr, nullptr);
     return cudaDeviceSynchronize() == cudaSuccess ? 0 : -1;
 #else
     (void)P;
@@ -729,10 +752,11 @@ void launch_fused_tc(const hpx_plan_s* P, float* alm, cudaStream_t s) {
     dim3 grid(P->fused_ntiles, (g.B + 31) / 32);
 #if HPX_TC_F16
     const size_t smem_h = NSH * (TILE_A + TILE_BP);
-    cudaFuncSetAttribute(fused_tc_ws_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_h);
-    fused_tc_ws_kernel<false><<<grid, NTW, smem_h, s>>>((const unsigned char*)P->fusedM, P->tcOff, P->tcRinv,
-                                                        P->fusedTiles, (const unsigned char*)P->bpk, P->bscale,
-                                                        (cplx<float>*)alm, g.P2, g.p, g.L, g.B, g.nalm, P->d_status);
+    cudaFuncSetAttribute(fused_tc_ws_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_h);
+    fused_tc_ws_kernel<0><<<grid, NTW, smem_h, s>>>((const unsigned char*)P->fusedM, P->tcOff, P->tcRinv,
+                                                    P->fusedTiles, (const unsigned char*)P->bpk, P->bscale,
+                                                    (cplx<float>*)alm, g.P2, g.p, g.L, g.B, g.nalm, P->d_status,
+                                                    nullptr);
 #else
     const size_t smem_t = NSA * TILE_A + 4 * TILE_B;
     cudaFuncSetAttribute(fused_tc_tmem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_t);
@@ -809,7 +833,7 @@ int prepare_dense_tc(hpx_plan_s* P) {
         cudaMemcpy(dto, off.data(), off.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
         const int nu = (int)uoff.size();
         dense_tiles_kernel<<<nu, TM>>>((const float*)P->t.D, (float*)P->dTC, duo, du, g.P2);
-        tc_to_f16_kernel<<<nu, TM>>>((float*)P->dTC, duo, du, g.P2, g.L, (float*)P->dRinv, g.P2);
+        tc_to_f16_kernel<<<nu, TM>>>((float*)P->dTC, duo, du, g.P2, g.L, (float*)P->dRinv, g.P2, nullptr, nullptr);
         ok = cudaDeviceSynchronize() == cudaSuccess;
     }
     if (du) cudaFree(du);
@@ -831,13 +855,138 @@ void launch_dense_tc(const hpx_plan_s* P, cudaStream_t s) {
     const auto& g = P->g;
     dim3 grid(P->dNtiles, (g.B + 31) / 32);
     const size_t smem_h = NSH * (TILE_A + TILE_BP);
-    cudaFuncSetAttribute(fused_tc_ws_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_h);
-    fused_tc_ws_kernel<true><<<grid, NTW, smem_h, s>>>((const unsigned char*)P->dTC, P->dTcOff, (const float*)P->dRinv,
-                                                       P->dTiles, (const unsigned char*)P->bpk, P->bscale,
-                                                       (cplx<float>*)P->beta, g.P2, g.p, g.L, g.B, g.nalm,
-                                                       P->d_status);
+    cudaFuncSetAttribute(fused_tc_ws_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_h);
+    fused_tc_ws_kernel<1><<<grid, NTW, smem_h, s>>>((const unsigned char*)P->dTC, P->dTcOff, (const float*)P->dRinv,
+                                                    P->dTiles, (const unsigned char*)P->bpk, P->bscale,
+                                                    (cplx<float>*)P->beta, g.P2, g.p, g.L, g.B, g.nalm, P->d_status,
+                                                    nullptr);
 #else
     (void)P;
+    (void)s;
+#endif
+}
+
+// S_{m,c} (row-major: chain row i, latitude mode k; n_alm x ldm) -> tiles of
+// S^T: tile (m, c, k0) = rows k = k0.. (rp of them), K = the chain's rows in
+// chunks of 32, in the FP32 core-matrix layout of the operator tiles (k past
+// P2 and i past the chain zero).  One block of 128 threads per tile, thread =
+// row; consecutive threads read consecutive k of one row of S.
+__global__ void __launch_bounds__(TM) syn_tiles_kernel(const float* __restrict__ S, int ldm,
+                                                       const int64_t* __restrict__ moff, float* __restrict__ Mt,
+                                                       const int64_t* __restrict__ tcOff, const int* __restrict__ tiles,
+                                                       int P2, int L) {
+    const int m = tiles[3 * blockIdx.x], c = tiles[3 * blockIdx.x + 1], k0 = tiles[3 * blockIdx.x + 2];
+    const int rp = (min(TM, P2 - k0) + 7) & ~7;
+    const int nrows = chain_len(m, c, L);
+    const int nch = (nrows + KC - 1) / KC;
+    const int r = threadIdx.x;
+    if (r >= rp) return;
+    const int k = k0 + r;
+    const float* A = S + moff[(size_t)m * 2 + c] * ldm;
+    float* At = Mt + tcOff[blockIdx.x];
+    for (int ch = 0; ch < nch; ++ch)
+        for (int kk = 0; kk < KC; ++kk) {
+            const int i = ch * KC + kk;
+            const float v = (i < nrows && k < P2) ? A[(size_t)i * ldm + k] : 0.f;
+            At[(int64_t)ch * rp * 32 + (r >> 3) * 256 + (kk >> 2) * 32 + (r & 7) * 4 + (kk & 3)] = v;
+        }
+}
+
+// The synthesis' coefficients in the packed B layout: per (map b, order m) the
+// two chains c (degrees m + c + 2i), each scaled by its own largest magnitude
+// (recorded in scale[b][m][c]).  One block per (map, order), maps fastest.
+__global__ void __launch_bounds__(256) pack_alm_kernel(const cplx<float>* __restrict__ alm,
+                                                       unsigned char* __restrict__ bpk, float* __restrict__ scale,
+                                                       int L, int P2, int64_t nalm) {
+    __shared__ float2 red32[32];
+    const int b = blockIdx.x, m = blockIdx.y;
+    const int nch = (P2 + KC - 1) / KC;
+    const cplx<float>* a = alm + (int64_t)b * nalm + (int64_t)m * (2 * L + 1 - m) / 2 + m;   // a[l - m]
+    const int n0 = chain_len(m, 0, L), n1 = chain_len(m, 1, L);
+    float mx0 = 0.f, mx1 = 0.f;
+    for (int j = threadIdx.x; j <= L - m; j += blockDim.x) {
+        const cplx<float> v = a[j];
+        const float x = fmaxf(fabsf(v.r), fabsf(v.i));
+        if (j & 1) mx1 = fmaxf(mx1, x);
+        else mx0 = fmaxf(mx0, x);
+    }
+    const float2 mx = block_max2(make_float2(mx0, mx1), red32);
+    if (threadIdx.x < 2) scale[((int64_t)b * (L + 1) + m) * 2 + threadIdx.x] = threadIdx.x ? mx.y : mx.x;
+    pack_half(bpk, b, m, 0, L, nch, pow2_scale(mx.x, 13),
+              [&](int i) { return i < n0 ? a[2 * i] : mk<float>(0.f, 0.f); }, threadIdx.x, blockDim.x);
+    pack_half(bpk, b, m, 1, L, nch, pow2_scale(mx.y, 13),
+              [&](int i) { return i < n1 ? a[2 * i + 1] : mk<float>(0.f, 0.f); }, threadIdx.x, blockDim.x);
+}
+
+int prepare_synth_tc(hpx_plan_s* P) {
+#if HPX_TC_F16
+    const auto& g = P->g;
+    std::vector<int> tiles, nchs;
+    std::vector<int64_t> off, rbase;
+    int64_t o = 0, rows = 0;
+    for (int m = 0; m <= g.L; ++m)
+        for (int c = 0; c < 2; ++c) {
+            const int nch = (chain_len(m, c, g.L) + KC - 1) / KC;
+            for (int k0 = 0; k0 < g.P2; k0 += TM) {
+                const int rp = (std::min(TM, g.P2 - k0) + 7) & ~7;
+                tiles.insert(tiles.end(), {m, c, k0});
+                nchs.push_back(nch);
+                off.push_back(o);
+                rbase.push_back(rows);
+                o += (int64_t)nch * rp * 32;
+                rows += rp;
+            }
+        }
+    const size_t sb = (size_t)g.B * (g.L + 1) * 2 * sizeof(float), pb = bpk_bytes(g.B, g.L, g.P2);
+    int *dt = nullptr, *dn = nullptr;
+    int64_t *doff = nullptr, *drb = nullptr;
+    bool ok = cudaMalloc(&P->synT, (size_t)std::max<int64_t>(o, 1) * 4) == cudaSuccess &&
+              cudaMalloc(&P->synRinv, (size_t)rows * 4) == cudaSuccess &&
+              cudaMalloc(&dt, tiles.size() * sizeof(int)) == cudaSuccess &&
+              cudaMalloc(&dn, nchs.size() * sizeof(int)) == cudaSuccess &&
+              cudaMalloc(&doff, off.size() * sizeof(int64_t)) == cudaSuccess &&
+              cudaMalloc(&drb, rbase.size() * sizeof(int64_t)) == cudaSuccess &&
+              cudaMalloc(&P->synScale, sb) == cudaSuccess && cudaMalloc(&P->synBpk, pb) == cudaSuccess;
+    P->synTiles = dt;
+    P->synNch = dn;
+    P->synOff = doff;
+    P->synRowBase = drb;
+    if (!ok) return -1;
+    cudaMemcpy(dt, tiles.data(), tiles.size() * sizeof(int), cudaMemcpyHostToDevice);
+    cudaMemcpy(dn, nchs.data(), nchs.size() * sizeof(int), cudaMemcpyHostToDevice);
+    cudaMemcpy(doff, off.data(), off.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
+    cudaMemcpy(drb, rbase.data(), rbase.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
+    cudaMemset(P->synBpk, 0, pb);   // columns of maps past the batch stay zero
+    P->synNtiles = (int)off.size();
+    const int nt = P->synNtiles;
+    syn_tiles_kernel<<<nt, TM>>>((const float*)P->synM, P->fused_ldm, P->fusedOff, (float*)P->synT, doff, dt,
+                                 g.P2, g.L);
+    tc_to_f16_kernel<<<nt, TM>>>((float*)P->synT, doff, dt, g.P2, g.L, (float*)P->synRinv, g.P2, dn, drb);
+    P->bytes += o * 4 + rows * 4 + (int64_t)(sb + pb) + (int64_t)(tiles.size() + nchs.size()) * 4 +
+                (int64_t)(off.size() + rbase.size()) * 8;
+    return cudaDeviceSynchronize() == cudaSuccess ? 0 : -1;
+#else
+    (void)P;
+    return 0;
+#endif
+}
+
+void launch_synth_tc(const hpx_plan_s* P, const float* alm, cudaStream_t s) {
+#if HPX_TC_F16
+    const auto& g = P->g;
+    pack_alm_kernel<<<dim3(g.B, g.L + 1), 256, 0, s>>>((const cplx<float>*)alm, (unsigned char*)P->synBpk,
+                                                       (float*)P->synScale, g.L, g.P2, g.nalm);
+    dim3 grid(P->synNtiles, (g.B + 31) / 32);
+    const size_t smem_h = NSH * (TILE_A + TILE_BP);
+    cudaFuncSetAttribute(fused_tc_ws_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_h);
+    fused_tc_ws_kernel<2><<<grid, NTW, smem_h, s>>>((const unsigned char*)P->synT, P->synOff,
+                                                    (const float*)P->synRinv, P->synTiles,
+                                                    (const unsigned char*)P->synBpk, (const float*)P->synScale,
+                                                    (cplx<float>*)P->bvec, g.P2, g.p, g.L, g.B, g.nalm, P->d_status,
+                                                    P->synRowBase);
+#else
+    (void)P;
+    (void)alm;
     (void)s;
 #endif
 }

@@ -103,6 +103,20 @@ struct hpx_plan_s {
     int* d_status = nullptr;       // device status word (timed-out waits, non-finite inputs)
     int64_t fused_bytes = 0;       // bytes of M
     void* synM = nullptr;          // T, n_alm x ldm row-major: synthesis operators R_{m,c} Es (HPX_FLAG_SYNTHESIS)
+    // FP32 plans on the tensor cores: the synthesis operators transposed into
+    // tiles of 128 latitude modes x the chain's degrees (FP16 pairs, K-chunks of
+    // 32), their row scales, the tile table (m, c, k0), each tile's K-chunk count,
+    // operator offset and first row scale; the packed coefficients and their
+    // per-(map, m, c) scales
+    void* synT = nullptr;
+    void* synRinv = nullptr;
+    int* synTiles = nullptr;
+    int* synNch = nullptr;
+    int64_t* synOff = nullptr;
+    int64_t* synRowBase = nullptr;
+    void* synScale = nullptr;
+    void* synBpk = nullptr;
+    int synNtiles = 0;
     void* jres = nullptr;          // T [B][npix]: Jacobi residual maps (HPX_FLAG_JACOBI)
     void* jalm = nullptr;          // cplx<T> [B][n_alm]: Jacobi update
     // sub-plan of an uneven batch whose maps are not adjacent in the caller's
@@ -210,6 +224,10 @@ int prepare_fused_tc(hpx_plan_s* P);
 // D of the sweeps path on the tensor cores: plan-time layout (0 on success) and
 // the launch (bvec -> beta, like launch_dense)
 int prepare_dense_tc(hpx_plan_s* P);
+// the synthesis operators on the tensor cores (from synM; 0 on success) and the
+// launch (alm -> bvec, like launch_synth_apply)
+int prepare_synth_tc(hpx_plan_s* P);
+void launch_synth_tc(const hpx_plan_s* P, const float* alm, cudaStream_t s);
 void launch_dense_tc(const hpx_plan_s* P, cudaStream_t s);
 void launch_timeout_selftest(const hpx_plan_s* P, int spins, cudaStream_t s);
 // HPX_FLAG_CHECKED: records HPX_ERR_NONFINITE in *status if any of the n reals

@@ -37,10 +37,12 @@ def _random_alm(L, B, seed, alpha=1.0):
 @pytest.mark.parametrize("sweeps", [False, True], ids=["operators", "sweeps"])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 @pytest.mark.parametrize("nside,lmax,B", [(2, 4, 2), (4, 8, 3), (8, 16, 2), (8, 11, 2), (16, 32, 3), (64, 128, 2),
-                                          (128, 256, 17)])
+                                          (128, 256, 17), (32, 57, 33)])
 def test_synthesis_matches_oracle(hp, prec, nside, lmax, B, sweeps):
-    """operators: per-order synthesis operators R_{m,c} Es built at plan time;
-    sweeps: transposed sweeps and the Legendre-to-Fourier table per call."""
+    """operators: per-order synthesis operators R_{m,c} Es built at plan time
+    (FP32 plans of more than 8 maps: on the tensor cores; 33 maps span two
+    32-map column tiles); sweeps: transposed sweeps and the Legendre-to-Fourier
+    table per call."""
     a = _random_alm(lmax, B, seed=nside + lmax)
     cdt = np.complex128 if prec == "fp64" else np.complex64
     a = a.astype(cdt)
