@@ -40,6 +40,9 @@ TRAFFIC_OVER_ALGORITHMIC = {
     "lat_fft": (0.53804 + 0.24894) / 0.80688,                      # lat_fft_pair_ct_kernel, packed b
     "spread": (0.54846 + 0.49414) / 1.07532,                       # spread_rb_kernel
 }
+# forms of the FP32 run-time sweep kernel (hpx_plan_tuning)
+SWEEP_FORMS = ["complex lanes, 32 stages per pass", "complex lanes, 16 stages per pass",
+               "real lanes, 32 stages per pass"]
 # FP32 SIMT peak: 152 SMs x 128 FP32 lanes x 2 flop/FMA x 2.070 GHz (maximum SM clock)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 
@@ -362,7 +365,7 @@ def gradient_leg(hp, torch, stream, args):
     ns, L, B = 2048, 4096, 8
     rng = np.random.default_rng(2048)
     x = torch.as_tensor(rng.standard_normal((B, 12 * ns * ns)).astype(np.float32), device="cuda")
-    plan = hp.Plan(ns, L, B, "fp32")
+    plan = hp.Plan(ns, L, B, "fp32", autotune=True)   # the sweeps: stages per pass and FFT launch shapes
     w = torch.zeros(L + 1, dtype=torch.float64, device="cuda")
     w[2:] = 1.0 / torch.arange(2, L + 1, dtype=torch.float64, device="cuda")
     cstar = torch.as_tensor(np.r_[0.0, 0.0, np.arange(2, L + 1, dtype=np.float64) ** -2.0], device="cuda")
@@ -386,9 +389,10 @@ def gradient_leg(hp, torch, stream, args):
     torch.cuda.synchronize()
     t = e0.elapsed_time(e1) / n / 1e3
     path = "sweeps" if plan.flags & hp.HPX_FLAG_SWEEPS else "per-order operators"
+    form = SWEEP_FORMS[plan.tuning[2]]
     plan.close()
     return {"value": B * 12 * ns * ns / t / 1e9, "unit": "Gpix/s (loss + map gradient)", "ms_per_step": t * 1e3,
-            "path": path, "inputs": "seeded white-noise maps"}
+            "path": path, "sweep_form": form, "inputs": "seeded white-noise maps"}
 
 
 # ------------------------------------------------------------------ GPU arm
@@ -622,7 +626,7 @@ def main():
 
     # the run-time Givens sweeps (HPX_FLAG_SWEEPS): D applied alone and the rotation kernel,
     # stage by stage, same batch
-    plan_sw = hp.Plan(NSIDE, LMAX, nb, "fp32", sweeps=True)
+    plan_sw = hp.Plan(NSIDE, LMAX, nb, "fp32", sweeps=True, autotune=True)
     alm_sw = torch.empty_like(alm)
     for _ in range(2):
         plan_sw.analyze(maps, out=alm_sw)
@@ -647,7 +651,8 @@ def main():
                             "peak": "FP32 FMA pipes: 152 SMs x 128 lanes x 2 flop x 2.070 GHz"},
               "lat_solve": {"flops": sw_work["lat_solve"][1],
                             "tflops": sw_work["lat_solve"][1] / (sw_stage["lat_solve"] / 1e3) / 1e12},
-              "max_abs_diff_vs_default": float((alm_sw - alm).abs().max() / alm.abs().max())}
+              "max_abs_diff_vs_default": float((alm_sw - alm).abs().max() / alm.abs().max()),
+              "sweep_form": SWEEP_FORMS[plan_sw.tuning[2]]}
     plan_sw.close()
     del alm_sw
 
@@ -729,7 +734,8 @@ def main():
             "fp32_batched_over_fp64_single": value / world / fp64["value"],
             "stages_ms_per_launch": per_launch, "plan_build_s": plan_build_s, "plan_gb": plan.nbytes / 1e9,
             "plan_path": "sweeps" if plan.flags & hp.HPX_FLAG_SWEEPS else "per-order operators",
-            "launch_shapes": {"ring_fft_elems_per_thread": plan.tuning[0], "grid_fft_elems_per_thread": plan.tuning[1]}}
+            "launch_shapes": {"ring_fft_elems_per_thread": plan.tuning[0], "grid_fft_elems_per_thread": plan.tuning[1],
+                              "b_packing": "own pass" if plan.tuning[3] else "in the grid-FFT kernel"}}
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

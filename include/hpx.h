@@ -88,9 +88,12 @@ extern "C" {
 /* HPX_FLAG_AUTOTUNE: at plan creation, on scratch buffers allocated and freed
  *   inside hpx_plan_ex: (1) time the ring-FFT and grid-FFT stages of the plan's
  *   batch with 16 and with 32 elements per thread (launch shapes of the
- *   compile-time FFT kernels) and keep the faster of each (hpx_plan_tuning;
- *   remembered per nside, lmax, batch and precision for the process's later
- *   plans); (2) when the per-order operators were built, time one analysis
+ *   compile-time FFT kernels), for FP32 plans that run the sweeps per call the
+ *   three forms of the sweep kernel, and for the tensor-core paths the two
+ *   placements of the packing of b, and keep the fastest of each
+ *   (hpx_plan_tuning; remembered per nside, lmax, batch, precision and path for
+ *   the process's later plans); (2) when the
+ *   per-order operators were built, time one analysis
  *   through them and through the run-time sweeps and keep the faster path; if
  *   that is the sweeps the operators are freed and HPX_FLAG_SWEEPS is set
  *   (hpx_plan_flags). */
@@ -238,16 +241,23 @@ int64_t hpx_plan_bytes(const hpx_plan_s* plan);
 int hpx_plan_flags(const hpx_plan_s* plan);
 /* Kernel launches of one hpx_analyze call (ring FFTs: one per transform length). */
 int hpx_plan_launches(const hpx_plan_s* plan);
-/* Launch shapes in effect (HPX_FLAG_AUTOTUNE, else 16 and 16): elements per
- * thread of the ring-FFT and of the grid-FFT kernels.  HPX_ERR_ARG for NULL
- * arguments or an uneven-batch plan. */
-int hpx_plan_tuning(const hpx_plan_s* plan, int* ring_elems, int* fft_elems);
-/* Sets those launch shapes (16 or 32 each; e.g. the values an earlier process's
- * HPX_FLAG_AUTOTUNE chose) and drops the plan's captured graphs, which are
- * captured again by the next call.  Results do not depend on the shapes: every
- * transform runs the same radix passes in the same order, only their split over
- * the threads differs.  HPX_ERR_ARG for other values or an uneven-batch plan. */
-int hpx_plan_set_tuning(hpx_plan_s* plan, int ring_elems, int fft_elems);
+/* Launch shapes in effect (HPX_FLAG_AUTOTUNE, else 16, 16, 0 and 0): elements
+ * per thread of the ring-FFT and of the grid-FFT kernels, the form of the FP32
+ * run-time Givens sweeps of 4 maps or more (0: one complex column per lane, 32
+ * stages per pass; 1: the same with 16 stages; 2: one real column per lane, 32
+ * stages), and whether the tensor-core paths' FP16-pair right-hand sides are
+ * written by a pass of their own (1) or by the grid-FFT kernel (0).  HPX_ERR_ARG
+ * for NULL arguments or an uneven-batch plan. */
+int hpx_plan_tuning(const hpx_plan_s* plan, int* ring_elems, int* fft_elems, int* sweep_form, int* pack_pass);
+/* Sets those launch shapes (16 or 32, 16 or 32, 0..2, 0 or 1; e.g. the values
+ * an earlier process's HPX_FLAG_AUTOTUNE chose) and drops the
+ * plan's captured graphs, which are captured again by the next call.  Results do
+ * not depend on the shapes: every transform runs the same radix passes in the
+ * same order, every sweep the same rotations on the same values and both
+ * packings the same scalings and roundings; only the split of the work over the
+ * threads (or the number of trips through memory) differs.  HPX_ERR_ARG for
+ * other values or an uneven-batch plan. */
+int hpx_plan_set_tuning(hpx_plan_s* plan, int ring_elems, int fft_elems, int sweep_form, int pack_pass);
 
 /* Stage timing for profiling.  With profiling enabled (enable = 1) every
  * hpx_analyze records CUDA events on the plan's stream around each of its

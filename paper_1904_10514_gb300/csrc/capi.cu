@@ -442,21 +442,26 @@ struct TuneKey {
         return std::tie(ns, L, B, prec) < std::tie(o.ns, o.L, o.B, o.prec);
     }
 };
+struct TuneVal {
+    int ringE, latE, rotForm, packSep;   // ring / grid-FFT elements per thread, sweep form, b packing
+};
 std::mutex g_tune_mutex;
-std::map<TuneKey, std::pair<int, int>> g_tune_cache;   // (ring elements per thread, grid-FFT elements per thread)
+std::map<TuneKey, TuneVal> g_tune_cache;
 
-// Times one stage (ring FFT: stage 0, grid FFT: stage 1) of the analysis for
-// every launch shape and keeps the fastest.
-float time_stage(hpx_plan_s* P, const void* maps, int stage, cudaEvent_t e0, cudaEvent_t e1) {
+// Times one stage (ring FFT: stage 0, grid FFT: stage 1, run-time sweeps:
+// stage 2, writing into the scratch alm) of the analysis with the plan's
+// current launch shape: one warm-up, then the best of three.
+float time_stage(hpx_plan_s* P, const void* maps, void* alm, int stage, cudaEvent_t e0, cudaEvent_t e1) {
     float best = 0.f;
-    for (int r = 0; r < 4; ++r) {   // one warm-up, then the best of three
+    for (int r = 0; r < 4; ++r) {
         cudaEventRecord(e0, P->stream);
         if (P->precision == HPX_FP64) {
             if (stage == 0) hpx::launch_ring_fft<double>(P, (const double*)maps, P->stream);
             else hpx::launch_lat_fft<double>(P, P->stream);
         } else {
             if (stage == 0) hpx::launch_ring_fft<float>(P, (const float*)maps, P->stream);
-            else hpx::launch_lat_fft<float>(P, P->stream, hpx::packs_b(P));
+            else if (stage == 1) hpx::launch_lat_fft<float>(P, P->stream, hpx::packs_b(P));
+            else hpx::launch_rot<float>(P, (float*)alm, P->stream);
         }
         cudaEventRecord(e1, P->stream);
         cudaEventSynchronize(e1);
@@ -467,27 +472,49 @@ float time_stage(hpx_plan_s* P, const void* maps, int stage, cudaEvent_t e0, cud
     return best;
 }
 
-void tune_shapes(hpx_plan_s* P, const void* maps, cudaEvent_t e0, cudaEvent_t e1) {
-    const TuneKey key{P->g.ns, P->g.L, P->g.B, P->precision};
+void tune_shapes(hpx_plan_s* P, const void* maps, void* alm, cudaEvent_t e0, cudaEvent_t e1) {
+    const bool sweeps = !P->fusedM && P->precision == HPX_FP32;   // the FP32 run-time sweeps run per call
+    const TuneKey key{P->g.ns, P->g.L, P->g.B, P->precision * 2 + (sweeps ? 1 : 0)};
     {
         std::lock_guard<std::mutex> lock(g_tune_mutex);
         auto it = g_tune_cache.find(key);
         if (it != g_tune_cache.end()) {
-            P->ringE = it->second.first;
-            P->latE = it->second.second;
+            P->ringE = it->second.ringE;
+            P->latE = it->second.latE;
+            P->rotForm = it->second.rotForm;
+            P->packSep = it->second.packSep;
             return;
         }
     }
-    float t[2][2];
+    float t[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
     for (int e = 0; e < 2; ++e) {
         P->ringE = P->latE = e ? 32 : 16;
-        t[0][e] = time_stage(P, maps, 0, e0, e1);
-        t[1][e] = time_stage(P, maps, 1, e0, e1);
+        t[0][e] = time_stage(P, maps, alm, 0, e0, e1);
+        t[1][e] = time_stage(P, maps, alm, 1, e0, e1);
     }
     P->ringE = t[0][1] < t[0][0] ? 32 : 16;
     P->latE = t[1][1] < t[1][0] ? 32 : 16;
+    P->rotForm = 0;
+    if (sweeps) {   // the three forms of the sweep kernel
+        float best = 0.f;
+        for (int f = 0; f < 3; ++f) {
+            const int keep = P->rotForm;
+            P->rotForm = f;
+            const float tf = time_stage(P, maps, alm, 2, e0, e1);
+            if (f == 0 || tf < best) best = tf;
+            else P->rotForm = keep;
+        }
+    }
+    // packed b for the tensor cores: in the grid-FFT kernel or in a pass of its own
+    if (hpx::packs_b(P)) {
+        P->packSep = 0;
+        const float tin = time_stage(P, maps, alm, 1, e0, e1);
+        P->packSep = 1;
+        const float tsep = time_stage(P, maps, alm, 1, e0, e1);
+        P->packSep = tsep < tin ? 1 : 0;
+    }
     std::lock_guard<std::mutex> lock(g_tune_mutex);
-    g_tune_cache[key] = {P->ringE, P->latE};
+    g_tune_cache[key] = {P->ringE, P->latE, P->rotForm, P->packSep};
 }
 
 // HPX_FLAG_AUTOTUNE: choose the launch shapes of the FFT stages (tune_shapes),
@@ -505,7 +532,7 @@ int autotune(hpx_plan_s* P) {
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    tune_shapes(P, maps, e0, e1);
+    tune_shapes(P, maps, alm, e0, e1);
     if (!P->fusedM) {   // only the sweeps: nothing else to choose
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
@@ -772,19 +799,24 @@ int hpx_plan_lmax(const hpx_plan_s* P) { return P ? P->g.L : -1; }
 int64_t hpx_plan_bytes(const hpx_plan_s* P) { return P ? P->bytes : 0; }
 int hpx_plan_flags(const hpx_plan_s* P) { return P ? (int)P->flags : -1; }
 
-int hpx_plan_tuning(const hpx_plan_s* P, int* ring_elems, int* fft_elems) {
-    if (!P || P->group || !ring_elems || !fft_elems) return set_err(HPX_ERR_ARG);
+int hpx_plan_tuning(const hpx_plan_s* P, int* ring_elems, int* fft_elems, int* sweep_form, int* pack_pass) {
+    if (!P || P->group || !ring_elems || !fft_elems || !sweep_form || !pack_pass) return set_err(HPX_ERR_ARG);
     *ring_elems = P->ringE;
     *fft_elems = P->latE;
+    *sweep_form = P->rotForm;
+    *pack_pass = P->packSep;
     return set_err(HPX_OK);
 }
 
-int hpx_plan_set_tuning(hpx_plan_s* P, int ring_elems, int fft_elems) {
+int hpx_plan_set_tuning(hpx_plan_s* P, int ring_elems, int fft_elems, int sweep_form, int pack_pass) {
     if (!P || P->group) return set_err(HPX_ERR_ARG);
     auto ok = [](int e) { return e == 16 || e == 32; };
-    if (!ok(ring_elems) || !ok(fft_elems)) return set_err(HPX_ERR_ARG);
+    if (!ok(ring_elems) || !ok(fft_elems) || sweep_form < 0 || sweep_form > 2 || (pack_pass != 0 && pack_pass != 1))
+        return set_err(HPX_ERR_ARG);
     P->ringE = ring_elems;
     P->latE = fft_elems;
+    P->rotForm = sweep_form;
+    P->packSep = pack_pass;
     // captured graphs hold the old launch shapes: capture again on the next call
     for (auto& e : P->graphs) cudaGraphExecDestroy(e.exec);
     P->graphs.clear();

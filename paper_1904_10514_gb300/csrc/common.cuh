@@ -26,6 +26,12 @@ __device__ __forceinline__ void cp_async8(void* dst, const void* src, int src_by
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
 }
 
+// 4-byte asynchronous global -> shared copy; src_bytes = 0 writes zeros.
+__device__ __forceinline__ void cp_async4(void* dst, const void* src, int src_bytes) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
+}
+
 // The power of two 2^(target - floor(log2 mx)) (clamped to normal floats), which
 // brings a largest magnitude mx into [2^target, 2^(target+1)); 1 when mx is zero
 // or not finite.

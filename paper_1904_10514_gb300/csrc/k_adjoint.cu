@@ -18,6 +18,7 @@
 #include "fft_ct.cuh"
 #include "plan.h"
 #include "plan_math.h"
+#include "sweep.cuh"
 
 namespace hpx {
 
@@ -103,6 +104,119 @@ __global__ void __launch_bounds__(128) rot_adj_kernel(const T* __restrict__ alm,
     for (int f = F - 1; f >= 0; --f) {
         const int s_lo = f * KMAX;
         sweep_pass_adj<T, KMAX>(chain, ldc, n, block(s_lo, KMAX), coff(s_lo, KMAX));
+        n += KMAX;
+    }
+}
+
+// FP32: the same transposed pass with the angle rows and the chain inputs of
+// step t staged through a per-warp ring of shared memory RB - 1 steps ahead
+// (8-byte copies of the 32 angles, one 4-byte copy per lane).  Every lane of
+// the warp runs it (lanes without a column neither load nor store chain values).
+// The outputs go to indices above every input still to be read, so the
+// prefetch never reads a value this pass has rewritten.
+template <int K, int RB>
+__device__ __forceinline__ void sweep_pass_adj_staged(float* chain, int64_t ldc, int n_in, bool live,
+                                                      const cplx<float>* __restrict__ A, int coff,
+                                                      cplx<float>* ring) {
+    constexpr int SL = SweepRing<RB>::kSlot;
+    const int lane = threadIdx.x & 31;
+    float carry[K], pipe[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) { carry[k] = 0.f; pipe[k] = 0.f; }
+    const int steps = n_in + 2 * K - 1;
+    auto issue = [&](int t) {
+        if (t < steps) {
+            cplx<float>* slot = ring + (t % RB) * SL;
+            cp_async8(slot + lane, A + (int64_t)t * 32 + lane, 8);
+            const bool have = live && t < n_in;
+            cp_async4(reinterpret_cast<float*>(slot + 32) + lane,
+                      have ? chain + (int64_t)(n_in - 1 - t) * ldc : (const float*)A, have ? 4 : 0);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+#pragma unroll
+    for (int q = 0; q < RB - 1; ++q) issue(q);
+    for (int t = 0; t < steps; ++t) {
+        __syncwarp();
+        issue(t + RB - 1);
+        asm volatile("cp.async.wait_group %0;" ::"n"(RB - 1) : "memory");
+        __syncwarp();
+        const cplx<float>* slot = ring + (t % RB) * SL;
+        const float x0 = reinterpret_cast<const float*>(slot + 32)[lane];
+        const cplx<float>* row = slot + coff;
+#pragma unroll
+        for (int k = K - 1; k >= 0; --k) {
+            const float x = (k == 0) ? x0 : pipe[k - 1];
+            const cplx<float> cs = row[k];
+            const float o = cs.i * x + cs.r * carry[k];
+            carry[k] = cs.r * x - cs.i * carry[k];
+            pipe[k] = o;
+        }
+        const int j = n_in + 2 * K - 2 - t;
+        if (live && j >= 0 && j < n_in + K) chain[(int64_t)j * ldc] = pipe[K - 1];
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncwarp();
+}
+
+// rot_adj_kernel for FP32 with the staged passes (one real column per lane,
+// warps of 2 per block; the whole warp stays in the passes).
+template <int KMAX>
+__global__ void __launch_bounds__(64, 8) rot_adj_staged_kernel(const float* __restrict__ alm, float* __restrict__ beta2,
+                                                              const int64_t* __restrict__ skOff,
+                                                              const cplx<float>* __restrict__ skewT, int nq, int P2,
+                                                              int L, int p, int B, int64_t nalm, int ngroups,
+                                                              int nitems, float wpos, bool dropim) {
+    constexpr int RB = 8;
+    constexpr int SL = SweepRing<RB>::kSlot;
+    __shared__ __align__(16) cplx<float> rings[2][RB * SL];
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp >= nitems) return;   // whole warps leave together
+    cplx<float>* ring = rings[(threadIdx.x >> 5) & 1];
+    const int g = warp % ngroups;
+    const int c = (warp / ngroups) & 1;
+    const int m = L - warp / (2 * ngroups);
+    const int m0 = m & 1;
+    const int S = (m - m0) >> 1;
+    const int ncol = 2 * B;
+    const int col = 32 * g + lane;
+    const bool live = col < ncol;
+    const int par = (m0 + c) & 1;
+    const int q0 = (m0 == 1 && c == 1) ? 1 : 0;
+    float* chain = beta2 + (((int64_t)m * 2 + par) * P2 + q0) * ncol + (live ? col : 0);
+    const int64_t ldc = ncol;
+    int n = chain_len(m, c, L);
+    if (live) {   // order-m chain from the weighted input coefficients
+        const int b = col >> 1, ri = col & 1;
+        const float w = (m == 0) ? 1.f : wpos;
+        const bool drop = dropim && ri == 1 && (m == 0 || m == p);
+        const float* in = alm + (int64_t)b * nalm * 2 + ri;
+        const int64_t base = (int64_t)m * (2 * L + 1 - m) / 2 + m + c;
+        for (int i = 0; i < n; ++i) chain[(int64_t)i * ldc] = drop ? 0.f : w * in[(base + 2 * i) * 2];
+    }
+    __syncwarp();
+    const int F = S / KMAX, r = S % KMAX;
+    auto block = [&](int s_lo, int K) {
+        const int e = 32 - (s_lo & 31) - K;
+        return skewT + (skOff[(size_t)(m0 * 2 + c) * nq + (s_lo >> 5)] + e) * 32;
+    };
+    auto coff = [&](int s_lo, int K) { return 32 - (s_lo & 31) - K; };
+#define HPX_SUBPASS_ADJ(KK)                                                                        \
+    if (KK < KMAX && (r & KK)) {                                                                   \
+        const int s_lo = F * KMAX + (r & ~(2 * KK - 1));                                           \
+        sweep_pass_adj_staged<KK, RB>(chain, ldc, n, live, block(s_lo, KK), coff(s_lo, KK), ring); \
+        n += KK;                                                                                   \
+    }
+    HPX_SUBPASS_ADJ(1)
+    HPX_SUBPASS_ADJ(2)
+    HPX_SUBPASS_ADJ(4)
+    HPX_SUBPASS_ADJ(8)
+    HPX_SUBPASS_ADJ(16)
+#undef HPX_SUBPASS_ADJ
+    for (int f = F - 1; f >= 0; --f) {
+        const int s_lo = f * KMAX;
+        sweep_pass_adj_staged<KMAX, RB>(chain, ldc, n, live, block(s_lo, KMAX), coff(s_lo, KMAX), ring);
         n += KMAX;
     }
 }
@@ -412,8 +526,13 @@ void launch_adjoint(const hpx_plan_s* P, const T* alm, T* maps, cudaStream_t s, 
         const int nitems = (g.L + 1) * 2 * ngroups;
         const int blocks = (nitems * 32 + 127) / 128;
         constexpr int KMAX = sizeof(T) == 4 ? 32 : 16;
-        rot_adj_kernel<T, KMAX><<<blocks, 128, 0, s>>>(alm, (T*)P->beta, t.skOff, (const cplx<T>*)t.skewT, t.nq,
-                                                       g.P2, g.L, g.p, g.B, g.nalm, ngroups, nitems, wpos, true);
+        if constexpr (sizeof(T) == 4)   // angle rows and inputs staged ahead of use
+            rot_adj_staged_kernel<32><<<(nitems * 32 + 63) / 64, 64, 0, s>>>(
+                (const float*)alm, (float*)P->beta, t.skOff, (const cplx<float>*)t.skewT, t.nq, g.P2, g.L, g.p, g.B,
+                g.nalm, ngroups, nitems, (float)wpos, true);
+        else
+            rot_adj_kernel<T, KMAX><<<blocks, 128, 0, s>>>(alm, (T*)P->beta, t.skOff, (const cplx<T>*)t.skewT, t.nq,
+                                                           g.P2, g.L, g.p, g.B, g.nalm, ngroups, nitems, wpos, true);
     }
     {
         const int nmp = g.L / 2 + 1;
@@ -664,8 +783,13 @@ void launch_sh_synthesis(const hpx_plan_s* P, const T* alm, T* maps, cudaStream_
         const int nitems = (g.L + 1) * 2 * ngroups;
         const int blocks = (nitems * 32 + 127) / 128;
         constexpr int KMAX = sizeof(T) == 4 ? 32 : 16;
-        rot_adj_kernel<T, KMAX><<<blocks, 128, 0, s>>>(alm, (T*)P->beta, t.skOff, (const cplx<T>*)t.skewT, t.nq,
-                                                       g.P2, g.L, g.p, g.B, g.nalm, ngroups, nitems, T(1), false);
+        if constexpr (sizeof(T) == 4)
+            rot_adj_staged_kernel<32><<<(nitems * 32 + 63) / 64, 64, 0, s>>>(
+                (const float*)alm, (float*)P->beta, t.skOff, (const cplx<float>*)t.skewT, t.nq, g.P2, g.L, g.p, g.B,
+                g.nalm, ngroups, nitems, 1.f, false);
+        else
+            rot_adj_kernel<T, KMAX><<<blocks, 128, 0, s>>>(alm, (T*)P->beta, t.skOff, (const cplx<T>*)t.skewT, t.nq,
+                                                           g.P2, g.L, g.p, g.B, g.nalm, ngroups, nitems, T(1), false);
         const int nmp = g.L / 2 + 1;
         dim3 grid((nmp * g.B + AC - 1) / AC, (g.P2 + AK - 1) / AK, 4);
         dense_adj_kernel<T><<<grid, 256, 0, s>>>((const T*)t.Es, (const cplx<T>*)P->beta, (cplx<T>*)P->bvec, g.P2,

@@ -500,23 +500,28 @@ __global__ void __launch_bounds__(NT, ((1 << LOGM) / NT == 16 ? (LOGM <= 13 ? 10
     }
 }
 
-// The packed form of b (fp16pair.cuh) from bvec, one block per (order, map):
-// for the grid-FFT kernels that write bvec only.
-__global__ void __launch_bounds__(256) pack_b_kernel(const cplx<float>* __restrict__ bvec,
-                                                     unsigned char* __restrict__ bpk, float* __restrict__ bscale,
-                                                     int p, int L, int P2) {
-    __shared__ float red32[32];
-    const int b = blockIdx.x, m = blockIdx.y;   // maps fastest, like the grid-FFT kernel
-    const cplx<float>* col = bvec + ((int64_t)b * (p + 1) + m) * 2 * P2;
-    auto val = [&](int par, int k) { return k < P2 ? col[par * P2 + k] : mk<float>(0.f, 0.f); };
-    float mx = 0.f;
-    for (int e = threadIdx.x; e < 2 * P2; e += blockDim.x) {
-        const cplx<float> v = col[e];
-        mx = fmaxf(mx, fmaxf(fabsf(v.r), fabsf(v.i)));
+// The packed form of b (fp16pair.cuh) from bvec and the column maxima in
+// bscale: one block of 256 threads per (map tile, order, parity), two K-chunks
+// per step; thread = (chunk, group of 8 k, map), so that the 8 lanes of a
+// 128-byte line of the packed layout are adjacent in a warp (full-line stores)
+// and each thread reads 64 contiguous bytes of its map's column.
+__global__ void __launch_bounds__(256) pack_b_tiles_kernel(const cplx<float>* __restrict__ bvec,
+                                                           unsigned char* __restrict__ bpk,
+                                                           const float* __restrict__ bscale, int p, int L, int P2,
+                                                           int B) {
+    const int m = blockIdx.x, par = blockIdx.y, mt = blockIdx.z;
+    const int nch = (P2 + 31) >> 5;
+    const int t = threadIdx.x, n = t & 31, kg = (t >> 5) & 3, cl = t >> 7;
+    const int b = mt * 32 + n;
+    if (b >= B) return;   // columns past the batch stay zero
+    const float sc = pow2_scale(bscale[(int64_t)b * (L + 1) + m], 13);
+    const cplx<float>* col = bvec + (((int64_t)b * (p + 1) + m) * 2 + par) * P2;
+    unsigned char* half = packed_half(bpk, b, m, par, L, nch);
+    const int offr = packed_col_offset(b);
+    for (int ch = cl; ch < nch; ch += 2) {
+        const int g8 = ch * 4 + kg;
+        pack_group(half, offr, g8, sc, [&](int k) { return k < P2 ? col[k] : mk<float>(0.f, 0.f); });
     }
-    mx = block_max(mx, red32);
-    if (threadIdx.x == 0) bscale[(int64_t)b * (L + 1) + m] = mx;
-    pack_column(bpk, b, m, L, P2, pow2_scale(mx, 13), val, threadIdx.x, blockDim.x);
 }
 
 bool packs_b(const hpx_plan_s* P) {
@@ -527,8 +532,19 @@ template <class T>
 void launch_lat_fft(const hpx_plan_s* P, cudaStream_t s, bool packed) {
     const auto& g = P->g;
     packed = packed && sizeof(T) == 4 && P->bpk && P->bscale;
+    // packed b: either written by the compile-time grid-FFT kernel itself, or
+    // (P->packSep, and the other grid lengths) FP32 b with the column maxima as
+    // atomic maxima of the float bits, then one pass of pack_b_tiles_kernel
     int logM = 0;
     while ((1 << logM) < g.M) ++logM;
+    const bool inFft = packed && !P->packSep && logM >= 12 && logM <= 14;
+    if (packed && !inFft) cudaMemsetAsync(P->bscale, 0, (size_t)g.B * (g.L + 1) * sizeof(float), s);
+    float* bsc = packed ? P->bscale : nullptr;
+    auto pack_pass = [&]() {
+        if (packed && !inFft)
+            pack_b_tiles_kernel<<<dim3(g.L + 1, 2, (g.B + 31) / 32), 256, 0, s>>>(
+                (const cplx<float>*)P->bvec, P->bpk, P->bscale, g.p, g.L, g.P2, g.B);
+    };
     const size_t smem = (size_t)(g.M + g.M / 16) * sizeof(cplx<T>);
     if (logM >= 12 && logM <= 14) {   // two orders per block, compile-time grid length
         const size_t smem2 = (size_t)(g.M + g.M / 16 + 2 * (g.p + 1)) * sizeof(cplx<T>);
@@ -537,12 +553,13 @@ void launch_lat_fft(const hpx_plan_s* P, cudaStream_t s, bool packed) {
             cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
             kern<<<grid2, threads, smem2, s>>>((const cplx<T>*)P->U, (cplx<T>*)P->bvec, (const T*)P->t.dec,
                                                (const cplx<T>*)P->t.twid, g.Lmax, g.p, g.L, g.P2, P->ldu,
-                                               packed ? P->bscale : nullptr, packed ? P->bpk : nullptr);
+                                               bsc, inFft ? P->bpk : nullptr);
         };
         const bool e32 = P->latE == 32;   // elements per thread (the plan's tuning), else 16
         if (logM == 12) { if (e32) run(lat_fft_pair_ct_kernel<T, 12, 128>, 128); else run(lat_fft_pair_ct_kernel<T, 12, 256>, 256); }
         else if (logM == 13) { if (e32) run(lat_fft_pair_ct_kernel<T, 13, 256>, 256); else run(lat_fft_pair_ct_kernel<T, 13, 512>, 512); }
         else run(lat_fft_pair_ct_kernel<T, 14, 512>, 512);
+        pack_pass();
         return;
     }
     if (logM >= 5) {   // two orders per block
@@ -552,18 +569,15 @@ void launch_lat_fft(const hpx_plan_s* P, cudaStream_t s, bool packed) {
         dim3 grid2((g.L + 2) / 2, g.B);
         kern2<<<grid2, 512, smem2, s>>>((const cplx<T>*)P->U, (cplx<T>*)P->bvec, (const T*)P->t.dec,
                                         (const cplx<T>*)P->t.twid, g.Lmax, g.M, logM, g.p, g.L, g.P2, P->ldu,
-                                        nullptr);
+                                        bsc);
     } else {
         auto kern = g.M > 16 * 512 ? lat_fft_kernel<T, 32> : lat_fft_kernel<T, 16>;
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         dim3 grid(g.L + 1, g.B);
         kern<<<grid, 512, smem, s>>>((const cplx<T>*)P->U, (cplx<T>*)P->bvec, (const T*)P->t.dec,
-                                     (const cplx<T>*)P->t.twid, g.Lmax, g.M, logM, g.p, g.L, g.P2, P->ldu, nullptr);
+                                     (const cplx<T>*)P->t.twid, g.Lmax, g.M, logM, g.p, g.L, g.P2, P->ldu, bsc);
     }
-    if (packed) {
-        dim3 gp(g.B, g.L + 1);
-        pack_b_kernel<<<gp, 256, 0, s>>>((const cplx<float>*)P->bvec, P->bpk, P->bscale, g.p, g.L, g.P2);
-    }
+    pack_pass();
 }
 
 template void launch_spread<float>(const hpx_plan_s*, cudaStream_t);

@@ -38,7 +38,7 @@ constexpr int kRotRing = 8;
 // shared memory ahead of use (sweep_pass_staged); every lane of a warp runs
 // the passes (lanes without a map neither load nor store chain values).
 template <int KMAX>
-__global__ void __launch_bounds__(64, 6) rot_staged_kernel(cplx<float>* __restrict__ beta2, cplx<float>* __restrict__ alm,
+__global__ void __launch_bounds__(64, (KMAX == 32 ? 6 : 10)) rot_staged_kernel(cplx<float>* __restrict__ beta2, cplx<float>* __restrict__ alm,
                                                         const int64_t* __restrict__ skOff,
                                                         const cplx<float>* __restrict__ skew, int nq, int P2, int L,
                                                         int B, int64_t nalm, int ngroups, int nitems) {
@@ -85,6 +85,60 @@ __global__ void __launch_bounds__(64, 6) rot_staged_kernel(cplx<float>* __restri
     cplx<float>* out = alm + (int64_t)col * nalm;
     const int64_t base = (int64_t)m * (2 * L + 1 - m) / 2 + m + c;
     for (int i = 0; i < n; ++i) out[base + 2 * i] = chain[(int64_t)i * ldc];
+}
+
+// FP32, one real column per lane (sweep_pass_staged_real): warp = (m, chain c,
+// group of 32 real columns: re and im of 16 maps), so a batch of B maps fills
+// 2B lanes.  Output: the lane's part of a_{m+c+2i}^m.
+template <int KMAX>
+__global__ void __launch_bounds__(64, 8) rot_staged_real_kernel(cplx<float>* __restrict__ beta2,
+                                                               cplx<float>* __restrict__ alm,
+                                                               const int64_t* __restrict__ skOff,
+                                                               const cplx<float>* __restrict__ skew, int nq, int P2,
+                                                               int L, int B, int64_t nalm, int ngroups, int nitems) {
+    constexpr int SL = SweepRing<kRotRing>::kSlot;
+    __shared__ __align__(16) cplx<float> rings[2][kRotRing * SL];
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp >= nitems) return;   // whole warps leave together (nitems counts warps)
+    cplx<float>* ring = rings[(threadIdx.x >> 5) & 1];
+    const int g = warp % ngroups;
+    const int c = (warp / ngroups) & 1;
+    const int m = L - warp / (2 * ngroups);
+    const int m0 = m & 1;
+    const int S = (m - m0) >> 1;
+    const int rc = 32 * g + lane;   // real column: 2 map + part
+    const bool live = rc < 2 * B;
+    const int par = (m0 + c) & 1;
+    const int q0 = (m0 == 1 && c == 1) ? 1 : 0;
+    float* chain = reinterpret_cast<float*>(beta2 + (((int64_t)m * 2 + par) * P2 + q0) * B) + (live ? rc : 0);
+    const int64_t ldc = 2 * (int64_t)B;
+    int n = chain_len(m0, c, L);
+    int s0 = 0;
+    auto block = [&](int s) {
+        return skew + (skOff[(size_t)(m0 * 2 + c) * nq + (s >> 5)] + 2 * (s & 31)) * 32;
+    };
+    while (S - s0 >= KMAX && n > 0) {
+        sweep_pass_staged_real<KMAX, kRotRing>(chain, ldc, n, live, block(s0), s0 & 31, ring);
+        n -= KMAX;
+        s0 += KMAX;
+    }
+#define HPX_SUBPASS(KK)                                                                      \
+    if (KK < KMAX && S - s0 >= KK && n > 0) {                                                \
+        sweep_pass_staged_real<KK, kRotRing>(chain, ldc, n, live, block(s0), s0 & 31, ring); \
+        n -= KK;                                                                             \
+        s0 += KK;                                                                            \
+    }
+    HPX_SUBPASS(16)
+    HPX_SUBPASS(8)
+    HPX_SUBPASS(4)
+    HPX_SUBPASS(2)
+    HPX_SUBPASS(1)
+#undef HPX_SUBPASS
+    if (!live) return;
+    float* out = reinterpret_cast<float*>(alm + (int64_t)(rc >> 1) * nalm) + (rc & 1);
+    const int64_t base = (int64_t)m * (2 * L + 1 - m) / 2 + m + c;
+    for (int i = 0; i < n; ++i) out[2 * (base + 2 * i)] = chain[(int64_t)i * ldc];
 }
 
 template <class T, int KMAX>
@@ -233,15 +287,33 @@ __global__ void __launch_bounds__(64) rot_stage_kernel(const cplx<T>* __restrict
 template <class T>
 void launch_rot(const hpx_plan_s* P, T* alm, cudaStream_t s) {
     const auto& g = P->g;
-    if (g.B >= 16) {
+    // one lane per map: from 16 maps (FP64) or 4 maps (FP32, whose angle rows are
+    // staged ahead by cp.async: at nside 2048 the per-stage angle tables of
+    // rot_stage_kernel, 134 MB, no longer stay in L2 and its per-step loads wait
+    // on DRAM)
+    if (g.B >= (sizeof(T) == 4 ? 4 : 16)) {
         const int ngroups = (g.B + 31) / 32;
         const int nitems = (g.L + 1) * 2 * ngroups;
         const int threads = 64;
         const int blocks = (nitems * 32 + threads - 1) / threads;
         if constexpr (sizeof(T) == 4) {
-            rot_staged_kernel<32><<<blocks, threads, 0, s>>>((cplx<float>*)P->beta, (cplx<float>*)alm, P->t.skOff,
-                                                            (const cplx<float>*)P->t.skew, P->t.nq, g.P2, g.L,
-                                                            g.B, g.nalm, ngroups, nitems);
+            // the plan's form (HPX_FLAG_AUTOTUNE): one complex column per lane with 32
+            // stages per pass (168 registers, 12 warps per SM) or 16 (twice the passes
+            // over the chains, 20 warps per SM), or one real column per lane with 32
+            // stages (128 registers, 16 warps per SM, 2B lanes for B maps)
+            if (P->rotForm == 2) {   // one real column per lane
+                const int rgroups = (2 * g.B + 31) / 32, ritems = (g.L + 1) * 2 * rgroups;
+                rot_staged_real_kernel<32><<<(ritems * 32 + threads - 1) / threads, threads, 0, s>>>(
+                    (cplx<float>*)P->beta, (cplx<float>*)alm, P->t.skOff, (const cplx<float>*)P->t.skew, P->t.nq,
+                    g.P2, g.L, g.B, g.nalm, rgroups, ritems);
+            } else if (P->rotForm == 1)
+                rot_staged_kernel<16><<<blocks, threads, 0, s>>>((cplx<float>*)P->beta, (cplx<float>*)alm,
+                                                                P->t.skOff, (const cplx<float>*)P->t.skew, P->t.nq,
+                                                                g.P2, g.L, g.B, g.nalm, ngroups, nitems);
+            else
+                rot_staged_kernel<32><<<blocks, threads, 0, s>>>((cplx<float>*)P->beta, (cplx<float>*)alm,
+                                                                P->t.skOff, (const cplx<float>*)P->t.skew, P->t.nq,
+                                                                g.P2, g.L, g.B, g.nalm, ngroups, nitems);
         } else {
             rot_kernel<T, 16><<<blocks, threads, 0, s>>>((cplx<T>*)P->beta, (cplx<T>*)alm, P->t.skOff,
                                                         (const cplx<T>*)P->t.skew, P->t.nq, g.P2, g.L, g.B,

@@ -135,6 +135,13 @@ struct hpx_plan_s {
     // launch shapes of the compile-time FFT kernels: elements per thread (16 or 32)
     // of the ring stage and of the grid FFT (HPX_FLAG_AUTOTUNE times both)
     int ringE = 16, latE = 16;
+    // form of the FP32 run-time sweeps (HPX_FLAG_AUTOTUNE): 0 = one complex column
+    // per lane, 32 stages per pass; 1 = the same with 16 stages; 2 = one real
+    // column per lane, 32 stages
+    int rotForm = 0;
+    // the tensor-core paths' packed b: written by the grid-FFT kernel (0) or by
+    // a separate full-line pass over FP32 b (1; HPX_FLAG_AUTOTUNE)
+    int packSep = 0;
 
     // uneven batches (group plans): one uniform sub-plan per distinct nside
     bool group = false;

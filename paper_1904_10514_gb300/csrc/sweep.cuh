@@ -60,6 +60,16 @@ __device__ __forceinline__ void sweep_pass(cplx<T>* chain, int64_t ldc, int n, c
 // step t are brought into a per-warp ring of RB shared-memory slots by 8-byte
 // cp.async copies RB - 1 steps ahead of their use, so a step waits only for
 // shared-memory loads.  ring: RB x 64 complex of this warp's shared memory.
+// One Givens rotation of (carry, x) in FP32 with fixed roundings (no
+// compiler-chosen contraction), so that every form of the staged sweeps gives
+// the same bits: c carry + s x and c x - s carry.
+__device__ __forceinline__ float rot_hi(float c, float s, float carry, float x) {
+    return __fmaf_rn(c, carry, __fmul_rn(s, x));
+}
+__device__ __forceinline__ float rot_lo(float c, float s, float carry, float x) {
+    return __fmaf_rn(c, x, -__fmul_rn(s, carry));
+}
+
 template <int RB>
 struct SweepRing {
     static constexpr int kSlot = 64;   // complex per slot: 32 angles + 32 lane inputs
@@ -99,9 +109,59 @@ __device__ __forceinline__ void sweep_pass_staged(cplx<T>* chain, int64_t ldc, i
         for (int k = K - 1; k >= 0; --k) {
             const cplx<T> x = (k == 0) ? x0 : pipe[k - 1];
             const cplx<T> cs = row[k];
-            const T c = cs.r, s = cs.i;
-            pipe[k] = mk<T>(c * carry[k].r + s * x.r, c * carry[k].i + s * x.i);
-            carry[k] = mk<T>(c * x.r - s * carry[k].r, c * x.i - s * carry[k].i);
+            // each part rotated with the roundings of sweep_pass_staged_real
+            pipe[k] = mk<T>(rot_hi(cs.r, cs.i, carry[k].r, x.r), rot_hi(cs.r, cs.i, carry[k].i, x.i));
+            carry[k] = mk<T>(rot_lo(cs.r, cs.i, carry[k].r, x.r), rot_lo(cs.r, cs.i, carry[k].i, x.i));
+        }
+        const int j = t - 2 * K + 1;
+        if (live && j >= 0 && j < nout) chain[(int64_t)j * ldc] = pipe[K - 1];
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncwarp();
+}
+
+// The same pass with one real column per lane (the real or the imaginary part of
+// one map's chain: the two parts share every rotation): half the registers and
+// half the arithmetic of a complex lane, so batches of fewer than 32 maps fill
+// twice as many lanes.  The ring slot holds the 32 angles and the 32 lanes'
+// inputs (4-byte copies).
+template <int K, int RB>
+__device__ __forceinline__ void sweep_pass_staged_real(float* chain, int64_t ldc, int n, bool live,
+                                                       const cplx<float>* __restrict__ A, int coff,
+                                                       cplx<float>* ring) {
+    constexpr int SL = SweepRing<RB>::kSlot;
+    const int lane = threadIdx.x & 31;
+    float carry[K], pipe[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) { carry[k] = 0.f; pipe[k] = 0.f; }
+    const int steps = n + 2 * (K - 1);
+    const int nout = n - K;   // outputs of the last stage
+    auto issue = [&](int t) {
+        if (t < steps) {
+            cplx<float>* slot = ring + (t % RB) * SL;
+            cp_async8(slot + lane, A + (int64_t)t * 32 + lane, 8);
+            const bool have = live && t < n;
+            cp_async4(reinterpret_cast<float*>(slot + 32) + lane, have ? chain + (int64_t)t * ldc : (const float*)A,
+                      have ? 4 : 0);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+#pragma unroll
+    for (int q = 0; q < RB - 1; ++q) issue(q);
+    for (int t = 0; t < steps; ++t) {
+        __syncwarp();                 // every lane is done with the slot refilled next
+        issue(t + RB - 1);
+        asm volatile("cp.async.wait_group %0;" ::"n"(RB - 1) : "memory");
+        __syncwarp();                 // step t's copies of all lanes are visible
+        const cplx<float>* slot = ring + (t % RB) * SL;
+        const float x0 = reinterpret_cast<const float*>(slot + 32)[lane];
+        const cplx<float>* row = slot + coff;
+#pragma unroll
+        for (int k = K - 1; k >= 0; --k) {
+            const float x = (k == 0) ? x0 : pipe[k - 1];
+            const cplx<float> cs = row[k];
+            pipe[k] = rot_hi(cs.r, cs.i, carry[k], x);
+            carry[k] = rot_lo(cs.r, cs.i, carry[k], x);
         }
         const int j = t - 2 * K + 1;
         if (live && j >= 0 && j < nout) chain[(int64_t)j * ldc] = pipe[K - 1];

@@ -42,10 +42,11 @@ def _run(hp, maps, nside, lmax, prec, sweeps=False, simt=False):
 @pytest.mark.parametrize("path", ["fused", "sweeps", "simt"])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 @pytest.mark.parametrize("nside,lmax,B", [(2, 4, 3), (4, 8, 3), (4, 5, 3), (8, 16, 3), (16, 32, 3), (16, 29, 17),
-                                          (32, 64, 3), (64, 128, 33), (128, 256, 20)])
+                                          (32, 64, 3), (64, 128, 33), (128, 256, 20), (64, 117, 6)])
 def test_parity_full(hp, prec, nside, lmax, B, path):
     """fused: per-order operators (tensor cores for FP32 batches of 9+ maps);
-    simt: the same on the FP32 pipes; sweeps: D and the Givens sweeps at run time."""
+    simt: the same on the FP32 pipes; sweeps: D and the Givens sweeps at run time
+    (FP32 from 4 maps: D on the tensor cores and the staged sweep kernel)."""
     if path == "simt" and (prec == "fp64" or B <= 8):
         pytest.skip("the tensor-core variant only exists for FP32 batches of 9+ maps")
     maps, _ = skies.small_powerlaw_maps(nside, B, seed=100 + nside, alpha=2.0, noise=1e-3, lmax=2 * nside)
@@ -332,26 +333,33 @@ def test_autotune_keeps_a_correct_path(hp, prec, nside, B):
 
 def test_launch_shapes_give_identical_results(hp):
     """The ring-FFT and grid-FFT kernels with 16 or 32 elements per thread run the
-    same radix passes in the same order, so every launch shape (and whatever
-    HPX_FLAG_AUTOTUNE picks) gives bit-identical coefficients; shapes outside
-    {16, 32} are refused."""
-    ns, B = 1024, 2
+    same radix passes in the same order, the three forms of the run-time sweeps
+    (complex lanes with 32 or 16 stages per pass, real lanes) the same rotations
+    on the same values, and both placements of the
+    FP16-pair packing of b the same scalings and roundings, so every launch shape
+    (and whatever HPX_FLAG_AUTOTUNE picks) gives bit-identical coefficients, on the
+    run-time sweeps (FP32 pipes, 2 maps) and on the tensor-core D (4 maps); other
+    values are refused."""
+    ns = 1024
     rng = np.random.default_rng(71)
-    x = torch.as_tensor(rng.standard_normal((B, 12 * ns * ns)).astype(np.float32), device="cuda")
-    plan = hp.Plan(ns, -1, B, "fp32", sweeps=True, autotune=True)
-    assert plan.tuning[0] in (16, 32) and plan.tuning[1] in (16, 32)
-    tuned = plan.analyze(x).clone()
-    outs = []
-    for shapes in ((16, 16), (32, 32), (16, 32)):
-        plan.tuning = shapes
-        assert plan.tuning == shapes
-        outs.append(plan.analyze(x).clone())
-    torch.cuda.synchronize()
-    for o in outs:
-        assert torch.equal(o, tuned)
-    for bad in ((8, 16), (16, 64), (0, 0)):
-        with pytest.raises(hp.HpxError):
-            plan.tuning = bad
+    for B in (2, 4):
+        x = torch.as_tensor(rng.standard_normal((B, 12 * ns * ns)).astype(np.float32), device="cuda")
+        plan = hp.Plan(ns, -1, B, "fp32", sweeps=True, autotune=True)
+        t = plan.tuning
+        assert t[0] in (16, 32) and t[1] in (16, 32) and t[2] in (0, 1, 2) and t[3] in (0, 1)
+        tuned = plan.analyze(x).clone()
+        outs = []
+        for shapes in ((16, 16, 0, 0), (32, 32, 1, 1), (16, 32, 2, 0), (32, 16, 2, 1)):
+            plan.tuning = shapes
+            assert plan.tuning == shapes
+            outs.append(plan.analyze(x).clone())
+        torch.cuda.synchronize()
+        for o in outs:
+            assert torch.equal(o, tuned)
+        for bad in ((8, 16, 0, 0), (16, 64, 0, 0), (16, 16, 3, 0), (16, 16, 0, 2)):
+            with pytest.raises(hp.HpxError):
+                plan.tuning = bad
+        plan.close()
 
 
 def test_graph_tensor_core_path_matches_eager(hp):
