@@ -735,7 +735,8 @@ def main():
             "stages_ms_per_launch": per_launch, "plan_build_s": plan_build_s, "plan_gb": plan.nbytes / 1e9,
             "plan_path": "sweeps" if plan.flags & hp.HPX_FLAG_SWEEPS else "per-order operators",
             "launch_shapes": {"ring_fft_elems_per_thread": plan.tuning[0], "grid_fft_elems_per_thread": plan.tuning[1],
-                              "b_packing": "own pass" if plan.tuning[3] else "in the grid-FFT kernel"}}
+                              "b_packing": "own pass" if plan.tuning[3] else "in the grid-FFT kernel",
+                              "bluestein_rings": "four quarter-length transforms" if plan.tuning[4] else "whole ring"}}
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -241,23 +241,29 @@ int64_t hpx_plan_bytes(const hpx_plan_s* plan);
 int hpx_plan_flags(const hpx_plan_s* plan);
 /* Kernel launches of one hpx_analyze call (ring FFTs: one per transform length). */
 int hpx_plan_launches(const hpx_plan_s* plan);
-/* Launch shapes in effect (HPX_FLAG_AUTOTUNE, else 16, 16, 0 and 0): elements
- * per thread of the ring-FFT and of the grid-FFT kernels, the form of the FP32
- * run-time Givens sweeps of 4 maps or more (0: one complex column per lane, 32
- * stages per pass; 1: the same with 16 stages; 2: one real column per lane, 32
- * stages), and whether the tensor-core paths' FP16-pair right-hand sides are
- * written by a pass of their own (1) or by the grid-FFT kernel (0).  HPX_ERR_ARG
- * for NULL arguments or an uneven-batch plan. */
-int hpx_plan_tuning(const hpx_plan_s* plan, int* ring_elems, int* fft_elems, int* sweep_form, int* pack_pass);
-/* Sets those launch shapes (16 or 32, 16 or 32, 0..2, 0 or 1; e.g. the values
- * an earlier process's HPX_FLAG_AUTOTUNE chose) and drops the
- * plan's captured graphs, which are captured again by the next call.  Results do
- * not depend on the shapes: every transform runs the same radix passes in the
+/* Launch shapes in effect (HPX_FLAG_AUTOTUNE, else 16, 16, 0, 0 and 0):
+ * elements per thread of the ring-FFT and of the grid-FFT kernels, the form of
+ * the FP32 run-time Givens sweeps of 4 maps or more (0: one complex column per
+ * lane, 32 stages per pass; 1: the same with 16 stages; 2: one real column per
+ * lane, 32 stages), whether the tensor-core paths' FP16-pair right-hand sides
+ * are written by a pass of their own (1) or by the grid-FFT kernel (0), and the
+ * form of the Bluestein ring classes of 4096 points and more (0: one
+ * convolution of the whole ring; 1: the DFT of nphi = 4j points from four
+ * Bluestein transforms of its quarter-length subsequences and one radix-4 step).
+ * HPX_ERR_ARG for NULL arguments or an uneven-batch plan. */
+int hpx_plan_tuning(const hpx_plan_s* plan, int* ring_elems, int* fft_elems, int* sweep_form, int* pack_pass,
+                    int* ring_form);
+/* Sets those launch shapes (16 or 32, 16 or 32, 0..2, 0 or 1, 0 or 1; e.g. the
+ * values an earlier process's HPX_FLAG_AUTOTUNE chose) and drops the plan's
+ * captured graphs, which are captured again by the next call.  The first four
+ * do not change the results: every transform runs the same radix passes in the
  * same order, every sweep the same rotations on the same values and both
- * packings the same scalings and roundings; only the split of the work over the
- * threads (or the number of trips through memory) differs.  HPX_ERR_ARG for
- * other values or an uneven-batch plan. */
-int hpx_plan_set_tuning(hpx_plan_s* plan, int ring_elems, int fft_elems, int sweep_form, int pack_pass);
+ * packings the same scalings and roundings; only the split of the work over
+ * the threads (or the number of trips through memory) differs.  The ring form
+ * computes the same DFTs with other roundings.  HPX_ERR_ARG for other values
+ * or an uneven-batch plan. */
+int hpx_plan_set_tuning(hpx_plan_s* plan, int ring_elems, int fft_elems, int sweep_form, int pack_pass,
+                        int ring_form);
 
 /* Stage timing for profiling.  With profiling enabled (enable = 1) every
  * hpx_analyze records CUDA events on the plan's stream around each of its

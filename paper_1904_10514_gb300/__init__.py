@@ -111,8 +111,8 @@ def lib():
             "hpx_analyze_vjp": (i32, [vp, vp, vp]),
             "hpx_sh_synthesis_adjoint": (i32, [vp, vp, vp]),
             "hpx_healpix_analysis": (i32, [vp, vp, vp, i32]),
-            "hpx_plan_tuning": (i32, [vp] + [ctypes.POINTER(ctypes.c_int)] * 4),
-            "hpx_plan_set_tuning": (i32, [vp, i32, i32, i32, i32]),
+            "hpx_plan_tuning": (i32, [vp] + [ctypes.POINTER(ctypes.c_int)] * 5),
+            "hpx_plan_set_tuning": (i32, [vp, i32, i32, i32, i32, i32]),
             "hpx_cl_vjp": (i32, [vp, vp, vp, vp]),
             "hpx_stage_times": (i32, [vp, ctypes.POINTER(ctypes.c_float), i32, ctypes.POINTER(ctypes.c_int)]),
         }
@@ -254,8 +254,8 @@ class Plan:
     @property
     def tuning(self):
         """(ring-FFT elements per thread, grid-FFT elements per thread, sweep form,
-        separate packing pass of b) in effect (HPX_FLAG_AUTOTUNE)."""
-        v = [ctypes.c_int(0) for _ in range(4)]
+        separate packing pass of b, Bluestein ring form) in effect (HPX_FLAG_AUTOTUNE)."""
+        v = [ctypes.c_int(0) for _ in range(5)]
         self._check(lib().hpx_plan_tuning(self.handle, *[ctypes.byref(x) for x in v]), "hpx_plan_tuning")
         return tuple(x.value for x in v)
 

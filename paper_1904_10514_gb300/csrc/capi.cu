@@ -70,7 +70,8 @@ void free_plan(hpx_plan_s* P) {
     if (P->cap) cudaStreamDestroy(P->cap);
     auto& t = P->t;
     void* ptrs[] = {t.nphi, t.startN, t.startS, t.pow2, t.logn, t.fftL, t.logL, t.shOff, t.chOff,
-                    t.bhOff, t.shift, t.chirp, t.bhat, t.twid, t.poleN, t.poleS, t.polew, t.rowptr,
+                    t.bhOff, t.shift, t.chirp, t.bhat, t.twid, t.ch4Off, t.bh4Off, t.chirp4, t.bhat4, t.poleN,
+                    t.poleS, t.polew, t.rowptr,
                     t.ent, t.entw, t.dec, t.D, t.tstart, t.hwn, t.angOff, t.ang, t.skOff, t.skew, t.skewT, t.nrowptr, t.nent, t.nentw, t.nstart, t.swts, t.hstart, t.hwts, t.Es, t.shifted, t.C, t.cgH, P->Y, P->U, P->bvec,
                     P->fusedM, P->fusedOff, P->fusedTiles, P->tcOff, P->tcFirst, P->tcRinv, P->bscale, P->d_status, P->synM, P->ringList,
                     P->jres, P->jalm, P->dTC, P->dRinv, P->dTiles, P->dTcOff, P->mapIdx, P->bpk, P->synT,
@@ -229,6 +230,8 @@ hpx_plan_s* hpx_plan_ex(const hpx_plan_desc* d) {
     t.pow2 = up.vec(tb.pow2); t.logn = up.vec(tb.logn); t.fftL = up.vec(tb.fftL); t.logL = up.vec(tb.logL);
     t.shOff = up.vec(tb.shOff); t.chOff = up.vec(tb.chOff); t.bhOff = up.vec(tb.bhOff);
     t.shift = up.real(tb.shift, fp64); t.chirp = up.real(tb.chirp, fp64); t.bhat = up.real(tb.bhat, fp64);
+    t.ch4Off = up.vec(tb.ch4Off); t.bh4Off = up.vec(tb.bh4Off);
+    t.chirp4 = up.real(tb.chirp4, fp64); t.bhat4 = up.real(tb.bhat4, fp64);
     t.twid = up.real(tb.twid, fp64);
     t.poleN = up.vec(tb.poleN); t.poleS = up.vec(tb.poleS); t.polew = up.vec(tb.polew);
     t.npole = (int)tb.polew.size();
@@ -443,7 +446,7 @@ struct TuneKey {
     }
 };
 struct TuneVal {
-    int ringE, latE, rotForm, packSep;   // ring / grid-FFT elements per thread, sweep form, b packing
+    int ringE, latE, rotForm, packSep, ringForm;   // shapes, sweep form, b packing, Bluestein ring form
 };
 std::mutex g_tune_mutex;
 std::map<TuneKey, TuneVal> g_tune_cache;
@@ -483,6 +486,7 @@ void tune_shapes(hpx_plan_s* P, const void* maps, void* alm, cudaEvent_t e0, cud
             P->latE = it->second.latE;
             P->rotForm = it->second.rotForm;
             P->packSep = it->second.packSep;
+            P->ringForm = it->second.ringForm;
             return;
         }
     }
@@ -494,6 +498,11 @@ void tune_shapes(hpx_plan_s* P, const void* maps, void* alm, cudaEvent_t e0, cud
     }
     P->ringE = t[0][1] < t[0][0] ? 32 : 16;
     P->latE = t[1][1] < t[1][0] ? 32 : 16;
+    {   // the Bluestein ring classes: whole-ring or quarter-length convolutions
+        P->ringForm = 1;
+        const float t4 = time_stage(P, maps, alm, 0, e0, e1);
+        P->ringForm = t4 < t[0][P->ringE == 32 ? 1 : 0] ? 1 : 0;
+    }
     P->rotForm = 0;
     if (sweeps) {   // the three forms of the sweep kernel
         float best = 0.f;
@@ -514,7 +523,7 @@ void tune_shapes(hpx_plan_s* P, const void* maps, void* alm, cudaEvent_t e0, cud
         P->packSep = tsep < tin ? 1 : 0;
     }
     std::lock_guard<std::mutex> lock(g_tune_mutex);
-    g_tune_cache[key] = {P->ringE, P->latE, P->rotForm, P->packSep};
+    g_tune_cache[key] = {P->ringE, P->latE, P->rotForm, P->packSep, P->ringForm};
 }
 
 // HPX_FLAG_AUTOTUNE: choose the launch shapes of the FFT stages (tune_shapes),
@@ -799,8 +808,11 @@ int hpx_plan_lmax(const hpx_plan_s* P) { return P ? P->g.L : -1; }
 int64_t hpx_plan_bytes(const hpx_plan_s* P) { return P ? P->bytes : 0; }
 int hpx_plan_flags(const hpx_plan_s* P) { return P ? (int)P->flags : -1; }
 
-int hpx_plan_tuning(const hpx_plan_s* P, int* ring_elems, int* fft_elems, int* sweep_form, int* pack_pass) {
-    if (!P || P->group || !ring_elems || !fft_elems || !sweep_form || !pack_pass) return set_err(HPX_ERR_ARG);
+int hpx_plan_tuning(const hpx_plan_s* P, int* ring_elems, int* fft_elems, int* sweep_form, int* pack_pass,
+                    int* ring_form) {
+    if (!P || P->group || !ring_elems || !fft_elems || !sweep_form || !pack_pass || !ring_form)
+        return set_err(HPX_ERR_ARG);
+    *ring_form = P->ringForm;
     *ring_elems = P->ringE;
     *fft_elems = P->latE;
     *sweep_form = P->rotForm;
@@ -808,11 +820,14 @@ int hpx_plan_tuning(const hpx_plan_s* P, int* ring_elems, int* fft_elems, int* s
     return set_err(HPX_OK);
 }
 
-int hpx_plan_set_tuning(hpx_plan_s* P, int ring_elems, int fft_elems, int sweep_form, int pack_pass) {
+int hpx_plan_set_tuning(hpx_plan_s* P, int ring_elems, int fft_elems, int sweep_form, int pack_pass,
+                        int ring_form) {
     if (!P || P->group) return set_err(HPX_ERR_ARG);
     auto ok = [](int e) { return e == 16 || e == 32; };
-    if (!ok(ring_elems) || !ok(fft_elems) || sweep_form < 0 || sweep_form > 2 || (pack_pass != 0 && pack_pass != 1))
+    if (!ok(ring_elems) || !ok(fft_elems) || sweep_form < 0 || sweep_form > 2 || (pack_pass != 0 && pack_pass != 1) ||
+        (ring_form != 0 && ring_form != 1))
         return set_err(HPX_ERR_ARG);
+    P->ringForm = ring_form;
     P->ringE = ring_elems;
     P->latE = fft_elems;
     P->rotForm = sweep_form;

@@ -23,15 +23,16 @@ __device__ __forceinline__ int padc(int i) { return i + (i >> 4); }
 // in-place shared-memory passes they read / write a[padded].  BAR: a barrier
 // between the loads and the stores (the pass reads and writes the same array).
 // tw: e^{-2 pi i t / twlen}, twstep = twlen / N.
+// tid: this thread's index among the NT threads of the transform (a block may
+// run several transforms side by side, each on its own NT threads and array).
 template <class T, int N, int R, int LOGS, int NT, bool INV, bool BAR, class LD, class ST>
-__device__ __forceinline__ void pass(const cplx<T>* __restrict__ tw, int twstep, LD ld, ST st) {
+__device__ __forceinline__ void pass(const cplx<T>* __restrict__ tw, int twstep, LD ld, ST st, int tid) {
     constexpr int S = 1 << LOGS;
     constexpr int NG = N / R;
     constexpr int G = (NG + NT - 1) / NT;
     constexpr int IN_STRIDE = NG + NG / 16;                 // padded distance of the R inputs (NG % 16 == 0)
     static_assert(NG % 16 == 0, "pass: N / R must be a multiple of 16");
     static_assert(NG % NT == 0 || G == 1, "pass: groups must split evenly over the threads");
-    const int tid = threadIdx.x;
     cplx<T> x[G][R];
 #pragma unroll
     for (int gg = 0; gg < G; ++gg) {
@@ -67,18 +68,18 @@ __device__ __forceinline__ void pass(const cplx<T>* __restrict__ tw, int twstep,
 
 // Passes of span 16^s, s >= 1, up to the last one, over the padded array a.
 template <class T, int LOGN, int LOGS, int NT, bool INV, class ST>
-__device__ __forceinline__ void rest(cplx<T>* a, const cplx<T>* __restrict__ tw, int twstep, ST last_st) {
+__device__ __forceinline__ void rest(cplx<T>* a, const cplx<T>* __restrict__ tw, int twstep, ST last_st, int tid) {
     constexpr int N = 1 << LOGN;
     constexpr int LEFT = LOGN - LOGS;   // log2 of the radices still to apply
     auto lds = [&](int, int pi) { return a[pi]; };
     auto sts = [&](int, int pi, cplx<T> v) { a[pi] = v; };
     if constexpr (LEFT > 4) {
-        pass<T, N, 16, LOGS, NT, INV, true>(tw, twstep, lds, sts);
+        pass<T, N, 16, LOGS, NT, INV, true>(tw, twstep, lds, sts, tid);
         __syncthreads();
-        rest<T, LOGN, LOGS + 4, NT, INV>(a, tw, twstep, last_st);
+        rest<T, LOGN, LOGS + 4, NT, INV>(a, tw, twstep, last_st, tid);
     } else {
         constexpr int R = 1 << LEFT;
-        pass<T, N, R, LOGS, NT, INV, true>(tw, twstep, lds, last_st);
+        pass<T, N, R, LOGS, NT, INV, true>(tw, twstep, lds, last_st, tid);
     }
 }
 
@@ -86,15 +87,18 @@ __device__ __forceinline__ void rest(cplx<T>* a, const cplx<T>* __restrict__ tw,
 // inputs through ld(nat, padded) (SYNC: ld reads a itself, so all threads load
 // before any stores), the passes in between run in the padded shared array a,
 // and the last pass hands every output to st(nat, padded, value).  Ends with a
-// barrier.
+// barrier.  The barriers are the block's: side-by-side transforms (tid = the
+// thread's index in its transform's group) run their passes in step.
 template <class T, int LOGN, int NT, bool INV, bool SYNC, class LD, class ST>
-__device__ __forceinline__ void fft(cplx<T>* a, const cplx<T>* __restrict__ tw, int twstep, LD ld, ST st) {
+__device__ __forceinline__ void fft(cplx<T>* a, const cplx<T>* __restrict__ tw, int twstep, LD ld, ST st,
+                                    int tid = -1) {
     constexpr int N = 1 << LOGN;
     static_assert(LOGN >= 8, "fft: at least 256 points");
+    if (tid < 0) tid = threadIdx.x;
     auto sts = [&](int, int pi, cplx<T> v) { a[pi] = v; };
-    pass<T, N, 16, 0, NT, INV, SYNC>(tw, twstep, ld, sts);
+    pass<T, N, 16, 0, NT, INV, SYNC>(tw, twstep, ld, sts, tid);
     __syncthreads();
-    rest<T, LOGN, 4, NT, INV>(a, tw, twstep, st);
+    rest<T, LOGN, 4, NT, INV>(a, tw, twstep, st, tid);
     __syncthreads();
 }
 

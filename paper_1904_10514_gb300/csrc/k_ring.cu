@@ -118,6 +118,75 @@ __global__ void __launch_bounds__(NT, ((1 << LOGN) / NT == 16 ? (LOGN <= 13 ? 10
                      rowN, rowS, equator, tid, NT);
 }
 
+// A Bluestein ring of nphi = 4j points as four transforms of j points: with
+// t = 4u + s the DFT is Z[q + r j] = sum_s (-i)^{s r} W^{s q} Y_s[q]
+// (W = e^{-2 pi i / nphi}, q < j, r < 4), Y_s the DFT of the subsequence
+// z[4u + s].  Each Y_s is a Bluestein convolution of L/4 = 2^(LOGN-2) points
+// (L the ring's convolution length, L/4 >= 2j), run on NT/4 threads of the
+// block beside the other three (compile-time FFT, one padded quarter of the
+// buffer each): a quarter of the transformed-kernel table per ring and one
+// radix-16 pass fewer than the full-length convolution.  The radix-4 step writes
+// Z into the free tail of the quarters (quarter r, from slot padc(j)), and the
+// output rows follow as in ring_ct_kernel.
+template <class T, int LOGN, int NT>
+__global__ void __launch_bounds__(NT, (LOGN <= 13 ? 1024 / NT : 1)) ring4_ct_kernel(
+    const T* __restrict__ maps, cplx<T>* __restrict__ Y, const int* __restrict__ nphi_t,
+    const int* __restrict__ startN_t, const int* __restrict__ startS_t, const int64_t* __restrict__ shOff_t,
+    const int64_t* __restrict__ ch4Off_t, const int64_t* __restrict__ bh4Off_t, const cplx<T>* __restrict__ shift,
+    const cplx<T>* __restrict__ chirp4, const cplx<T>* __restrict__ bhat4, const cplx<T>* __restrict__ tw, int twlen,
+    int p, int Q, int64_t npix, const int* __restrict__ ringlist, T ew, const int* __restrict__ shifted_t, int L,
+    const int64_t* __restrict__ mapIdx) {
+    constexpr int LOGQ = LOGN - 2, NQ = 1 << LOGQ, NTQ = NT / 4;
+    constexpr int QS = NQ + NQ / 16;   // one padded quarter
+    static_assert(NTQ % 32 == 0, "ring4: whole warps per quarter");
+    extern __shared__ unsigned char smem_raw[];
+    cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw);
+    const int i = ringlist[blockIdx.y];
+    const int b = blockIdx.x;
+    const int n = nphi_t[i], jq = n >> 2;
+    const int sN = startN_t[i], sS = startS_t[i];
+    const T* f = maps + (mapIdx ? mapIdx[b] : (int64_t)b * npix);
+    const int tid = threadIdx.x;
+    const int s = tid / NTQ, ltid = tid - s * NTQ;
+    cplx<T>* qb = buf + s * QS;
+    const cplx<T>* ch = chirp4 + ch4Off_t[i];
+    const cplx<T>* bh = bhat4 + bh4Off_t[i];
+    const int twstep = twlen >> LOGQ;
+    ct::fft<T, LOGQ, NTQ, false, false>(
+        qb, tw, twstep,
+        [&](int u, int) {
+            return u < jq ? mul(mk<T>(f[sN + 4 * u + s], f[sS + 4 * u + s]), ch[u]) : mk<T>(T(0), T(0));
+        },
+        [&](int k, int pi, cplx<T> v) { qb[pi] = mul(v, bh[k]); }, ltid);
+    ct::fft<T, LOGQ, NTQ, true, true>(
+        qb, tw, twstep, [&](int, int pi) { return qb[pi]; },
+        [&](int k, int pi, cplx<T> v) { qb[pi] = k < jq ? mul(v, ch[k]) : v; }, ltid);
+    const int S0 = ct::padc(jq);   // first slot past the Y_s values (S0 + jq <= QS)
+    for (int q = tid; q < jq; q += NT) {
+        T sn, cs;
+        if constexpr (sizeof(T) == 4) sincospif(-2.f * (float)q / (float)n, &sn, &cs);
+        else sincospi(-2.0 * (double)q / (double)n, &sn, &cs);
+        const cplx<T> w1 = mk<T>(cs, sn), w2 = mul(w1, w1), w3 = mul(w1, w2);
+        const int pq = ct::padc(q);
+        const cplx<T> t0 = buf[pq], t1 = mul(w1, buf[QS + pq]), t2 = mul(w2, buf[2 * QS + pq]),
+                      t3 = mul(w3, buf[3 * QS + pq]);
+        const cplx<T> a = add(t0, t2), bb = sub(t0, t2), c = add(t1, t3), d = sub(t1, t3);
+        buf[S0 + q] = add(a, c);                                   // r = 0
+        buf[QS + S0 + q] = mk<T>(bb.r + d.i, bb.i - d.r);          // r = 1: bb - i d
+        buf[2 * QS + S0 + q] = sub(a, c);                          // r = 2
+        buf[3 * QS + S0 + q] = mk<T>(bb.r - d.i, bb.i + d.r);      // r = 3: bb + i d
+    }
+    __syncthreads();
+    cplx<T>* rowN = Y + ((int64_t)b * Q + (i + 1)) * (p + 1);
+    cplx<T>* rowS = Y + ((int64_t)b * Q + (Q - 2 - i)) * (p + 1);
+    ring_rows_out<T>(
+        [&](int k) {
+            const int r = (k >= jq) + (k >= 2 * jq) + (k >= 3 * jq);
+            return buf[r * QS + S0 + (k - r * jq)];
+        },
+        n, p, L, shift + shOff_t[i], shifted_t[i] != 0, ew, rowN, rowS, false, tid, NT);
+}
+
 // The step for ring pair i of map b by the whole block (runtime transform
 // length; the generic form behind ring_fft_kernel and ring_list_kernel).
 template <class T, int E>
@@ -326,6 +395,20 @@ void launch_ring_fft(const hpx_plan_s* P, const T* maps, cudaStream_t s, T ew, i
                                              (const cplx<T>*)t.bhat, (const cplx<T>*)t.twid, g.Lmax, g.p, g.Q,
                                              g.npix, P->ringList + c.first, ew, t.shifted, g.L, P->mapIdx);
         };
+        if (c.blue && P->ringForm == 1) {   // four quarter-length Bluestein transforms, N / 16 threads
+            auto run4 = [&](auto kern, int threads) {
+                cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                kern<<<grid, threads, smem, s>>>(maps, (cplx<T>*)P->Y, t.nphi, t.startN, t.startS, t.shOff,
+                                                 t.ch4Off, t.bh4Off, (const cplx<T>*)t.shift,
+                                                 (const cplx<T>*)t.chirp4, (const cplx<T>*)t.bhat4,
+                                                 (const cplx<T>*)t.twid, g.Lmax, g.p, g.Q, g.npix,
+                                                 P->ringList + c.first, ew, t.shifted, g.L, P->mapIdx);
+            };
+            if (c.N == 4096) run4(ring4_ct_kernel<T, 12, 256>, 256);
+            else if (c.N == 8192) run4(ring4_ct_kernel<T, 13, 512>, 512);
+            else run4(ring4_ct_kernel<T, 14, 512>, 512);
+            continue;
+        }
         // elements per thread: 16 (N / 16 threads) or, when the plan's tuning chose
         // it, 32 (N / 32 threads, two groups per thread and pass)
         const bool e32 = P->ringE == 32;

@@ -18,6 +18,8 @@ struct DevTables {
         *fftL = nullptr, *logL = nullptr;
     int64_t *shOff = nullptr, *chOff = nullptr, *bhOff = nullptr;
     void *shift = nullptr, *chirp = nullptr, *bhat = nullptr, *twid = nullptr;   // cplx<T>
+    int64_t *ch4Off = nullptr, *bh4Off = nullptr;   // quarter-length Bluestein tables (ring form 1)
+    void *chirp4 = nullptr, *bhat4 = nullptr;       // cplx<T>
     int *poleN = nullptr, *poleS = nullptr;
     double* polew = nullptr;
     int npole = 0;
@@ -135,6 +137,9 @@ struct hpx_plan_s {
     // launch shapes of the compile-time FFT kernels: elements per thread (16 or 32)
     // of the ring stage and of the grid FFT (HPX_FLAG_AUTOTUNE times both)
     int ringE = 16, latE = 16;
+    // Bluestein ring classes of 4096 points and more: one convolution of the whole
+    // ring (0) or four of its quarter-length subsequences (1; HPX_FLAG_AUTOTUNE)
+    int ringForm = 0;
     // form of the FP32 run-time sweeps (HPX_FLAG_AUTOTUNE): 0 = one complex column
     // per lane, 32 stages per pass; 1 = the same with 16 stages; 2 = one real
     // column per lane, 32 stages

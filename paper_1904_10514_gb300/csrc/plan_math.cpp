@@ -160,6 +160,8 @@ std::string build_tables(int nside, int lmax, bool fp64, PlanTables& t) {
     t.nphi.resize(np); t.startN.resize(np); t.startS.resize(np); t.pow2.resize(np);
     t.logn.resize(np); t.fftL.resize(np); t.logL.resize(np);
     t.shOff.resize(np); t.chOff.resize(np); t.bhOff.resize(np);
+    t.ch4Off.assign(np, 0); t.bh4Off.assign(np, 0);
+    int64_t ch4N = 0, bh4N = 0;
     std::vector<double> phi0(np), theta(np);
     int64_t shN = 0, chN = 0, bhN = 0;
     int lmaxfft = 8 * ns;   // the latitude NUFFT grid
@@ -183,8 +185,17 @@ std::string build_tables(int nside, int lmax, bool fp64, PlanTables& t) {
         lmaxfft = std::max(lmaxfft, Lb);
         t.shOff[i] = shN; shN += n / 2 + 1;
         t.chOff[i] = chN; t.bhOff[i] = bhN;
-        if (!t.pow2[i]) { chN += n; bhN += Lb; }
+        if (!t.pow2[i]) {
+            chN += n;
+            bhN += Lb;
+            t.ch4Off[i] = ch4N;
+            t.bh4Off[i] = bh4N;
+            ch4N += n / 4;
+            bh4N += Lb / 4;
+        }
     }
+    t.chirp4.assign(2 * ch4N, 0.0);
+    t.bhat4.assign(2 * bh4N, 0.0);
     t.Lmax = lmaxfft;
     t.shift.assign(2 * shN, 0.0);
     t.chirp.assign(2 * chN, 0.0);
@@ -220,6 +231,22 @@ std::string build_tables(int nside, int lmax, bool fp64, PlanTables& t) {
             for (int k = 0; k < Lb; ++k) {
                 t.bhat[2 * (t.bhOff[i] + k)] = b[k].real() / Lb;
                 t.bhat[2 * (t.bhOff[i] + k) + 1] = b[k].imag() / Lb;
+            }
+            // quarter-length subsequences: j = n / 4 points, convolution length Lb / 4 >= 2 j
+            const int jq = n / 4, Lq = Lb / 4;
+            std::vector<cd> bq(Lq, cd(0.0, 0.0));
+            for (int u = 0; u < jq; ++u) {
+                const long long r = ((long long)u * u) % (2LL * jq);
+                const double ang = kPi * (double)r / (double)jq;
+                t.chirp4[2 * (t.ch4Off[i] + u)] = std::cos(ang);
+                t.chirp4[2 * (t.ch4Off[i] + u) + 1] = -std::sin(ang);
+                bq[u] = cd(std::cos(ang), std::sin(ang));
+                if (u > 0) bq[Lq - u] = bq[u];
+            }
+            fft_host(bq);
+            for (int k = 0; k < Lq; ++k) {
+                t.bhat4[2 * (t.bh4Off[i] + k)] = bq[k].real() / Lq;
+                t.bhat4[2 * (t.bh4Off[i] + k) + 1] = bq[k].imag() / Lq;
             }
         }
     }

@@ -22,6 +22,11 @@ struct PlanTables {
     std::vector<double> shift;   // complex: (1/nphi) e^{-i m phi0}, Nyquist split folded in
     std::vector<double> chirp;   // complex: e^{-i pi k^2 / nphi} (Bluestein rings)
     std::vector<double> bhat;    // complex: FFT_L of the conjugate chirp, divided by L
+    // the same for the quarter-length subsequences z[4u + s] of a Bluestein ring
+    // (nphi = 4j: DFT_nphi from four DFT_j, each by Bluestein with L / 4 points)
+    std::vector<int64_t> ch4Off, bh4Off;
+    std::vector<double> chirp4;  // complex: e^{-i pi u^2 / j}, u < j
+    std::vector<double> bhat4;   // complex: FFT_{L/4} of the conjugate chirp, divided by L / 4
     int Lmax = 0;                // twiddle table covers FFT lengths up to Lmax
     std::vector<double> twid;    // complex: e^{-2 pi i k / Lmax}, k < Lmax/2
     int smem_ring = 0;           // largest in-CTA FFT length of step 1

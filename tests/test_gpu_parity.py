@@ -346,20 +346,54 @@ def test_launch_shapes_give_identical_results(hp):
         x = torch.as_tensor(rng.standard_normal((B, 12 * ns * ns)).astype(np.float32), device="cuda")
         plan = hp.Plan(ns, -1, B, "fp32", sweeps=True, autotune=True)
         t = plan.tuning
-        assert t[0] in (16, 32) and t[1] in (16, 32) and t[2] in (0, 1, 2) and t[3] in (0, 1)
+        assert t[0] in (16, 32) and t[1] in (16, 32) and t[2] in (0, 1, 2) and t[3] in (0, 1) and t[4] in (0, 1)
         tuned = plan.analyze(x).clone()
         outs = []
-        for shapes in ((16, 16, 0, 0), (32, 32, 1, 1), (16, 32, 2, 0), (32, 16, 2, 1)):
+        rf = t[4]   # the ring form changes the roundings; the other choices must not
+        for shapes in ((16, 16, 0, 0, rf), (32, 32, 1, 1, rf), (16, 32, 2, 0, rf), (32, 16, 2, 1, rf)):
             plan.tuning = shapes
             assert plan.tuning == shapes
             outs.append(plan.analyze(x).clone())
         torch.cuda.synchronize()
         for o in outs:
             assert torch.equal(o, tuned)
-        for bad in ((8, 16, 0, 0), (16, 64, 0, 0), (16, 16, 3, 0), (16, 16, 0, 2)):
+        for bad in ((8, 16, 0, 0, 0), (16, 64, 0, 0, 0), (16, 16, 3, 0, 0), (16, 16, 0, 2, 0), (16, 16, 0, 0, 2)):
             with pytest.raises(hp.HpxError):
                 plan.tuning = bad
         plan.close()
+
+
+def test_quarter_length_bluestein_rings(hp):
+    """Ring form 1 (the Bluestein rings of 4096 points and more as four
+    quarter-length Bluestein transforms and a radix-4 step) on maps 0 and 1 of
+    the benchmark workload at Nside 1024: against the oracle on a sample of
+    orders plus the edge orders (the parity gate), and per degree within half the
+    gate of ring form 0 (both are FP32 evaluations of the same DFTs)."""
+    ns, L = 1024, 2048
+    maps, alms = skies.workload_maps("bench_nside1024x32", nmaps=2, dtype=np.float32, return_alm=True)
+    x = torch.as_tensor(maps, device="cuda")
+    plan = hp.Plan(ns, L, 2, "fp32")
+    t = list(plan.tuning)
+    res = {}
+    for rf in (0, 1):
+        t[4] = rf
+        plan.tuning = tuple(t)
+        res[rf] = plan.analyze(x).cpu().numpy().astype(np.complex128)
+    plan.close()
+    assert not np.array_equal(res[0], res[1])   # the other form did run
+    strat = [int((k + 0.5) * (L + 1) / 6) for k in range(6)]
+    low = [0, 1, 2, L]
+    ref = hp2sph.analyze_columns(maps[0].astype(np.float64), ns, L, strat + low)
+    norms = per_l_norms(alms[0], L)
+    got = {m: res[1][0][hp2sph.alm_index(m, m, L):hp2sph.alm_index(m, m, L) + L - m + 1] for m in strat + low}
+    err = sampled_per_l_error({m: got[m] for m in strat}, {m: ref[m][0] for m in strat}, norms, L)
+    assert err < TOL["fp32"], err
+    for m in low:
+        l = np.arange(max(m, 2), L + 1)
+        d = np.abs(got[m][l - m] - ref[m][0][l - m]) / norms[l]
+        assert d.max() < TOL["fp32"], (m, d.max())
+    for b in range(2):
+        assert per_l_error(res[1][b], res[0][b], L)[2:].max() < 0.5 * TOL["fp32"]
 
 
 def test_graph_tensor_core_path_matches_eager(hp):
