@@ -73,3 +73,15 @@ def test_descriptor_fields_rejected_before_any_cuda_call(hp):
     assert hp.hpx_last_error() == hp.HPX_ERR_LMAX
     assert not hp.hpx_plan_ex(0, -1, 2, hp.HPX_FP32, 0, [8, 12], None)    # nside not a power of two
     assert hp.hpx_last_error() == hp.HPX_ERR_NSIDE
+
+
+def test_service_calls_reject_null_plans(hp):
+    """The plan queries and the tuning calls check their arguments on the host."""
+    import ctypes
+    L = hp.lib()
+    v = [ctypes.c_int(0) for _ in range(5)]
+    assert L.hpx_plan_tuning(None, *[ctypes.byref(x) for x in v]) == hp.HPX_ERR_ARG
+    assert L.hpx_plan_set_tuning(None, 16, 16, 0, 0, 0) == hp.HPX_ERR_ARG
+    assert L.hpx_plan_launches(None) == -1
+    assert L.hpx_plan_flags(None) == -1
+    assert L.hpx_plan_lmax(None) == -1
