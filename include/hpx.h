@@ -89,8 +89,9 @@ extern "C" {
  *   inside hpx_plan_ex: (1) time the ring-FFT and grid-FFT stages of the plan's
  *   batch with 16 and with 32 elements per thread (launch shapes of the
  *   compile-time FFT kernels), for FP32 plans that run the sweeps per call the
- *   three forms of the sweep kernel, and for the tensor-core paths the two
- *   placements of the packing of b, and keep the fastest of each
+ *   three forms of the sweep kernel, for the tensor-core paths the two
+ *   placements of the packing of b, and the two forms of the Bluestein ring
+ *   classes of 4096 points and more, and keep the fastest of each
  *   (hpx_plan_tuning; remembered per nside, lmax, batch, precision and path for
  *   the process's later plans); (2) when the
  *   per-order operators were built, time one analysis
